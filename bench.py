@@ -1,0 +1,297 @@
+"""Benchmark: CLS random walks on one GB300 (or N, as independent history shards).
+
+Workload (default): 3D box of side 10, Sigma = (0.1, 10), Lambda = (1, 0.1),
+c = 0.99, cosine-law incidence on x = 0, 200 flux bins, 1e8 histories per GPU
+per step, FP64, persistent history-based tracker.  One step = one pass of the
+whole walk (source, flights, events, track-length tallies) over 1e8 histories;
+`value` is histories/s over all ranks, device-timed with CUDA events.  The same
+workload also runs with FP32 tracking / FP64 tallies, and both arms report the
+figure of merit FOM = 1 / (sigma_rel(<phi>)^2 T).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank takes its own disjoint history range (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "histories/s and FOM 1/(sigma^2 T) at equal sigma, FP32-batched vs FP64-plain on 1 GB300"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--histories", type=int, default=None, help="override histories per step (tests only)")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-tracking arm")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 arm (profiling only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ distributed
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        import torch
+        if not torch.cuda.is_available():
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v: float) -> float:
+    if pg is None:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (every 200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [int(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": int(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ------------------------------------------------------------ oracle timing
+def oracle_rate(params, seconds_target: float, cores: int, first: int = 0):
+    """Time the FP64 oracle on a bounded sample of the workload over `cores` processes."""
+    import oracle
+    case = oracle.Case(*params[:7], int(params[7]), int(params[8]))
+    t0 = time.perf_counter()
+    pilot = 2000
+    oracle.run(case, 1, first, pilot)
+    rate1 = pilot / (time.perf_counter() - t0)
+    n = max(cores * 2048, int(rate1 * cores * seconds_target))
+    t0 = time.perf_counter()
+    raw = oracle.run_parallel(case, 1, first, n, workers=cores)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, raw["workers"]
+
+
+def reference_arm(args, rank, world, pg):
+    from paper_1708_00765_gb300 import workloads
+    if rank != 0:
+        barrier(pg)
+        return
+    params = workloads.BOX_L10
+    cores = os.cpu_count() or 1
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, n, dt, used = oracle_rate(params, 4.0, cores, first=i * 10_000_000)
+        if i >= args.warmup:
+            rates.append((r, n, dt))
+    value = sum(r for r, _, _ in rates) / len(rates)
+    n_mean = int(sum(n for _, n, _ in rates) / len(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(d for _, _, d in rates) / len(rates),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, 200 bins, FP64 (oracle sample)",
+                   "histories_per_step": n_mean},
+        "cpu_baseline": {"value": value, "unit": "histories/s", "cores": used, "kind": "oracle",
+                         "sample": f"{n_mean} histories of the box L=10 workload per step"},
+        "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    barrier(pg)
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    rank, world, local, pg = dist_setup()
+    if args.impl == "reference":
+        reference_arm(args, rank, world, pg)
+        return
+    import torch
+    import paper_1708_00765_gb300 as cls
+    from paper_1708_00765_gb300 import workloads
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the walk never runs on the CPU)")
+    torch.cuda.set_device(local)
+    cls.load(build_if_missing=True)
+    params = workloads.BOX_L10
+    n = args.histories or workloads.BOX_L10_HISTORIES
+    seed = 1
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    results = {}
+    arms = ([] if args.no_fp64 else ["fp64"]) + ([] if args.no_fp32 else ["fp32"])
+    clocks = None
+    for arm in arms:
+        prob = cls.Problem(params)
+        prob.set_option("precision", arm)
+        # rank r walks its own history ids: warm-up runs come first, the timed runs follow
+        base = rank * (args.warmup + args.steps) * n
+        if base:
+            prob.set_option("first_history", base)
+        barrier(pg)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        with sampler:
+            times = []
+            for i in range(args.warmup + args.steps):
+                flush.zero_()
+                if i == args.warmup:
+                    prob.reset()
+                    if base:
+                        prob.set_option("first_history", base + args.warmup * n)
+                    torch.cuda.synchronize()
+                    barrier(pg)
+                start = torch.cuda.Event(enable_timing=True)
+                stop = torch.cuda.Event(enable_timing=True)
+                start.record(stream)
+                prob.run(n, seed, stream=stream)
+                stop.record(stream)
+                if i >= args.warmup:
+                    times.append((start, stop))
+            torch.cuda.synchronize()
+            barrier(pg)
+        dev_s = sum(a.elapsed_time(b) for a, b in times) * 1e-3
+        if arm == "fp64":
+            clocks = sampler.summary()
+        else:
+            sampler.summary()
+        tal = prob.tallies()
+        dev_max = max_over_ranks(pg, dev_s)
+        hist = world * args.steps * n
+        rel = tal["sigma_total_flux"] / tal["total_flux"]
+        results[arm] = {
+            "histories_per_s": hist / dev_max,
+            "ms_per_step": 1e3 * dev_max / args.steps,
+            "events_per_s": world * tal["n_events"] / dev_max,
+            "collisions_per_s": world * tal["n_coll"] / dev_max,
+            "events_per_history": tal["n_events"] / tal["n_histories"],
+            "R": tal["R"], "T": tal["T"], "A": tal["A"], "total_flux": tal["total_flux"],
+            "sigma_total_flux": tal["sigma_total_flux"],
+            "fom_total_flux": 1.0 / (rel * rel * dev_max / world) if rel > 0 else None,
+            "launch_ms": 1e3 * dev_s / args.steps,
+        }
+        # end to end through the C ABI: host-side run + tallies (D2H + FP64 normalisation) per step
+        if arm == "fp64":
+            e2e_steps = max(1, args.steps)
+            barrier(pg)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                prob.run(n, seed, stream=stream)
+                prob.tallies()
+            e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+            nbatch = prob.get_option("nbatch")
+            results["e2e"] = {"value": world * e2e_steps * n / e2e_s, "unit": "histories/s",
+                              "h2d_bytes_per_step": 48,
+                              "d2h_bytes_per_step": nbatch * int(params[8]) * 8 + 4 * 8 + 9 * 8}
+        prob.close()
+
+    if rank == 0 and "fp64" not in results:
+        print(json.dumps({"profiling_only": True, **results}), flush=True)
+    elif rank == 0:
+        r64 = results["fp64"]
+        line = {
+            "metric": METRIC, "value": r64["histories_per_s"], "unit": "histories/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r64["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, cosine incidence, 200 bins",
+                       "histories_per_step_per_gpu": n, "schedule": "history", "precision": "fp64",
+                       "l2": "flushed between steps (512 MB write)", "seed": seed},
+            "clocks": clocks,
+            "e2e": results["e2e"],
+            "gpu_launches": args.steps * (1 + (0 if args.no_fp32 else 1)),
+            "fp64": r64,
+        }
+        if "fp32" in results:
+            r32 = results["fp32"]
+            line["fp32"] = r32
+            if r32["fom_total_flux"] and r64["fom_total_flux"]:
+                line["fom_ratio_fp32_over_fp64"] = r32["fom_total_flux"] / r64["fom_total_flux"]
+        if not args.no_cpu_baseline and world == 1:
+            rate, ns, dt, used = oracle_rate(params, 10.0, os.cpu_count() or 1, first=10**12)
+            line["cpu_baseline"] = {"value": rate, "unit": "histories/s", "cores": used, "kind": "oracle",
+                                    "sample": f"{ns} histories of the same workload ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+    barrier(pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

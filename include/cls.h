@@ -1,0 +1,206 @@
+/*
+ * cls.h -- C ABI of the GB300 Chord Length Sampling (CLS) library (libcls.so).
+ *
+ * The library runs CLS "Algorithm A" random walks (paper Sec. 4) for
+ * single-speed transport with isotropic scattering through a binary Markov
+ * mixture.  Two geometries: the rod (d = 1, directions +-1) and the 3D box
+ * (d = 3, paper Sec. 4.3) of side L with leakage on the faces normal to x and
+ * specular reflection on the four lateral faces (paper Sec. 2).  Particles
+ * enter through x = 0 with the isotropic incident flux of benchmark suite I
+ * (cosine law, paper Sec. 4.3).  Estimators: reflection R = J(x=0),
+ * transmission T = J(x=L), absorption A, and the track-length scalar flux
+ * phi(x) integrated over y and z on a uniform x mesh (paper Sec. 2).
+ *
+ * Everything runs on one CUDA device in hand-written kernels; there is no CPU
+ * fallback.  Pointers are plain host pointers unless stated; streams are
+ * cudaStream_t passed as void* (NULL = the legacy default stream).
+ *
+ * Error handling: every int-returning call returns CLS_OK (0) or a negative
+ * CLS_E_* code; cls_strerror() names it.  A call that fails leaves the handle
+ * usable unless it returned CLS_E_CUDA, after which the CUDA context may be
+ * unusable (sticky device error).  Nothing is ever printed.
+ *
+ * Thread safety: a handle may be used by one host thread at a time.
+ */
+#ifndef CLS_H
+#define CLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define CLS_OK 0
+#define CLS_E_INVAL (-1)       /* invalid argument or parameter out of range          */
+#define CLS_E_NOMEM (-2)       /* host or device allocation failed                    */
+#define CLS_E_CUDA (-3)        /* a CUDA runtime call or kernel launch failed         */
+#define CLS_E_EVENT_LIMIT (-4) /* some history hit the per-history event cap;        */
+                               /* tallies are still filled (capped histories count    */
+                               /* in n_capped and in no outcome)                      */
+#define CLS_E_STATE (-5)       /* call not valid in the handle's state                */
+#define CLS_E_NODEVICE (-6)    /* no CUDA device: the library never runs on the CPU   */
+
+/* ---------------------------------------------------------------- options */
+#define CLS_OPT_PRECISION 1     /* CLS_PREC_FP64 (default) or CLS_PREC_FP32                 */
+#define CLS_OPT_SCHEDULE 2      /* CLS_SCHED_HISTORY (default) or CLS_SCHED_EVENT           */
+#define CLS_OPT_BLOCK 3         /* threads per block, multiple of 32 in [32, 256]            */
+#define CLS_OPT_CHUNK 4         /* histories a warp claims at once: 32, 64, ..., 1024       */
+#define CLS_OPT_NBATCH 5        /* statistics batches per run, 2..1024 (default 64)         */
+#define CLS_OPT_MAX_EVENTS 6    /* per-history event cap, 1..2^28 (default 1e8)             */
+#define CLS_OPT_BLOCKS_PER_SM 7 /* persistent grid = SMs x this; 0 = occupancy maximum     */
+#define CLS_OPT_BANK 8          /* event schedule: particle bank slots (0 = automatic)      */
+#define CLS_OPT_EVENTS_PER_PASS 9 /* event schedule: events per particle per pass (1..64)  */
+#define CLS_OPT_FIRST_HISTORY 10  /* set the next history id of every case (0..2^62); lets   */
+                                  /* processes walk disjoint history ranges of one seed     */
+
+#define CLS_PREC_FP64 0 /* all arithmetic in FP64 (draw-for-draw equal to the FP64 oracle) */
+#define CLS_PREC_FP32 1 /* position / direction / distance in FP32, tallies in FP64          */
+
+#define CLS_SCHED_HISTORY 1 /* persistent history-based tracker, state in registers          */
+#define CLS_SCHED_EVENT 2   /* event-based tracker over a structure-of-arrays particle bank   */
+
+/* --------------------------------------------------------------- results */
+typedef struct cls_handle cls_handle; /* opaque, owned by the library */
+
+/* Normalised results of one case, filled by cls_tallies / cls_batch_tallies.
+ * All per-source-particle (unit incident current).  Caller-owned. */
+typedef struct {
+    uint64_t n_histories; /* histories accumulated since create / reset            */
+    uint64_t nR, nT, nA;  /* reflected, transmitted, absorbed histories            */
+    uint64_t n_coll;      /* collisions                                            */
+    uint64_t n_interface; /* material-interface crossings                          */
+    uint64_t n_reflect;   /* specular reflections on lateral faces (box only)      */
+    uint64_t n_events;    /* all events (flights)                                  */
+    uint64_t max_events;  /* longest history, in events                            */
+    uint64_t n_capped;    /* histories stopped by the event cap                    */
+    double R, T, A;       /* nR/N, nT/N, nA/N                                       */
+    double total_flux;    /* <phi> = int phi(x) dx = mean track length per history  */
+    double sigma_R, sigma_T, sigma_A; /* standard errors (Bernoulli, per history)   */
+    double sigma_total_flux;          /* standard error from per-history squares    */
+    double track0, track1; /* mean track length in material 0 / 1                   */
+    double *flux;       /* caller array [nbins] or NULL: phi_k = track in bin / (N dx) */
+    double *flux_sigma; /* caller array [nbins] or NULL: standard error of the batch means */
+    double seconds;     /* device time of all runs since create / reset (CUDA events) */
+} cls_tallies_t;
+
+/* Raw (un-normalised) accumulators of one case, for merging runs made on
+ * several devices or processes: sums add, max_events takes the maximum. */
+typedef struct {
+    uint64_t n_histories, nR, nT, nA, n_coll, n_interface, n_reflect, n_events, max_events, n_capped;
+    double sum_t;    /* sum over histories of the total track length */
+    double sum_t2;   /* sum over histories of its square             */
+    double track[2]; /* track length summed per material             */
+    int32_t nbins, nbatch;
+} cls_raw_t;
+
+/* ------------------------------------------------------------ single case */
+
+/* Create a handle for one CLS problem (paper Sec. 2, Tables 1-2 notation):
+ *   sigma0, sigma1   total cross sections Sigma_i >= 0, finite
+ *   lambda0, lambda1 mean chord lengths Lambda_i > 0, finite; material i is
+ *                    picked at the source with p_i = Lambda_i / (Lambda_0 + Lambda_1)
+ *   c0, c1           scattering probabilities c_i = Sigma_s,i / Sigma_i in [0, 1]
+ *   L                rod length / box side, > 0
+ *   d                1 (rod) or 3 (box)
+ *   nbins            uniform flux bins along x, 1..4096
+ * Selects the current CUDA device, allocates the device tallies (library-
+ * owned, freed by cls_destroy) and zeroes them.
+ * Errors: CLS_E_INVAL, CLS_E_NOMEM, CLS_E_NODEVICE, CLS_E_CUDA. */
+int cls_create(double sigma0, double sigma1, double lambda0, double lambda1, double c0, double c1,
+               double L, int d, int nbins, cls_handle **out);
+
+/* Set a CLS_OPT_* option (values above).  Takes effect at the next run.
+ * Errors: CLS_E_INVAL (unknown key or value out of range). */
+int cls_set_option(cls_handle *h, int key, int64_t value);
+
+/* Read back a CLS_OPT_* option (after automatic choices have been made, the
+ * value used by the last run).  Errors: CLS_E_INVAL. */
+int cls_get_option(const cls_handle *h, int key, int64_t *value);
+
+/* Enqueue histories [next, next + n_histories) on `stream` and add them to the
+ * tallies; next starts at 0 and advances by n_histories, so a sequence of runs
+ * equals one long run (checkpoint / resume).  History h draws its random
+ * numbers from Philox4x32-10 with key `seed` and counter (j/2, h, case), so a
+ * run is fully determined by (seed, first history, n).  Asynchronous; the
+ * caller must keep the handle alive until the stream has finished.
+ * Errors: CLS_E_INVAL (n == 0), CLS_E_CUDA. */
+int cls_run(cls_handle *h, uint64_t n_histories, uint64_t seed, void *stream);
+
+/* Synchronise with the last run's stream, copy the tallies to the host and
+ * normalise them in FP64 into *out (out->flux / out->flux_sigma, if not NULL,
+ * receive nbins values).  Errors: CLS_E_STATE (no history run yet),
+ * CLS_E_CUDA, CLS_E_EVENT_LIMIT (out is filled; some histories were capped). */
+int cls_tallies(cls_handle *h, cls_tallies_t *out);
+
+/* Raw accumulators of case `case_idx` (0 for a single-case handle) and, if
+ * flux_batches is not NULL, its raw track-length sums [nbatch][nbins]
+ * (row-major, caller-owned) and, if batch_histories is not NULL, the number of
+ * histories in each batch [nbatch].  Synchronises like cls_tallies.
+ * Errors: CLS_E_INVAL, CLS_E_STATE, CLS_E_CUDA. */
+int cls_raw_tallies(cls_handle *h, int case_idx, cls_raw_t *out, double *flux_batches,
+                    uint64_t *batch_histories);
+
+/* Zero the tallies and restart history numbering at 0 (synchronous). */
+int cls_reset(cls_handle *h);
+
+/* Free all device and host resources of the handle (synchronises first). */
+void cls_destroy(cls_handle *h);
+
+/* Static string describing an error code. */
+const char *cls_strerror(int code);
+
+/* Trace history `history` of case `case_idx` event by event on the device in
+ * the handle's precision: rows of 10 doubles (event, draw index after the
+ * event, x, y, z, wx, wy, wz, material after the event, flight length) with
+ * event codes 0 leak at x=0, 1 leak at x=L, 2 lateral reflection,
+ * 3 scatter, 4 absorption, 5 interface crossing, 6 event cap.  Writes at most
+ * `cap` rows to the caller array `rows` and the number of rows of the whole
+ * history to *n_rows.  Synchronous; does not touch the tallies.
+ * Errors: CLS_E_INVAL, CLS_E_CUDA. */
+int cls_trace(cls_handle *h, int case_idx, uint64_t seed, uint64_t history, double *rows, int cap,
+              int *n_rows);
+
+/* --------------------------------------------------------------- batches */
+
+/* Create a handle for `ncases` independent CLS problems run together in one
+ * persistent launch.  params: ncases x 9 doubles, row-major
+ * (sigma0, sigma1, lambda0, lambda1, c0, c1, L, d, nbins) with the meanings
+ * and limits of cls_create; case k draws with Philox counter word 3 = k.
+ * Errors: as cls_create; ncases in 1..65536. */
+int cls_batch_create(const double *params, int ncases, cls_handle **out);
+
+/* Run n_per_case histories of every case in one persistent launch, its cases
+ * ordered by estimated cost (largest first).  The launch sequence (counter
+ * reset, tracker, nothing else) is captured once into a CUDA graph and
+ * replayed on later calls with new history ranges.  Asynchronous on `stream`.
+ * Errors: CLS_E_INVAL, CLS_E_CUDA. */
+int cls_batch_run(cls_handle *h, uint64_t n_per_case, uint64_t seed, void *stream);
+
+/* Normalised results of case `case_idx`, as cls_tallies.
+ * Errors: CLS_E_INVAL, CLS_E_STATE, CLS_E_CUDA, CLS_E_EVENT_LIMIT. */
+int cls_batch_tallies(cls_handle *h, int case_idx, cls_tallies_t *out);
+
+/* Number of cases of the handle (1 for cls_create handles). */
+int cls_num_cases(const cls_handle *h);
+
+/* ------------------------------------------------------------ diagnostics */
+
+/* Evaluate this library's device Philox4x32-10 and, for comparison, CUDA's
+ * curand_Philox4x32_10 on n counter/key sets.  in: n x 6 u32 (c0, c1, c2, c3,
+ * k0, k1); ours, theirs: n x 4 u32 outputs.  Host arrays; synchronous.
+ * Errors: CLS_E_INVAL, CLS_E_CUDA, CLS_E_NOMEM. */
+int cls_debug_philox(const uint32_t *in, int n, uint32_t *ours, uint32_t *theirs);
+
+/* Device uniforms: draw j of history h (case_id, seed) for n (h, j) pairs, in
+ * FP64 (53 bits, out64) and FP32 (24 bits, out32); either may be NULL. */
+int cls_debug_uniform(uint64_t seed, uint32_t case_id, const uint64_t *h, const uint64_t *j, int n,
+                      double *out64, float *out32);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLS_H */

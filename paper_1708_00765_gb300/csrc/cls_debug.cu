@@ -1,0 +1,93 @@
+// cls_debug.cu -- diagnostic entry points: the device Philox next to CUDA's
+// curand_Philox4x32_10 (called from CUDA's header, not restated), and the
+// device draw-to-uniform mapping.
+#include <curand_kernel.h>
+
+#include <vector>
+
+#include "../../include/cls.h"
+#include "cls_device.cuh"
+
+namespace {
+
+__global__ void philox_pair_kernel(const uint32_t *in, int n, uint32_t *ours, uint32_t *theirs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = make_uint4(in[6 * i + 0], in[6 * i + 1], in[6 * i + 2], in[6 * i + 3]);
+    const uint2 k = make_uint2(in[6 * i + 4], in[6 * i + 5]);
+    const uint4 a = cls::philox4x32_10(c, k);
+    const uint4 b = curand_Philox4x32_10(c, k);
+    ours[4 * i + 0] = a.x;
+    ours[4 * i + 1] = a.y;
+    ours[4 * i + 2] = a.z;
+    ours[4 * i + 3] = a.w;
+    theirs[4 * i + 0] = b.x;
+    theirs[4 * i + 1] = b.y;
+    theirs[4 * i + 2] = b.z;
+    theirs[4 * i + 3] = b.w;
+}
+
+__global__ void uniform_kernel(uint64_t seed, uint32_t case_id, const uint64_t *h, const uint64_t *j, int n,
+                               double *o64, float *o32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint2 key = cls::seed_key(seed);
+    cls::History<double> s64;
+    cls::History<float> s32;
+    s64.h_lo = s32.h_lo = (uint32_t)h[i];
+    s64.h_hi = s32.h_hi = (uint32_t)(h[i] >> 32);
+    s64.cid = s32.cid = case_id;
+    // the cached odd words come from the even draw before them
+    const uint32_t jj = (uint32_t)j[i];
+    s64.j = s32.j = jj & ~1u;
+    double u64 = cls::draw(s64, key);
+    float u32 = cls::draw(s32, key);
+    if (jj & 1u) {
+        u64 = cls::draw(s64, key);
+        u32 = cls::draw(s32, key);
+    }
+    o64[i] = u64;
+    o32[i] = u32;
+}
+
+}  // namespace
+
+extern "C" int cls_debug_philox(const uint32_t *in, int n, uint32_t *ours, uint32_t *theirs) {
+    if (!in || n < 1 || !ours || !theirs) return CLS_E_INVAL;
+    uint32_t *d = nullptr;
+    const size_t bytes = (size_t)n * (6 + 4 + 4) * sizeof(uint32_t);
+    if (cudaMalloc(&d, bytes) != cudaSuccess) return CLS_E_NOMEM;
+    uint32_t *din = d, *dours = d + 6 * (size_t)n, *dtheirs = dours + 4 * (size_t)n;
+    cudaError_t e = cudaMemcpy(din, in, 6 * (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        philox_pair_kernel<<<(n + 255) / 256, 256>>>(din, n, dours, dtheirs);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(ours, dours, 4 * (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(theirs, dtheirs, 4 * (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? CLS_OK : CLS_E_CUDA;
+}
+
+extern "C" int cls_debug_uniform(uint64_t seed, uint32_t case_id, const uint64_t *h, const uint64_t *j, int n,
+                                 double *out64, float *out32) {
+    if (!h || !j || n < 1) return CLS_E_INVAL;
+    for (int i = 0; i < n; ++i)
+        if (j[i] >= (1ull << 32)) return CLS_E_INVAL;
+    uint64_t *dh = nullptr;
+    if (cudaMalloc(&dh, (size_t)n * (2 * sizeof(uint64_t) + sizeof(double) + sizeof(float))) != cudaSuccess)
+        return CLS_E_NOMEM;
+    uint64_t *dj = dh + n;
+    double *d64 = reinterpret_cast<double *>(dj + n);
+    float *d32 = reinterpret_cast<float *>(d64 + n);
+    cudaError_t e = cudaMemcpy(dh, h, n * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dj, j, n * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        uniform_kernel<<<(n + 255) / 256, 256>>>(seed, case_id, dh, dj, n, d64, d32);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && out64) e = cudaMemcpy(out64, d64, n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && out32) e = cudaMemcpy(out32, d32, n * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(dh);
+    return e == cudaSuccess ? CLS_OK : CLS_E_CUDA;
+}

@@ -1,0 +1,539 @@
+// cls_device.cuh -- device side of the CLS random walk (paper Sec. 4, "Algorithm A").
+//
+// One history: sample the source (paper Sec. 4.3 for the box: y, z uniform on
+// the x = 0 face, cosine-law direction; rod: x = 0 moving +x), sample the
+// material label from p_0, then repeat: draw the collision distance
+// l_c = -ln(1-u)/Sigma_m and the interface distance l_i = -Lambda_m ln(1-u),
+// compute the boundary distance l_b, and take the smallest.  Boundary: leak
+// through an x face (R or T) or reflect specularly on a lateral face.
+// Collision: scatter isotropically with probability c_m, else absorb.
+// Interface: switch the label.  Every flight is scored by the track-length
+// estimator on the uniform x mesh.
+//
+// Ties: boundary wins over collision and interface, collision over interface;
+// an x face wins over a lateral face; equal lateral distances reflect both.
+// The collision draw is consumed even when Sigma_m = 0.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cls_internal.h"
+
+namespace cls {
+
+#define CLS_FULL_MASK 0xffffffffu
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies mixed with the other two words and the round key;
+// the key advances by the Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// ------------------------------------------------------- precision traits
+template <typename P>
+struct Real;
+
+template <>
+struct Real<double> {
+    // 53-bit uniform in [0, 1) from the (hi, lo) output words
+    static __device__ __forceinline__ double uniform(uint32_t hi, uint32_t lo) {
+        const unsigned long long b = ((unsigned long long)hi << 32) | (unsigned long long)lo;
+        return (double)(b >> 11) * 0x1p-53;
+    }
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+    static __device__ __forceinline__ double sigma(const CaseParams &c, int m) { return c.sigma[m]; }
+    static __device__ __forceinline__ double lambda(const CaseParams &c, int m) { return c.lambda[m]; }
+    static __device__ __forceinline__ double cscat(const CaseParams &c, int m) { return c.c[m]; }
+    static __device__ __forceinline__ double L(const CaseParams &c) { return c.L; }
+    static __device__ __forceinline__ double p0(const CaseParams &c) { return c.p0; }
+    static __device__ __forceinline__ double dx(const CaseParams &c) { return c.dx; }
+    static __device__ __forceinline__ double inv_dx(const CaseParams &c) { return c.inv_dx; }
+    // l_c = -ln(1 - u) / Sigma (division, as stated; FP64 path is draw-exact)
+    static __device__ __forceinline__ double collision(const CaseParams &c, int m, double u) {
+        return -log(1.0 - u) / c.sigma[m];
+    }
+    static __device__ __forceinline__ double interface(const CaseParams &c, int m, double u) {
+        return -c.lambda[m] * log(1.0 - u);
+    }
+    static __device__ __forceinline__ double recip(double a) { return 1.0 / a; }
+    // (sin, cos) of 2 pi u
+    static __device__ __forceinline__ void sincos_2pi(double u, double *s, double *co) {
+        const double ph = (2.0 * 3.14159265358979323846) * u;
+        sincos(ph, s, co);
+    }
+};
+
+template <>
+struct Real<float> {
+    // the same draw truncated to its top 24 bits
+    static __device__ __forceinline__ float uniform(uint32_t hi, uint32_t) {
+        return (float)(hi >> 8) * 0x1p-24f;
+    }
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+    static __device__ __forceinline__ float sigma(const CaseParams &c, int m) { return c.sigma_f[m]; }
+    static __device__ __forceinline__ float lambda(const CaseParams &c, int m) { return c.lambda_f[m]; }
+    static __device__ __forceinline__ float cscat(const CaseParams &c, int m) { return c.c_f[m]; }
+    static __device__ __forceinline__ float L(const CaseParams &c) { return c.L_f; }
+    static __device__ __forceinline__ float p0(const CaseParams &c) { return c.p0_f; }
+    static __device__ __forceinline__ float dx(const CaseParams &c) { return c.dx_f; }
+    static __device__ __forceinline__ float inv_dx(const CaseParams &c) { return c.inv_dx_f; }
+    static __device__ __forceinline__ float collision(const CaseParams &c, int m, float u) {
+        return -__logf(1.0f - u) * c.inv_sigma_f[m];
+    }
+    static __device__ __forceinline__ float interface(const CaseParams &c, int m, float u) {
+        return -c.lambda_f[m] * __logf(1.0f - u);
+    }
+    static __device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
+    static __device__ __forceinline__ void sincos_2pi(float u, float *s, float *co) {
+        sincospif(2.0f * u, s, co);
+    }
+};
+
+// ----------------------------------------------------------- history state
+template <typename P>
+struct History {
+    P r[3];
+    P w[3];
+    int m;
+    uint32_t j;       // per-history draw index
+    uint32_t c2, c3;  // words 2, 3 of the last Philox block (odd draws)
+    uint32_t h_lo, h_hi, cid;
+    uint32_t events, n_coll, n_int, n_refl;
+    double t, track0, track1;  // FP64 per-history track accumulators
+};
+
+template <typename P>
+__device__ __forceinline__ P draw(History<P> &s, uint2 key) {
+    uint32_t hi, lo;
+    if ((s.j & 1u) == 0u) {
+        const uint4 o = philox4x32_10(make_uint4(s.j >> 1, s.h_lo, s.h_hi, s.cid), key);
+        hi = o.x;
+        lo = o.y;
+        s.c2 = o.z;
+        s.c3 = o.w;
+    } else {
+        hi = s.c2;
+        lo = s.c3;
+    }
+    ++s.j;
+    return Real<P>::uniform(hi, lo);
+}
+
+__device__ __forceinline__ uint2 seed_key(uint64_t seed) {
+    return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Source: position and direction first, then the material label.
+template <typename P>
+__device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint2 key, uint64_t h) {
+    using R = Real<P>;
+    s.h_lo = (uint32_t)h;
+    s.h_hi = (uint32_t)(h >> 32);
+    s.cid = cp.case_id;
+    s.j = 0;
+    s.events = s.n_coll = s.n_int = s.n_refl = 0;
+    s.t = s.track0 = s.track1 = 0.0;
+    s.r[0] = P(0);
+    s.r[1] = P(0);
+    s.r[2] = P(0);
+    s.w[0] = P(1);
+    s.w[1] = P(0);
+    s.w[2] = P(0);
+    if (cp.d == 3) {
+        const P L = R::L(cp);
+        s.r[1] = L * draw(s, key);
+        s.r[2] = L * draw(s, key);
+        const P mu = sqrt(draw(s, key));  // cosine law mu' = sqrt(xi)
+        P sn, cs;
+        R::sincos_2pi(draw(s, key), &sn, &cs);
+        const P st = sqrt(P(1) - mu * mu);
+        s.w[0] = mu;
+        s.w[1] = st * cs;
+        s.w[2] = st * sn;
+    }
+    s.m = (draw(s, key) < R::p0(cp)) ? 0 : 1;
+}
+
+// Trace sink (only instantiated by the trace kernel).
+struct TraceSink {
+    double *rows;
+    int cap;
+    int n;
+};
+
+template <typename P, bool TRACE>
+__device__ __forceinline__ void trace_row(TraceSink *tr, int ev, const History<P> &s, double l) {
+    if constexpr (TRACE) {
+        if (tr->n < tr->cap) {
+            double *row = tr->rows + 10 * (size_t)tr->n;
+            row[0] = ev;
+            row[1] = (double)s.j;
+            row[2] = (double)s.r[0];
+            row[3] = (double)s.r[1];
+            row[4] = (double)s.r[2];
+            row[5] = (double)s.w[0];
+            row[6] = (double)s.w[1];
+            row[7] = (double)s.w[2];
+            row[8] = (double)s.m;
+            row[9] = l;
+        }
+        tr->n++;
+    }
+}
+
+// Track-length estimator: the flight x0 -> x1 (direction cosine wx, length l)
+// deposits in bin k the path length inside e_k <= x < e_k+1, i.e. the
+// x-overlap divided by |wx|.  A flight with wx == 0 scores its whole length
+// in the bin that contains x0.
+template <typename P, bool TALLY>
+__device__ __forceinline__ void deposit(double *bins, const CaseParams &cp, History<P> &s, P x0, P x1, P wx,
+                                        P l, int m) {
+    using R = Real<P>;
+    s.t += (double)l;
+    if (m == 0)
+        s.track0 += (double)l;
+    else
+        s.track1 += (double)l;
+    if constexpr (!TALLY) return;
+    if (!(l > P(0))) return;
+    const int nb = cp.nbins;
+    const P inv_dx = R::inv_dx(cp);
+    if (wx == P(0)) {
+        int k = (int)floor(x0 * inv_dx);
+        k = min(max(k, 0), nb - 1);
+        atomicAdd(&bins[k], (double)l);
+        return;
+    }
+    const P lo = fmin(x0, x1);
+    const P hi = fmax(x0, x1);
+    const P dx = R::dx(cp);
+    const P inv_aw = (cp.d == 1) ? P(1) : R::recip(fabs(wx));
+    int k0 = (int)floor(lo * inv_dx);
+    int k1 = (int)floor(hi * inv_dx);
+    k0 = min(max(k0, 0), nb - 1);
+    k1 = min(max(k1, 0), nb - 1);
+    for (int k = k0; k <= k1; ++k) {
+        const P a = fmax(lo, (P)k * dx);
+        const P b = fmin(hi, (P)(k + 1) * dx);
+        if (b > a) atomicAdd(&bins[k], (double)((b - a) * inv_aw));
+    }
+}
+
+// One event of Algorithm A.  Returns -1 while the history continues, else the
+// terminating event (EV_LEAK_X0, EV_LEAK_XL, EV_ABSORB, EV_CAPPED).
+template <typename P, bool TALLY, bool TRACE>
+__device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 key, uint32_t max_events,
+                                    double *bins, TraceSink *tr) {
+    using R = Real<P>;
+    if (s.events == max_events) {
+        trace_row<P, TRACE>(tr, EV_CAPPED, s, 0.0);
+        return EV_CAPPED;
+    }
+    ++s.events;
+    const int m = s.m;
+    const P INF = R::inf();
+    const P L = R::L(cp);
+
+    // collision, then interface distance
+    const P u_c = draw(s, key);
+    const P l_c = (R::sigma(cp, m) > P(0)) ? R::collision(cp, m, u_c) : INF;
+    const P u_i = draw(s, key);
+    const P l_i = R::interface(cp, m, u_i);
+
+    // boundary distance: x faces, then the lateral faces of the box
+    P l_b = INF;
+    int face = -1;  // 0: x = 0, 1: x = L, 2: lateral
+    if (s.w[0] > P(0)) {
+        l_b = (L - s.r[0]) / s.w[0];
+        face = 1;
+    } else if (s.w[0] < P(0)) {
+        l_b = (P(0) - s.r[0]) / s.w[0];
+        face = 0;
+    }
+    if (l_b < P(0)) l_b = P(0);
+    P l_y = INF, l_z = INF;
+    if (cp.d == 3) {
+        if (s.w[1] > P(0)) l_y = (L - s.r[1]) / s.w[1];
+        else if (s.w[1] < P(0)) l_y = (P(0) - s.r[1]) / s.w[1];
+        if (l_y < P(0)) l_y = P(0);
+        if (l_y < l_b) {
+            l_b = l_y;
+            face = 2;
+        }
+        if (s.w[2] > P(0)) l_z = (L - s.r[2]) / s.w[2];
+        else if (s.w[2] < P(0)) l_z = (P(0) - s.r[2]) / s.w[2];
+        if (l_z < P(0)) l_z = P(0);
+        if (l_z < l_b) {
+            l_b = l_z;
+            face = 2;
+        }
+    }
+
+    if (l_b <= l_c && l_b <= l_i) {
+        if (face != 2) {
+            const P xf = (face == 0) ? P(0) : L;
+            deposit<P, TALLY>(bins, cp, s, s.r[0], xf, s.w[0], l_b, m);
+            s.r[0] = xf;
+            if (cp.d == 3) {
+                s.r[1] += l_b * s.w[1];
+                s.r[2] += l_b * s.w[2];
+            }
+            const int ev = (face == 0) ? EV_LEAK_X0 : EV_LEAK_XL;
+            trace_row<P, TRACE>(tr, ev, s, (double)l_b);
+            return ev;
+        }
+        const P x1 = s.r[0] + l_b * s.w[0];
+        deposit<P, TALLY>(bins, cp, s, s.r[0], x1, s.w[0], l_b, m);
+        s.r[0] = x1;
+        if (l_y == l_b) {
+            s.r[1] = (s.w[1] > P(0)) ? L : P(0);
+            s.w[1] = -s.w[1];
+        } else {
+            s.r[1] += l_b * s.w[1];
+        }
+        if (l_z == l_b) {
+            s.r[2] = (s.w[2] > P(0)) ? L : P(0);
+            s.w[2] = -s.w[2];
+        } else {
+            s.r[2] += l_b * s.w[2];
+        }
+        ++s.n_refl;
+        trace_row<P, TRACE>(tr, EV_REFLECT, s, (double)l_b);
+        return -1;
+    }
+
+    const P l = (l_c <= l_i) ? l_c : l_i;
+    const P x1 = s.r[0] + l * s.w[0];
+    deposit<P, TALLY>(bins, cp, s, s.r[0], x1, s.w[0], l, m);
+    s.r[0] = x1;
+    if (cp.d == 3) {
+        s.r[1] += l * s.w[1];
+        s.r[2] += l * s.w[2];
+    }
+    if (l_c <= l_i) {
+        ++s.n_coll;
+        if (draw(s, key) < R::cscat(cp, m)) {
+            if (cp.d == 1) {
+                s.w[0] = (draw(s, key) < P(0.5)) ? P(1) : P(-1);
+            } else {
+                const P mu = P(2) * draw(s, key) - P(1);
+                P sn, cs;
+                R::sincos_2pi(draw(s, key), &sn, &cs);
+                const P st = sqrt(P(1) - mu * mu);
+                s.w[0] = st * cs;
+                s.w[1] = st * sn;
+                s.w[2] = mu;
+            }
+            trace_row<P, TRACE>(tr, EV_SCATTER, s, (double)l);
+            return -1;
+        }
+        trace_row<P, TRACE>(tr, EV_ABSORB, s, (double)l);
+        return EV_ABSORB;
+    }
+    s.m = 1 - m;
+    ++s.n_int;
+    trace_row<P, TRACE>(tr, EV_INTERFACE, s, (double)l);
+    return -1;
+}
+
+// ------------------------------------------------------- tally regions
+// A warp-private shared-memory region: nbins_stride flux doubles, then S_NUM
+// FP64 statistics, then C_NUM u64 counters.
+template <typename P>
+__device__ __forceinline__ void finish_history(double *region, int nbs, const History<P> &s, int outcome) {
+    double *st = region + nbs;
+    unsigned long long *ct = reinterpret_cast<unsigned long long *>(st + S_NUM);
+    atomicAdd(&st[S_T], s.t);
+    atomicAdd(&st[S_T2], s.t * s.t);
+    if (s.track0 != 0.0) atomicAdd(&st[S_TRACK0], s.track0);
+    if (s.track1 != 0.0) atomicAdd(&st[S_TRACK1], s.track1);
+    const int c = (outcome == EV_LEAK_X0) ? C_R : (outcome == EV_LEAK_XL) ? C_T : (outcome == EV_ABSORB) ? C_A : C_CAPPED;
+    atomicAdd(&ct[c], 1ull);
+    if (s.n_coll) atomicAdd(&ct[C_COLL], (unsigned long long)s.n_coll);
+    if (s.n_int) atomicAdd(&ct[C_INT], (unsigned long long)s.n_int);
+    if (s.n_refl) atomicAdd(&ct[C_REFL], (unsigned long long)s.n_refl);
+    atomicAdd(&ct[C_EVENTS], (unsigned long long)s.events);
+    atomicMax(&ct[C_MAXEV], (unsigned long long)s.events);
+}
+
+// Flush a warp region into the global tally block of (case, batch): one global
+// atomic per non-zero bin, statistic and counter; the region is zeroed.
+__device__ __forceinline__ void flush_region(double *region, const LaunchArgs &a, int case_index, uint32_t batch,
+                                             int lane) {
+    const int nbs = a.t.nbins_stride;
+    const int nb = a.cases[case_index].nbins;
+    double *g = a.t.flux + ((size_t)case_index * a.t.nbatch + batch) * (size_t)nbs;
+    for (int k = lane; k < nb; k += 32) {
+        const double v = region[k];
+        if (v != 0.0) {
+            atomicAdd(&g[k], v);
+            region[k] = 0.0;
+        }
+    }
+    if (lane < S_NUM) {
+        const double v = region[nbs + lane];
+        if (v != 0.0) {
+            atomicAdd(&a.t.stats[(size_t)case_index * S_NUM + lane], v);
+            region[nbs + lane] = 0.0;
+        }
+    } else if (lane < S_NUM + C_NUM) {
+        const int c = lane - S_NUM;
+        unsigned long long *ct = reinterpret_cast<unsigned long long *>(region + nbs + S_NUM);
+        const unsigned long long v = ct[c];
+        if (v != 0ull) {
+            unsigned long long *gc = &a.t.counters[(size_t)case_index * C_NUM + c];
+            if (c == C_MAXEV) atomicMax(gc, v);
+            else atomicAdd(gc, v);
+            ct[c] = 0ull;
+        }
+    }
+    __syncwarp();
+}
+
+// Global chunk index -> run entry (runs are in chunk order).
+__device__ __forceinline__ int find_run(const LaunchArgs &a, uint64_t ch) {
+    int lo = 0, hi = a.nruns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.runs[mid].chunk_begin <= ch) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------- history-based tracker
+// Persistent kernel.  Each warp claims chunks of consecutive histories from a
+// global counter; a lane whose history ends immediately takes the next history
+// of the warp's current chunk (ballot + prefix popcount), so lanes stay busy
+// across history and chunk boundaries.  Each warp owns two shared-memory tally
+// regions keyed by (case, batch); a region is flushed to global memory when
+// its key changes or the warp retires.
+template <typename P>
+__global__ void __launch_bounds__(256) history_kernel(const LaunchArgs a) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int rs = a.region_stride;
+    double *regions = smem + (size_t)warp * 2 * rs;
+    for (int i = lane; i < 2 * rs; i += 32) regions[i] = 0.0;
+    __syncwarp();
+
+    // warp-uniform feeding state
+    int key_run[2] = {-1, -1};
+    uint32_t key_batch[2] = {0, 0};
+    uint64_t cursor = 0, end = 0;  // history ids of the chunk being fed
+    int feed_reg = 0, feed_run = 0;
+    bool exhausted = false, have_pending = false;
+    unsigned long long pending = 0;
+
+    // lane state
+    History<P> s;
+    bool alive = false;
+    int lreg = 0, lcase = 0;
+    uint2 key = make_uint2(0u, 0u);
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    while (true) {
+        unsigned need = __ballot_sync(CLS_FULL_MASK, !alive);
+        while (need != 0u && !exhausted) {
+            if (cursor == end) {
+                unsigned long long ch;
+                if (have_pending) {
+                    ch = pending;
+                    have_pending = false;
+                } else {
+                    if (lane == 0) ch = atomicAdd(a.chunk_counter, 1ull);
+                    ch = __shfl_sync(CLS_FULL_MASK, ch, 0);
+                }
+                if (ch >= a.total_chunks) {
+                    exhausted = true;
+                    break;
+                }
+                const int run = find_run(a, ch);
+                const RunCase &rc = a.runs[run];
+                const uint64_t local0 = (ch - rc.chunk_begin) * (uint64_t)a.chunk;
+                const uint64_t cnt = min((uint64_t)a.chunk, rc.n - local0);
+                const uint32_t batch = (uint32_t)(local0 / rc.batch_len);
+                int r = -1;
+                if (key_run[0] == run && key_batch[0] == batch) r = 0;
+                else if (key_run[1] == run && key_batch[1] == batch) r = 1;
+                if (r < 0) {
+                    const bool live0 = __any_sync(CLS_FULL_MASK, alive && lreg == 0);
+                    const bool live1 = __any_sync(CLS_FULL_MASK, alive && lreg == 1);
+                    const int other = feed_reg ^ 1;
+                    if (!(other ? live1 : live0)) r = other;
+                    else if (!(feed_reg ? live1 : live0)) r = feed_reg;
+                    if (r < 0) {  // both regions in use by other keys: drain first
+                        pending = ch;
+                        have_pending = true;
+                        break;
+                    }
+                    if (key_run[r] >= 0) flush_region(regions + r * rs, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
+                    key_run[r] = run;
+                    key_batch[r] = batch;
+                }
+                feed_reg = r;
+                feed_run = run;
+                cursor = rc.first + local0;
+                end = cursor + cnt;
+            }
+            const uint64_t avail = end - cursor;
+            const uint32_t nneed = __popc(need);
+            const uint32_t take = (avail < nneed) ? (uint32_t)avail : nneed;
+            const uint32_t rank = __popc(need & lt_mask);
+            if (((need >> lane) & 1u) && rank < take) {
+                const RunCase &rc = a.runs[feed_run];
+                lcase = rc.case_index;
+                lreg = feed_reg;
+                key = seed_key(a.seed);
+                source<P>(s, a.cases[lcase], key, cursor + rank);
+                alive = true;
+            }
+            cursor += take;
+            need = __ballot_sync(CLS_FULL_MASK, !alive);
+        }
+        if (!__any_sync(CLS_FULL_MASK, alive)) break;
+        if (alive) {
+            double *region = regions + lreg * rs;
+            const int out = step<P, true, false>(s, a.cases[lcase], key, a.max_events, region, nullptr);
+            if (out >= 0) {
+                finish_history<P>(region, a.t.nbins_stride, s, out);
+                alive = false;
+            }
+        }
+    }
+    __syncwarp();
+    for (int r = 0; r < 2; ++r)
+        if (key_run[r] >= 0) flush_region(regions + r * rs, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
+}
+
+// ------------------------------------------------------------ trace kernel
+template <typename P>
+__global__ void trace_kernel(const TraceArgs a) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const CaseParams &cp = a.cases[a.case_index];
+    const uint2 key = seed_key(a.seed);
+    History<P> s;
+    source<P>(s, cp, key, a.history);
+    TraceSink tr{a.rows, a.cap, 0};
+    while (step<P, false, true>(s, cp, key, a.max_events, nullptr, &tr) < 0) {
+    }
+    *a.n_rows = tr.n;
+}
+
+}  // namespace cls

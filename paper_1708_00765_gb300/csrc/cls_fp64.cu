@@ -1,0 +1,34 @@
+// cls_fp64.cu -- double instantiations of the CLS kernels.
+// Built with --fmad=false: FP64 arithmetic is rounded operation by operation,
+// as the CPU oracle does, so the walk is draw-for-draw identical to it.
+#include "cls_device.cuh"
+#include "cls_event.cuh"
+
+namespace cls {
+
+static bool g_history_attr_set = false;
+
+cudaError_t launch_history_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
+    if (!g_history_attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(history_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        g_history_attr_set = true;
+    }
+    history_kernel<double><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_event_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
+    return launch_event_impl<double>(a, grid, block, smem, s);
+}
+
+cudaError_t launch_trace_fp64(const TraceArgs &a, cudaStream_t s) {
+    trace_kernel<double><<<1, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double>, block, smem);
+}
+
+}  // namespace cls

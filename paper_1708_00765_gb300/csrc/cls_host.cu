@@ -1,0 +1,690 @@
+// cls_host.cu -- host side of the C ABI declared in include/cls.h.
+//
+// Owns the device tallies, orders batched cases by estimated cost, builds the
+// per-run work list, launches the trackers (directly for single cases,
+// through a captured CUDA graph for batches) and normalises the tallies in
+// FP64 (paper Sec. 2 observables; standard errors per Sec. 5 / Eq.
+// combined_var usage: per-history for R, T, A and <phi>, batch means for phi(x)).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cls.h"
+#include "cls_internal.h"
+
+using namespace cls;
+
+namespace {
+
+constexpr int kBatchQuantum = 1024;   // statistics batches are multiples of this many histories
+constexpr int kMaxBins = 4096;
+constexpr int kMaxCases = 65536;
+constexpr uint32_t kMaxEventsLimit = 1u << 28;
+constexpr size_t kMaxSmemPerBlock = 200 * 1024;  // opt-in dynamic shared memory per block
+
+struct Options {
+    int precision = CLS_PREC_FP64;
+    int schedule = CLS_SCHED_HISTORY;
+    int block = 256;
+    int chunk = 256;
+    int nbatch = 64;
+    uint32_t max_events = 100000000u;
+    int blocks_per_sm = 0;
+    int bank = 0;
+    int events_per_pass = 4;
+};
+
+}  // namespace
+
+struct cls_handle {
+    int device = 0;
+    int sm_count = 0;
+    bool batch = false;
+    Options opt;
+    int used_blocks_per_sm = 0;
+    std::vector<CaseParams> cases;
+    CaseParams *d_cases = nullptr;
+    // tallies
+    int nbatch = 0;        // allocated batches (fixed at the first run / reset)
+    int nbins_stride = 0;
+    int nbins_max = 0;
+    double *d_flux = nullptr;
+    double *d_stats = nullptr;
+    unsigned long long *d_counters = nullptr;
+    unsigned long long *d_chunk_counter = nullptr;
+    // per-run work
+    RunCase *h_runs = nullptr;  // pinned
+    RunCase *d_runs = nullptr;
+    cudaEvent_t runs_copied = nullptr;
+    std::vector<int> order;  // case indices, largest estimated cost first
+    std::vector<uint64_t> next_history;
+    std::vector<std::vector<uint64_t>> batch_hist;  // [case][nbatch]
+    std::vector<uint64_t> n_hist;
+    // event-schedule bank
+    void *d_bank = nullptr;
+    size_t bank_bytes = 0;
+    // timing / sync
+    cudaStream_t last_stream = nullptr;
+    bool ran = false;
+    std::vector<cudaEvent_t> ev_pairs;  // start/stop per pending run
+    double seconds = 0.0;
+    // batch graph
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_total_chunks = 0;
+    int graph_key[8] = {0};
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaSuccess ? CLS_OK : CLS_E_CUDA; }
+
+#define CLS_CUDA(call)                              \
+    do {                                            \
+        cudaError_t _e = (call);                    \
+        if (_e != cudaSuccess) return CLS_E_CUDA;   \
+    } while (0)
+
+bool finite(double v) { return std::isfinite(v); }
+
+int validate(const double *p) {
+    const double s0 = p[0], s1 = p[1], l0 = p[2], l1 = p[3], c0 = p[4], c1 = p[5], L = p[6];
+    const double d = p[7], nb = p[8];
+    if (!(finite(s0) && s0 >= 0 && finite(s1) && s1 >= 0)) return CLS_E_INVAL;
+    if (!(finite(l0) && l0 > 0 && finite(l1) && l1 > 0)) return CLS_E_INVAL;
+    if (!(c0 >= 0 && c0 <= 1 && c1 >= 0 && c1 <= 1)) return CLS_E_INVAL;
+    if (!(finite(L) && L > 0)) return CLS_E_INVAL;
+    if (!(d == 1.0 || d == 3.0)) return CLS_E_INVAL;
+    if (!(nb >= 1 && nb <= kMaxBins && nb == std::floor(nb))) return CLS_E_INVAL;
+    return CLS_OK;
+}
+
+// Rough events-per-history estimate, used only to order cases largest first:
+// flights per unit path length times an estimate of the path length, which
+// grows with the number of scatterings ~ 1/(1 - c) and with the size L.
+double cost_estimate(const CaseParams &c) {
+    const double p0 = c.p0, p1 = 1.0 - c.p0;
+    const double sig = p0 * c.sigma[0] + p1 * c.sigma[1];
+    const double rate = sig + p0 / c.lambda[0] + p1 / c.lambda[1];
+    const double cbar = sig > 0 ? (p0 * c.c[0] * c.sigma[0] + p1 * c.c[1] * c.sigma[1]) / sig : 0.0;
+    const double tau = sig * c.L;
+    const double ncol = std::min(1.0 / std::max(1.0 - cbar, 1e-6), 1.0 + tau * tau);
+    const double path = std::min(c.L, 1.0 / std::max(sig, 1e-12)) * (1.0 + ncol * std::min(1.0, tau));
+    return 1.0 + rate * path;
+}
+
+CaseParams make_case(const double *p, uint32_t case_id) {
+    CaseParams c;
+    std::memset(&c, 0, sizeof(c));
+    for (int i = 0; i < 2; ++i) {
+        c.sigma[i] = p[i];
+        c.lambda[i] = p[2 + i];
+        c.c[i] = p[4 + i];
+        c.sigma_f[i] = (float)p[i];
+        c.inv_sigma_f[i] = p[i] > 0 ? (float)(1.0 / p[i]) : 0.0f;
+        c.lambda_f[i] = (float)p[2 + i];
+        c.c_f[i] = (float)p[4 + i];
+    }
+    c.L = p[6];
+    c.d = (int32_t)p[7];
+    c.nbins = (int32_t)p[8];
+    c.p0 = c.lambda[0] / (c.lambda[0] + c.lambda[1]);
+    c.dx = c.L / c.nbins;
+    c.inv_dx = c.nbins / c.L;
+    c.L_f = (float)c.L;
+    c.p0_f = (float)c.p0;
+    c.dx_f = (float)c.dx;
+    c.inv_dx_f = (float)c.inv_dx;
+    c.case_id = case_id;
+    c.cost = cost_estimate(c);
+    return c;
+}
+
+void free_tallies(cls_handle *h) {
+    cudaFree(h->d_flux);
+    cudaFree(h->d_stats);
+    cudaFree(h->d_counters);
+    h->d_flux = nullptr;
+    h->d_stats = nullptr;
+    h->d_counters = nullptr;
+}
+
+int alloc_tallies(cls_handle *h) {
+    const size_t nc = h->cases.size();
+    const size_t nflux = nc * (size_t)h->nbatch * (size_t)h->nbins_stride;
+    if (cudaMalloc(&h->d_flux, nflux * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->d_stats, nc * S_NUM * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->d_counters, nc * C_NUM * sizeof(unsigned long long)) != cudaSuccess) {
+        free_tallies(h);
+        cudaGetLastError();
+        return CLS_E_NOMEM;
+    }
+    return CLS_OK;
+}
+
+int zero_tallies(cls_handle *h) {
+    const size_t nc = h->cases.size();
+    CLS_CUDA(cudaMemset(h->d_flux, 0, nc * (size_t)h->nbatch * h->nbins_stride * sizeof(double)));
+    CLS_CUDA(cudaMemset(h->d_stats, 0, nc * S_NUM * sizeof(double)));
+    CLS_CUDA(cudaMemset(h->d_counters, 0, nc * C_NUM * sizeof(unsigned long long)));
+    h->next_history.assign(nc, 0);
+    h->n_hist.assign(nc, 0);
+    h->batch_hist.assign(nc, std::vector<uint64_t>(h->nbatch, 0));
+    for (cudaEvent_t e : h->ev_pairs) cudaEventDestroy(e);
+    h->ev_pairs.clear();
+    h->seconds = 0.0;
+    h->ran = false;
+    return CLS_OK;
+}
+
+void destroy_graph(cls_handle *h) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
+}
+
+int create_common(const double *params, int ncases, bool batch, cls_handle **out) {
+    if (!out || !params || ncases < 1 || ncases > kMaxCases) return CLS_E_INVAL;
+    *out = nullptr;
+    for (int k = 0; k < ncases; ++k) {
+        int rc = validate(params + 9 * (size_t)k);
+        if (rc) return rc;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return CLS_E_NODEVICE;
+    }
+    cls_handle *h = new (std::nothrow) cls_handle();
+    if (!h) return CLS_E_NOMEM;
+    h->batch = batch;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return CLS_E_CUDA;
+    }
+    h->cases.reserve(ncases);
+    for (int k = 0; k < ncases; ++k) {
+        h->cases.push_back(make_case(params + 9 * (size_t)k, (uint32_t)k));
+        h->nbins_max = std::max(h->nbins_max, h->cases.back().nbins);
+    }
+    h->nbins_stride = (h->nbins_max + 1) & ~1;
+    h->order.resize(ncases);
+    std::iota(h->order.begin(), h->order.end(), 0);
+    std::stable_sort(h->order.begin(), h->order.end(),
+                     [&](int a, int b) { return h->cases[a].cost > h->cases[b].cost; });
+    h->nbatch = h->opt.nbatch;
+    int rc = CLS_OK;
+    if (cudaMalloc(&h->d_cases, ncases * sizeof(CaseParams)) != cudaSuccess ||
+        cudaMalloc(&h->d_runs, ncases * sizeof(RunCase)) != cudaSuccess ||
+        cudaMalloc(&h->d_chunk_counter, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&h->h_runs, ncases * sizeof(RunCase)) != cudaSuccess) {
+        rc = CLS_E_NOMEM;
+    }
+    if (!rc) rc = alloc_tallies(h);
+    if (!rc && cudaMemcpy(h->d_cases, h->cases.data(), ncases * sizeof(CaseParams), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = CLS_E_CUDA;
+    if (!rc && cudaEventCreateWithFlags(&h->runs_copied, cudaEventDisableTiming) != cudaSuccess) rc = CLS_E_CUDA;
+    if (!rc) rc = zero_tallies(h);
+    if (rc) {
+        cudaGetLastError();
+        cls_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return CLS_OK;
+}
+
+uint64_t batch_len_for(uint64_t n, int nbatch) {
+    const uint64_t q = (uint64_t)kBatchQuantum * (uint64_t)nbatch;
+    return (uint64_t)kBatchQuantum * std::max<uint64_t>(1, (n + q - 1) / q);
+}
+
+size_t region_stride(const cls_handle *h) {
+    size_t rs = (size_t)h->nbins_stride + S_NUM + C_NUM;
+    return (rs + 1) & ~(size_t)1;
+}
+
+// Fill the pinned work list for n histories per case and describe the launch.
+int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, LaunchArgs *a) {
+    // the previous run's copy of the pinned work list must have completed
+    CLS_CUDA(cudaEventSynchronize(h->runs_copied));
+    const int nc = (int)h->cases.size();
+    uint64_t chunk_begin = 0;
+    for (int i = 0; i < nc; ++i) {
+        const int k = h->order[i];
+        RunCase &r = h->h_runs[i];
+        r.first = h->next_history[k];
+        r.n = n;
+        r.batch_len = batch_len_for(n, h->nbatch);
+        r.chunk_begin = chunk_begin;
+        r.case_index = k;
+        r.pad = 0;
+        chunk_begin += (n + h->opt.chunk - 1) / h->opt.chunk;
+    }
+    std::memset(a, 0, sizeof(*a));
+    a->cases = h->d_cases;
+    a->runs = h->d_runs;
+    a->nruns = nc;
+    a->chunk = (uint32_t)h->opt.chunk;
+    a->total_chunks = chunk_begin;
+    a->chunk_counter = h->d_chunk_counter;
+    a->t = Tallies{h->d_flux, h->d_stats, h->d_counters, h->nbatch, h->nbins_stride};
+    a->seed = seed;
+    a->max_events = h->opt.max_events;
+    a->region_stride = (int)region_stride(h);
+    return CLS_OK;
+}
+
+void account_run(cls_handle *h, uint64_t n) {
+    const uint64_t bl = batch_len_for(n, h->nbatch);
+    for (size_t k = 0; k < h->cases.size(); ++k) {
+        for (uint64_t b = 0; b * bl < n; ++b) h->batch_hist[k][b] += std::min(bl, n - b * bl);
+        h->next_history[k] += n;
+        h->n_hist[k] += n;
+    }
+    h->ran = true;
+}
+
+int launch_tracker(cls_handle *h, const LaunchArgs &a, cudaStream_t s) {
+    // each warp owns two tally regions; wide meshes get fewer warps per block
+    const size_t per_warp = 2 * (size_t)a.region_stride * sizeof(double);
+    const int fit_warps = (int)std::min<size_t>(kMaxSmemPerBlock / per_warp, 8);
+    if (fit_warps < 1) return CLS_E_INVAL;
+    const int block = 32 * std::min(h->opt.block / 32, fit_warps);
+    const size_t smem = (size_t)(block / 32) * per_warp;
+    int bps = h->opt.blocks_per_sm;
+    if (bps <= 0) {
+        cudaError_t e = (h->opt.precision == CLS_PREC_FP64) ? occupancy_history_fp64(block, smem, &bps)
+                                                             : occupancy_history_fp32(block, smem, &bps);
+        if (e != cudaSuccess) return CLS_E_CUDA;
+        if (bps < 1) return CLS_E_INVAL;  // the block does not fit on an SM
+    }
+    h->used_blocks_per_sm = bps;
+    const int grid = h->sm_count * bps;
+    cudaError_t e;
+    if (h->opt.schedule == CLS_SCHED_EVENT) {
+        e = (h->opt.precision == CLS_PREC_FP64) ? launch_event_fp64(a, grid, block, smem, s)
+                                                 : launch_event_fp32(a, grid, block, smem, s);
+    } else {
+        e = (h->opt.precision == CLS_PREC_FP64) ? launch_history_fp64(a, grid, block, smem, s)
+                                                 : launch_history_fp32(a, grid, block, smem, s);
+    }
+    return cuda_fail(e);
+}
+
+int record_pair(cls_handle *h, cudaStream_t s, bool start) {
+    if (start) {
+        cudaEvent_t e0, e1;
+        CLS_CUDA(cudaEventCreate(&e0));
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return CLS_E_CUDA;
+        }
+        h->ev_pairs.push_back(e0);
+        h->ev_pairs.push_back(e1);
+    }
+    return cuda_fail(cudaEventRecord(h->ev_pairs[h->ev_pairs.size() - (start ? 2 : 1)], s));
+}
+
+int sync_and_time(cls_handle *h) {
+    if (!h->ran) return CLS_E_STATE;
+    CLS_CUDA(cudaSetDevice(h->device));
+    CLS_CUDA(cudaStreamSynchronize(h->last_stream));
+    for (size_t i = 0; i + 1 < h->ev_pairs.size(); i += 2) {
+        float ms = 0.f;
+        CLS_CUDA(cudaEventElapsedTime(&ms, h->ev_pairs[i], h->ev_pairs[i + 1]));
+        h->seconds += ms * 1e-3;
+        cudaEventDestroy(h->ev_pairs[i]);
+        cudaEventDestroy(h->ev_pairs[i + 1]);
+    }
+    h->ev_pairs.clear();
+    return CLS_OK;
+}
+
+int fetch_case(cls_handle *h, int k, std::vector<double> &flux, double stats[S_NUM], unsigned long long ct[C_NUM]) {
+    const size_t nfl = (size_t)h->nbatch * h->nbins_stride;
+    flux.resize(nfl);
+    CLS_CUDA(cudaMemcpy(flux.data(), h->d_flux + (size_t)k * nfl, nfl * sizeof(double), cudaMemcpyDeviceToHost));
+    CLS_CUDA(cudaMemcpy(stats, h->d_stats + (size_t)k * S_NUM, S_NUM * sizeof(double), cudaMemcpyDeviceToHost));
+    CLS_CUDA(cudaMemcpy(ct, h->d_counters + (size_t)k * C_NUM, C_NUM * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost));
+    return CLS_OK;
+}
+
+int tallies_of(cls_handle *h, int k, cls_tallies_t *out) {
+    if (!h || !out || k < 0 || k >= (int)h->cases.size()) return CLS_E_INVAL;
+    int rc = sync_and_time(h);
+    if (rc) return rc;
+    std::vector<double> flux;
+    double st[S_NUM];
+    unsigned long long ct[C_NUM];
+    rc = fetch_case(h, k, flux, st, ct);
+    if (rc) return rc;
+    const CaseParams &cp = h->cases[k];
+    const double N = (double)h->n_hist[k];
+    out->n_histories = h->n_hist[k];
+    out->nR = ct[C_R];
+    out->nT = ct[C_T];
+    out->nA = ct[C_A];
+    out->n_coll = ct[C_COLL];
+    out->n_interface = ct[C_INT];
+    out->n_reflect = ct[C_REFL];
+    out->n_events = ct[C_EVENTS];
+    out->max_events = ct[C_MAXEV];
+    out->n_capped = ct[C_CAPPED];
+    auto bern = [&](unsigned long long c, double *p, double *sd) {
+        *p = c / N;
+        *sd = N > 1 ? std::sqrt(*p * (1.0 - *p) / (N - 1.0)) : NAN;
+    };
+    bern(ct[C_R], &out->R, &out->sigma_R);
+    bern(ct[C_T], &out->T, &out->sigma_T);
+    bern(ct[C_A], &out->A, &out->sigma_A);
+    const double mean = st[S_T] / N;
+    out->total_flux = mean;
+    const double var = std::max(st[S_T2] / N - mean * mean, 0.0);
+    out->sigma_total_flux = N > 1 ? std::sqrt(var / (N - 1.0)) : NAN;
+    out->track0 = st[S_TRACK0] / N;
+    out->track1 = st[S_TRACK1] / N;
+    out->seconds = h->seconds;
+    // phi_k = sum_b flux[b][k] / (N dx); sigma from batch means weighted by batch size:
+    // var = B/(B-1) sum_b (n_b/N)^2 (X_b - X)^2 over the B non-empty batches
+    const int nb = cp.nbins;
+    const std::vector<uint64_t> &bh = h->batch_hist[k];
+    int B = 0;
+    for (int b = 0; b < h->nbatch; ++b) B += bh[b] > 0;
+    for (int j = 0; j < nb; ++j) {
+        double tot = 0.0;
+        for (int b = 0; b < h->nbatch; ++b) tot += flux[(size_t)b * h->nbins_stride + j];
+        const double phi = tot / (N * cp.dx);
+        if (out->flux) out->flux[j] = phi;
+        if (out->flux_sigma) {
+            if (B < 2) {
+                out->flux_sigma[j] = NAN;
+                continue;
+            }
+            double acc = 0.0;
+            for (int b = 0; b < h->nbatch; ++b) {
+                if (!bh[b]) continue;
+                const double nbh = (double)bh[b];
+                const double xb = flux[(size_t)b * h->nbins_stride + j] / (nbh * cp.dx);
+                const double wgt = nbh / N;
+                acc += wgt * wgt * (xb - phi) * (xb - phi);
+            }
+            out->flux_sigma[j] = std::sqrt(acc * B / (B - 1.0));
+        }
+    }
+    return ct[C_CAPPED] ? CLS_E_EVENT_LIMIT : CLS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cls_create(double sigma0, double sigma1, double lambda0, double lambda1, double c0, double c1, double L,
+               int d, int nbins, cls_handle **out) {
+    const double p[9] = {sigma0, sigma1, lambda0, lambda1, c0, c1, L, (double)d, (double)nbins};
+    return create_common(p, 1, false, out);
+}
+
+int cls_batch_create(const double *params, int ncases, cls_handle **out) {
+    return create_common(params, ncases, true, out);
+}
+
+int cls_num_cases(const cls_handle *h) { return h ? (int)h->cases.size() : 0; }
+
+int cls_set_option(cls_handle *h, int key, int64_t v) {
+    if (!h) return CLS_E_INVAL;
+    Options &o = h->opt;
+    switch (key) {
+    case CLS_OPT_PRECISION:
+        if (v != CLS_PREC_FP64 && v != CLS_PREC_FP32) return CLS_E_INVAL;
+        o.precision = (int)v;
+        break;
+    case CLS_OPT_SCHEDULE:
+        if (v != CLS_SCHED_HISTORY && v != CLS_SCHED_EVENT) return CLS_E_INVAL;
+        o.schedule = (int)v;
+        break;
+    case CLS_OPT_BLOCK:
+        if (v < 32 || v > 256 || v % 32) return CLS_E_INVAL;
+        o.block = (int)v;
+        break;
+    case CLS_OPT_CHUNK:
+        if (v < 32 || v > kBatchQuantum || (v & (v - 1))) return CLS_E_INVAL;
+        o.chunk = (int)v;
+        break;
+    case CLS_OPT_NBATCH:
+        if (v < 2 || v > 1024) return CLS_E_INVAL;
+        if (v != h->nbatch) {
+            // changes the tally layout: only allowed before the first run
+            if (h->ran) return CLS_E_STATE;
+            CLS_CUDA(cudaSetDevice(h->device));
+            free_tallies(h);
+            h->nbatch = (int)v;
+            o.nbatch = (int)v;
+            int rc = alloc_tallies(h);
+            if (rc) return rc;
+            rc = zero_tallies(h);
+            if (rc) return rc;
+        }
+        break;
+    case CLS_OPT_MAX_EVENTS:
+        if (v < 1 || v > (int64_t)kMaxEventsLimit) return CLS_E_INVAL;
+        o.max_events = (uint32_t)v;
+        break;
+    case CLS_OPT_BLOCKS_PER_SM:
+        if (v < 0 || v > 32) return CLS_E_INVAL;
+        o.blocks_per_sm = (int)v;
+        break;
+    case CLS_OPT_BANK:
+        if (v < 0 || v > (int64_t)1 << 26) return CLS_E_INVAL;
+        o.bank = (int)v;
+        break;
+    case CLS_OPT_EVENTS_PER_PASS:
+        if (v < 1 || v > 64) return CLS_E_INVAL;
+        o.events_per_pass = (int)v;
+        break;
+    case CLS_OPT_FIRST_HISTORY:
+        if (v < 0 || v > ((int64_t)1 << 62)) return CLS_E_INVAL;
+        for (auto &nh : h->next_history) nh = (uint64_t)v;
+        return CLS_OK;
+    default:
+        return CLS_E_INVAL;
+    }
+    destroy_graph(h);
+    return CLS_OK;
+}
+
+int cls_get_option(const cls_handle *h, int key, int64_t *v) {
+    if (!h || !v) return CLS_E_INVAL;
+    const Options &o = h->opt;
+    switch (key) {
+    case CLS_OPT_PRECISION: *v = o.precision; break;
+    case CLS_OPT_SCHEDULE: *v = o.schedule; break;
+    case CLS_OPT_BLOCK: *v = o.block; break;
+    case CLS_OPT_CHUNK: *v = o.chunk; break;
+    case CLS_OPT_NBATCH: *v = h->nbatch; break;
+    case CLS_OPT_MAX_EVENTS: *v = o.max_events; break;
+    case CLS_OPT_BLOCKS_PER_SM: *v = o.blocks_per_sm ? o.blocks_per_sm : h->used_blocks_per_sm; break;
+    case CLS_OPT_BANK: *v = o.bank; break;
+    case CLS_OPT_EVENTS_PER_PASS: *v = o.events_per_pass; break;
+    case CLS_OPT_FIRST_HISTORY: *v = h->next_history.empty() ? 0 : (int64_t)h->next_history[0]; break;
+    default: return CLS_E_INVAL;
+    }
+    return CLS_OK;
+}
+
+int cls_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
+    if (!h || n == 0 || n > (1ull << 62)) return CLS_E_INVAL;
+    CLS_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    LaunchArgs a;
+    int rc = prepare_run(h, n, seed, &a);
+    if (rc) return rc;
+    rc = record_pair(h, s, true);
+    if (rc) return rc;
+    CLS_CUDA(cudaMemcpyAsync(h->d_runs, h->h_runs, h->cases.size() * sizeof(RunCase), cudaMemcpyHostToDevice, s));
+    CLS_CUDA(cudaEventRecord(h->runs_copied, s));
+    CLS_CUDA(cudaMemsetAsync(h->d_chunk_counter, 0, sizeof(unsigned long long), s));
+    rc = launch_tracker(h, a, s);
+    if (rc) return rc;
+    rc = record_pair(h, s, false);
+    if (rc) return rc;
+    h->last_stream = s;
+    account_run(h, n);
+    return CLS_OK;
+}
+
+int cls_batch_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
+    if (!h || n == 0 || n > (1ull << 62)) return CLS_E_INVAL;
+    CLS_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    LaunchArgs a;
+    int rc = prepare_run(h, n, seed, &a);
+    if (rc) return rc;
+    // capture {counter reset, tracker} once per (launch shape, seed); later calls only
+    // refresh the work list (history ranges) before replaying the graph
+    const int key[8] = {h->opt.precision, h->opt.schedule, h->opt.block, h->opt.chunk,
+                        (int)h->opt.max_events, h->opt.blocks_per_sm, (int)(seed & 0x7fffffff), (int)(seed >> 31)};
+    if (h->graph_exec && (a.total_chunks != h->graph_total_chunks || std::memcmp(key, h->graph_key, sizeof(key))))
+        destroy_graph(h);
+    if (!h->graph_exec) {
+        if (!h->capture_stream) CLS_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+        CLS_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemsetAsync(h->d_chunk_counter, 0, sizeof(unsigned long long), h->capture_stream);
+        int lrc = (e == cudaSuccess) ? launch_tracker(h, a, h->capture_stream) : CLS_E_CUDA;
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
+        if (lrc || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return lrc ? lrc : CLS_E_CUDA;
+        }
+        h->graph = g;
+        if (cudaGraphInstantiate(&h->graph_exec, g, 0) != cudaSuccess) {
+            destroy_graph(h);
+            return CLS_E_CUDA;
+        }
+        h->graph_total_chunks = a.total_chunks;
+        std::memcpy(h->graph_key, key, sizeof(key));
+    }
+    rc = record_pair(h, s, true);
+    if (rc) return rc;
+    CLS_CUDA(cudaMemcpyAsync(h->d_runs, h->h_runs, h->cases.size() * sizeof(RunCase), cudaMemcpyHostToDevice, s));
+    CLS_CUDA(cudaEventRecord(h->runs_copied, s));
+    CLS_CUDA(cudaGraphLaunch(h->graph_exec, s));
+    rc = record_pair(h, s, false);
+    if (rc) return rc;
+    h->last_stream = s;
+    account_run(h, n);
+    return CLS_OK;
+}
+
+int cls_tallies(cls_handle *h, cls_tallies_t *out) { return tallies_of(h, 0, out); }
+
+int cls_batch_tallies(cls_handle *h, int case_idx, cls_tallies_t *out) { return tallies_of(h, case_idx, out); }
+
+int cls_raw_tallies(cls_handle *h, int k, cls_raw_t *out, double *flux_batches, uint64_t *batch_histories) {
+    if (!h || !out || k < 0 || k >= (int)h->cases.size()) return CLS_E_INVAL;
+    int rc = sync_and_time(h);
+    if (rc) return rc;
+    std::vector<double> flux;
+    double st[S_NUM];
+    unsigned long long ct[C_NUM];
+    rc = fetch_case(h, k, flux, st, ct);
+    if (rc) return rc;
+    out->n_histories = h->n_hist[k];
+    out->nR = ct[C_R];
+    out->nT = ct[C_T];
+    out->nA = ct[C_A];
+    out->n_coll = ct[C_COLL];
+    out->n_interface = ct[C_INT];
+    out->n_reflect = ct[C_REFL];
+    out->n_events = ct[C_EVENTS];
+    out->max_events = ct[C_MAXEV];
+    out->n_capped = ct[C_CAPPED];
+    out->sum_t = st[S_T];
+    out->sum_t2 = st[S_T2];
+    out->track[0] = st[S_TRACK0];
+    out->track[1] = st[S_TRACK1];
+    out->nbins = h->cases[k].nbins;
+    out->nbatch = h->nbatch;
+    if (flux_batches)
+        for (int b = 0; b < h->nbatch; ++b)
+            std::memcpy(flux_batches + (size_t)b * out->nbins, flux.data() + (size_t)b * h->nbins_stride,
+                        out->nbins * sizeof(double));
+    if (batch_histories)
+        for (int b = 0; b < h->nbatch; ++b) batch_histories[b] = h->batch_hist[k][b];
+    return CLS_OK;
+}
+
+int cls_reset(cls_handle *h) {
+    if (!h) return CLS_E_INVAL;
+    CLS_CUDA(cudaSetDevice(h->device));
+    if (h->last_stream || h->ran) CLS_CUDA(cudaDeviceSynchronize());
+    return zero_tallies(h);
+}
+
+void cls_destroy(cls_handle *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    destroy_graph(h);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    for (cudaEvent_t e : h->ev_pairs) cudaEventDestroy(e);
+    if (h->runs_copied) cudaEventDestroy(h->runs_copied);
+    free_tallies(h);
+    cudaFree(h->d_cases);
+    cudaFree(h->d_runs);
+    cudaFree(h->d_chunk_counter);
+    cudaFree(h->d_bank);
+    if (h->h_runs) cudaFreeHost(h->h_runs);
+    cudaGetLastError();
+    delete h;
+}
+
+const char *cls_strerror(int code) {
+    switch (code) {
+    case CLS_OK: return "success";
+    case CLS_E_INVAL: return "invalid argument";
+    case CLS_E_NOMEM: return "out of memory";
+    case CLS_E_CUDA: return "CUDA error";
+    case CLS_E_EVENT_LIMIT: return "a history reached the event cap";
+    case CLS_E_STATE: return "call not valid in this state";
+    case CLS_E_NODEVICE: return "no CUDA device";
+    default: return "unknown error";
+    }
+}
+
+int cls_trace(cls_handle *h, int k, uint64_t seed, uint64_t history, double *rows, int cap, int *n_rows) {
+    if (!h || !rows || cap < 1 || !n_rows || k < 0 || k >= (int)h->cases.size()) return CLS_E_INVAL;
+    CLS_CUDA(cudaSetDevice(h->device));
+    double *d_rows = nullptr;
+    int *d_n = nullptr;
+    if (cudaMalloc(&d_rows, (size_t)cap * 10 * sizeof(double)) != cudaSuccess) return CLS_E_NOMEM;
+    if (cudaMalloc(&d_n, sizeof(int)) != cudaSuccess) {
+        cudaFree(d_rows);
+        return CLS_E_NOMEM;
+    }
+    TraceArgs ta{h->d_cases, k, seed, history, h->opt.max_events, d_rows, cap, d_n};
+    cudaError_t e = (h->opt.precision == CLS_PREC_FP64) ? launch_trace_fp64(ta, 0) : launch_trace_fp32(ta, 0);
+    int n = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&n, d_n, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(rows, d_rows, (size_t)std::min(n, cap) * 10 * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d_rows);
+    cudaFree(d_n);
+    if (e != cudaSuccess) return CLS_E_CUDA;
+    *n_rows = n;
+    return CLS_OK;
+}
+
+}  // extern "C"

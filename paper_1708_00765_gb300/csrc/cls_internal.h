@@ -1,0 +1,101 @@
+// cls_internal.h -- structures shared by the host API and the kernels of libcls.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cls {
+
+// One CLS problem as the kernels read it (paper Sec. 2: Sigma_i, Lambda_i, c_i,
+// p_i = Lambda_i / (Lambda_0 + Lambda_1); box side L; uniform x mesh).
+struct CaseParams {
+    double sigma[2];
+    double lambda[2];
+    double c[2];
+    double L;
+    double p0;      // Lambda_0 / (Lambda_0 + Lambda_1)
+    double dx;      // L / nbins
+    double inv_dx;  // nbins / L
+    float sigma_f[2];
+    float inv_sigma_f[2];  // 1 / Sigma_i (0 when Sigma_i = 0, unused then)
+    float lambda_f[2];
+    float c_f[2];
+    float L_f, p0_f, dx_f, inv_dx_f;
+    int32_t d;      // 1 rod, 3 box
+    int32_t nbins;
+    uint32_t case_id;  // Philox counter word 3
+    uint32_t pad;
+    double cost;    // host estimate of events per history (ordering only)
+};
+
+// Per-run work of one case: histories [first, first + n), statistics batch
+// length, and the case's first global chunk index.
+struct RunCase {
+    uint64_t first;
+    uint64_t n;
+    uint64_t batch_len;
+    uint64_t chunk_begin;
+    int32_t case_index;  // index into the CaseParams array / tally blocks
+    int32_t pad;
+};
+
+// Order of the counters and statistics in every tally block and smem region.
+enum Counter { C_R = 0, C_T, C_A, C_COLL, C_INT, C_REFL, C_EVENTS, C_CAPPED, C_MAXEV, C_NUM };
+enum Stat { S_T = 0, S_T2, S_TRACK0, S_TRACK1, S_NUM };
+
+// Event codes of traces (shared with the public trace format).
+enum Event { EV_LEAK_X0 = 0, EV_LEAK_XL = 1, EV_REFLECT = 2, EV_SCATTER = 3, EV_ABSORB = 4,
+             EV_INTERFACE = 5, EV_CAPPED = 6 };
+
+// Device tallies of all cases.  Case k owns
+//   flux     + k * nbatch * nbins_stride   [nbatch][nbins_stride] doubles
+//   stats    + k * S_NUM                   doubles
+//   counters + k * C_NUM                   u64
+struct Tallies {
+    double *flux;
+    double *stats;
+    unsigned long long *counters;
+    int nbatch;
+    int nbins_stride;
+};
+
+struct LaunchArgs {
+    const CaseParams *cases;
+    const RunCase *runs;  // in chunk order (largest estimated cost first)
+    int nruns;
+    uint32_t chunk;       // histories per chunk (divides 1024)
+    uint64_t total_chunks;
+    unsigned long long *chunk_counter;  // zeroed before each launch
+    Tallies t;
+    uint64_t seed;
+    uint32_t max_events;
+    int region_stride;    // doubles per smem region (>= nbins_max + S_NUM + C_NUM, even)
+    // event schedule only
+    void *bank;
+    uint32_t bank_slots;
+    uint32_t events_per_pass;
+};
+
+// Trace kernel arguments (one history).
+struct TraceArgs {
+    const CaseParams *cases;
+    int case_index;
+    uint64_t seed;
+    uint64_t history;
+    uint32_t max_events;
+    double *rows;  // cap x 10
+    int cap;
+    int *n_rows;
+};
+
+// Launchers, one set per precision translation unit.
+cudaError_t launch_history_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_history_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_event_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_event_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_trace_fp64(const TraceArgs &a, cudaStream_t s);
+cudaError_t launch_trace_fp32(const TraceArgs &a, cudaStream_t s);
+cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm);
+cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm);
+
+}  // namespace cls
