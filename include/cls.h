@@ -199,6 +199,46 @@ int cls_debug_philox(const uint32_t *in, int n, uint32_t *ours, uint32_t *theirs
 int cls_debug_uniform(uint64_t seed, uint32_t case_id, const uint64_t *h, const uint64_t *j, int n,
                       double *out64, float *out32);
 
+/* ------------------------------------------------- allocation-free run */
+
+/* Largest number of cases one cls_run_noalloc call takes. */
+#define CLS_NOALLOC_MAX_CASES 64
+
+/* cls_run_noalloc -- run the FP64 history-based tracker without allocating
+ * any device memory.  The paper has no counterpart: this exists for callers
+ * that cannot call cudaMalloc (code living inside another framework's memory
+ * budget, or a process that reserved all device memory up front), for whom
+ * cls_create's allocations are not an option.
+ *
+ * Runs histories [first, first + n) of each of `ncases` cases
+ * (1..CLS_NOALLOC_MAX_CASES; params: ncases x 9 doubles on the host, as in
+ * cls_batch_create; case k draws with Philox counter word 3 = k) with key
+ * `seed`, and ADDS the raw tallies into caller-owned device buffers, which the
+ * caller zeroes before its first call:
+ *   d_flux     [ncases][nbatch][nbins_stride] doubles: track length per
+ *              statistics batch and bin (batch b holds histories
+ *              first + b * L_b ..., L_b = 1024 * ceil(n / (1024 * nbatch)));
+ *   d_stats    [ncases][4] doubles: sum of per-history track length, of its
+ *              square, track length in material 0, in material 1;
+ *   d_counters [ncases][9] u64: reflected, transmitted, absorbed, collisions,
+ *              interface crossings, lateral reflections, events, capped
+ *              histories (all added), longest history in events (maximum).
+ * nbatch is 1..1024, nbins_stride >= the largest nbins.  Results equal
+ * cls_run's for the same seed and history range (default options).
+ *
+ * Scratch (case parameters, work list, work counter; about 12 KB) lives in a
+ * static device array that every GPU loading the library holds until the
+ * process exits.  The first call on each device looks up that array's device
+ * address (with the device current); make that first call before any stream
+ * capture.  All calls share the array and each call rewrites it, so calls that
+ * overlap on the GPU race and must be serialised by the caller (one stream).
+ * Asynchronous on `stream`.
+ * Errors: CLS_E_INVAL (NULL buffer, ncases or n out of range, invalid case,
+ * nbins_stride too small), CLS_E_CUDA. */
+int cls_run_noalloc(const double *params, int ncases, uint64_t first, uint64_t n, uint64_t seed, int nbatch,
+                    int nbins_stride, double *d_flux, double *d_stats, unsigned long long *d_counters,
+                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

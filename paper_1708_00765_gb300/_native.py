@@ -39,7 +39,9 @@ CLS_SCHED_EVENT = 2
 # every symbol include/cls.h declares
 EXPORTED = ("cls_create", "cls_set_option", "cls_get_option", "cls_run", "cls_tallies", "cls_raw_tallies",
             "cls_reset", "cls_destroy", "cls_strerror", "cls_trace", "cls_batch_create", "cls_batch_run",
-            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform")
+            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_run_noalloc")
+
+CLS_NOALLOC_MAX_CASES = 64
 
 
 class ClsError(RuntimeError):
@@ -103,6 +105,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "cls_num_cases": ([H], i),
         "cls_debug_philox": ([P(u32), i, P(u32), P(u32)], i),
         "cls_debug_uniform": ([u64, u32, P(u64), P(u64), i, P(d), P(ctypes.c_float)], i),
+        "cls_run_noalloc": ([P(d), i, u64, u64, u64, i, i, H, H, H, H], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -259,3 +262,12 @@ def debug_uniform(seed: int, case_id: int, h, j):
     _check(load().cls_debug_uniform(seed, case_id, _ptr(h, ctypes.c_uint64), _ptr(j, ctypes.c_uint64), n,
                                     _ptr(o64), _ptr(o32, ctypes.c_float)), "cls_debug_uniform")
     return o64, o32
+
+
+def run_noalloc(params, first: int, n: int, seed: int, nbatch: int, nbins_stride: int, d_flux: int, d_stats: int,
+                d_counters: int, stream=None) -> int:
+    """cls_run_noalloc: tallies are added into caller-owned device buffers given as
+    raw device addresses; returns the library's status code."""
+    params = np.ascontiguousarray(np.atleast_2d(np.asarray(params, dtype=np.float64)))
+    return load().cls_run_noalloc(_ptr(params), params.shape[0], first, n, seed, nbatch, nbins_stride, d_flux,
+                                  d_stats, d_counters, _stream_handle(stream))

@@ -25,6 +25,7 @@ UNITS = {
     "cls_fp32.cu": [],
     "cls_host.cu": [],
     "cls_debug.cu": [],
+    "cls_noalloc.cu": ["--fmad=false"],
 }
 
 
