@@ -31,6 +31,21 @@ sys.path.insert(0, ROOT)
 METRIC = "histories/s and FOM 1/(sigma^2 T) at equal sigma, FP32-batched vs FP64-plain on 1 GB300"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
+# Per-event work of the benchmark workload's kernels, from ncu op counters on a
+# 2e6-history launch (profiles/history_kernel_box_L10.md): FP64 flops
+# (DADD + DMUL + 2 DFMA thread instructions) per event of history_kernel<double>,
+# and warp instructions per event of history_kernel<float>.  Re-measured
+# whenever the kernel changes.
+FP64_FLOP_PER_EVENT = 149.6
+FP32_WARP_INST_PER_EVENT = 39.2
+# DRAM bytes per full-size FP64 launch (1e8 histories) from a one-pass ncu
+# capture of the current kernel (profiles/history_kernel_box_L10.md); set to
+# None whenever the kernel changes until it is captured again.
+FP64_DRAM_BYTES_PER_LAUNCH = 778240
+SM_COUNT = 152           # GB300
+DFMA_PER_SM_CLK = 2      # ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / 152 SMs
+ISSUE_PER_SM_CLK = 4     # one warp instruction per scheduler per clock, 4 schedulers
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -244,6 +259,7 @@ def main():
             "sigma_total_flux": tal["sigma_total_flux"],
             "fom_total_flux": 1.0 / (rel * rel * dev_max / world) if rel > 0 else None,
             "launch_ms": 1e3 * dev_s / args.steps,
+            "events_per_launch": tal["n_events"] / args.steps,
         }
         # end to end through the C ABI: host-side run + tallies (D2H + FP64 normalisation) per step
         if arm == "fp64":
@@ -261,6 +277,24 @@ def main():
                               "d2h_bytes_per_step": nbatch * int(params[8]) * 8 + 4 * 8 + 9 * 8}
         prob.close()
 
+    clk_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    if "fp64" in results:
+        r = results["fp64"]
+        achieved = FP64_FLOP_PER_EVENT * r["events_per_launch"] / (r["launch_ms"] * 1e-3) / 1e12
+        peak = SM_COUNT * DFMA_PER_SM_CLK * 2 * clk_mhz * 1e6 / 1e12
+        r["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": FP64_DRAM_BYTES_PER_LAUNCH,
+                         "kernel": "history_kernel<double>",
+                         "work": f"{FP64_FLOP_PER_EVENT} FP64 flop/event x {r['events_per_launch']:.4g} events/launch",
+                         "peak_from": f"{SM_COUNT} SM x {DFMA_PER_SM_CLK} DFMA/clk x 2 flop x {clk_mhz} MHz (sampled)"}
+    if "fp32" in results:
+        r = results["fp32"]
+        achieved = FP32_WARP_INST_PER_EVENT * r["events_per_launch"] / (r["launch_ms"] * 1e-3) / 1e12
+        peak = SM_COUNT * ISSUE_PER_SM_CLK * clk_mhz * 1e6 / 1e12
+        r["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
+                         "frac": achieved / peak, "kernel": "history_kernel<float>",
+                         "work": f"{FP32_WARP_INST_PER_EVENT} warp instructions/event",
+                         "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} issue/clk x {clk_mhz} MHz"}
     if rank == 0 and "fp64" not in results:
         print(json.dumps({"profiling_only": True, **results}), flush=True)
     elif rank == 0:
@@ -275,7 +309,8 @@ def main():
                        "l2": "flushed between steps (512 MB write)", "seed": seed},
             "clocks": clocks,
             "e2e": results["e2e"],
-            "gpu_launches": args.steps * (1 + (0 if args.no_fp32 else 1)),
+            "gpu_launches": args.steps,
+            "roofline": r64["roofline"],
             "fp64": r64,
         }
         if "fp32" in results:

@@ -48,8 +48,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 template <typename P>
 struct Real;
 
+// FP64 walk: every quantity in double; shared-memory tally bins in double.
 template <>
 struct Real<double> {
+    using Bin = double;
     // 53-bit uniform in [0, 1) from the (hi, lo) output words
     static __device__ __forceinline__ double uniform(uint32_t hi, uint32_t lo) {
         const unsigned long long b = ((unsigned long long)hi << 32) | (unsigned long long)lo;
@@ -57,15 +59,14 @@ struct Real<double> {
     }
     static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
     static __device__ __forceinline__ double sigma(const CaseParams &c, int m) { return c.sigma[m]; }
-    static __device__ __forceinline__ double lambda(const CaseParams &c, int m) { return c.lambda[m]; }
     static __device__ __forceinline__ double cscat(const CaseParams &c, int m) { return c.c[m]; }
     static __device__ __forceinline__ double L(const CaseParams &c) { return c.L; }
     static __device__ __forceinline__ double p0(const CaseParams &c) { return c.p0; }
     static __device__ __forceinline__ double dx(const CaseParams &c) { return c.dx; }
     static __device__ __forceinline__ double inv_dx(const CaseParams &c) { return c.inv_dx; }
-    // l_c = -ln(1 - u) / Sigma (division, as stated; FP64 path is draw-exact)
+    // l_c = -ln(1 - u) / Sigma_m, as -ln(1 - u) * (1 / Sigma_m)
     static __device__ __forceinline__ double collision(const CaseParams &c, int m, double u) {
-        return -log(1.0 - u) / c.sigma[m];
+        return -log(1.0 - u) * c.inv_sigma[m];
     }
     static __device__ __forceinline__ double interface(const CaseParams &c, int m, double u) {
         return -c.lambda[m] * log(1.0 - u);
@@ -78,15 +79,18 @@ struct Real<double> {
     }
 };
 
+// FP32 tracking: position, direction and distances in float; shared-memory
+// tally bins in float, flushed into the FP64 global tallies every few hundred
+// histories; per-history sums convert to FP64 when the history ends.
 template <>
 struct Real<float> {
+    using Bin = float;
     // the same draw truncated to its top 24 bits
     static __device__ __forceinline__ float uniform(uint32_t hi, uint32_t) {
         return (float)(hi >> 8) * 0x1p-24f;
     }
     static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
     static __device__ __forceinline__ float sigma(const CaseParams &c, int m) { return c.sigma_f[m]; }
-    static __device__ __forceinline__ float lambda(const CaseParams &c, int m) { return c.lambda_f[m]; }
     static __device__ __forceinline__ float cscat(const CaseParams &c, int m) { return c.c_f[m]; }
     static __device__ __forceinline__ float L(const CaseParams &c) { return c.L_f; }
     static __device__ __forceinline__ float p0(const CaseParams &c) { return c.p0_f; }
@@ -109,12 +113,21 @@ template <typename P>
 struct History {
     P r[3];
     P w[3];
+    P iw[3];          // 1 / w (infinite when the component is 0)
     int m;
     uint32_t j;       // per-history draw index
     uint32_t c2, c3;  // words 2, 3 of the last Philox block (odd draws)
     uint32_t h_lo, h_hi, cid;
     uint32_t events, n_coll, n_int, n_refl;
-    double t, track0, track1;  // FP64 per-history track accumulators
+    P track0, track1; // per-history track length in material 0 / 1
+};
+
+// One flight's contribution to the mesh: a0 into bin k0, a1 into bin k1
+// (k1 > k0) and c into each interior bin k0 < k < k1.  Empty when k1 < k0.
+template <typename P>
+struct Flight {
+    int k0, k1;
+    P a0, a1, c;
 };
 
 template <typename P>
@@ -138,6 +151,17 @@ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
     return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
+template <typename P>
+__device__ __forceinline__ void set_direction(History<P> &s, P wx, P wy, P wz) {
+    using R = Real<P>;
+    s.w[0] = wx;
+    s.w[1] = wy;
+    s.w[2] = wz;
+    s.iw[0] = (wx != P(0)) ? R::recip(wx) : R::inf();
+    s.iw[1] = (wy != P(0)) ? R::recip(wy) : R::inf();
+    s.iw[2] = (wz != P(0)) ? R::recip(wz) : R::inf();
+}
+
 // Source: position and direction first, then the material label.
 template <typename P>
 __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint2 key, uint64_t h) {
@@ -147,13 +171,10 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint
     s.cid = cp.case_id;
     s.j = 0;
     s.events = s.n_coll = s.n_int = s.n_refl = 0;
-    s.t = s.track0 = s.track1 = 0.0;
+    s.track0 = s.track1 = P(0);
     s.r[0] = P(0);
     s.r[1] = P(0);
     s.r[2] = P(0);
-    s.w[0] = P(1);
-    s.w[1] = P(0);
-    s.w[2] = P(0);
     if (cp.d == 3) {
         const P L = R::L(cp);
         s.r[1] = L * draw(s, key);
@@ -162,9 +183,14 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint
         P sn, cs;
         R::sincos_2pi(draw(s, key), &sn, &cs);
         const P st = sqrt(P(1) - mu * mu);
-        s.w[0] = mu;
-        s.w[1] = st * cs;
-        s.w[2] = st * sn;
+        set_direction(s, mu, st * cs, st * sn);
+    } else {
+        s.w[0] = P(1);
+        s.w[1] = P(0);
+        s.w[2] = P(0);
+        s.iw[0] = P(1);
+        s.iw[1] = R::inf();
+        s.iw[2] = R::inf();
     }
     s.m = (draw(s, key) < R::p0(cp)) ? 0 : 1;
 }
@@ -196,50 +222,55 @@ __device__ __forceinline__ void trace_row(TraceSink *tr, int ev, const History<P
     }
 }
 
-// Track-length estimator: the flight x0 -> x1 (direction cosine wx, length l)
-// deposits in bin k the path length inside e_k <= x < e_k+1, i.e. the
-// x-overlap divided by |wx|.  A flight with wx == 0 scores its whole length
-// in the bin that contains x0.
-template <typename P, bool TALLY>
-__device__ __forceinline__ void deposit(double *bins, const CaseParams &cp, History<P> &s, P x0, P x1, P wx,
-                                        P l, int m) {
+// Track-length estimator: the flight x0 -> x1 (length l, direction cosine wx)
+// scores in bin k the path length inside e_k <= x < e_k+1, the x-overlap times
+// 1/|wx|.  Interior bins receive dx/|wx| each.  A flight with wx == 0 scores
+// its whole length in the bin that contains x0.
+template <typename P>
+__device__ __forceinline__ void plan_flight(Flight<P> &f, History<P> &s, const CaseParams &cp, P x0, P x1, P l,
+                                            int m) {
     using R = Real<P>;
-    s.t += (double)l;
-    if (m == 0)
-        s.track0 += (double)l;
-    else
-        s.track1 += (double)l;
-    if constexpr (!TALLY) return;
+    if (m == 0) s.track0 += l;
+    else s.track1 += l;
+    f.k0 = 0;
+    f.k1 = -1;
     if (!(l > P(0))) return;
     const int nb = cp.nbins;
     const P inv_dx = R::inv_dx(cp);
+    const P wx = s.w[0];
     if (wx == P(0)) {
-        int k = (int)floor(x0 * inv_dx);
-        k = min(max(k, 0), nb - 1);
-        atomicAdd(&bins[k], (double)l);
+        const int k = min(max((int)floor(x0 * inv_dx), 0), nb - 1);
+        f.k0 = f.k1 = k;
+        f.a0 = l;
         return;
     }
-    const P lo = fmin(x0, x1);
-    const P hi = fmax(x0, x1);
-    const P dx = R::dx(cp);
-    const P inv_aw = (cp.d == 1) ? P(1) : R::recip(fabs(wx));
-    int k0 = (int)floor(lo * inv_dx);
-    int k1 = (int)floor(hi * inv_dx);
-    k0 = min(max(k0, 0), nb - 1);
-    k1 = min(max(k1, 0), nb - 1);
-    for (int k = k0; k <= k1; ++k) {
-        const P a = fmax(lo, (P)k * dx);
-        const P b = fmin(hi, (P)(k + 1) * dx);
-        if (b > a) atomicAdd(&bins[k], (double)((b - a) * inv_aw));
+    const P L = R::L(cp);
+    const P lo = fmax(fmin(x0, x1), P(0));
+    const P hi = fmin(fmax(x0, x1), L);
+    const P iaw = fabs(s.iw[0]);
+    const int k0 = min(max((int)floor(lo * inv_dx), 0), nb - 1);
+    const int k1 = min(max((int)floor(hi * inv_dx), 0), nb - 1);
+    f.k0 = k0;
+    f.k1 = k1;
+    if (k0 == k1) {
+        f.a0 = fmax(hi - lo, P(0)) * iaw;
+        return;
     }
+    const P dx = R::dx(cp);
+    f.a0 = fmax((P)(k0 + 1) * dx - lo, P(0)) * iaw;
+    f.a1 = fmax(hi - (P)k1 * dx, P(0)) * iaw;
+    f.c = dx * iaw;
 }
 
-// One event of Algorithm A.  Returns -1 while the history continues, else the
-// terminating event (EV_LEAK_X0, EV_LEAK_XL, EV_ABSORB, EV_CAPPED).
-template <typename P, bool TALLY, bool TRACE>
+// One event of Algorithm A.  Fills the flight to score and returns -1 while
+// the history continues, else the terminating event (EV_LEAK_X0, EV_LEAK_XL,
+// EV_ABSORB, EV_CAPPED).
+template <typename P, bool TRACE>
 __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 key, uint32_t max_events,
-                                    double *bins, TraceSink *tr) {
+                                    Flight<P> &f, TraceSink *tr) {
     using R = Real<P>;
+    f.k0 = 0;
+    f.k1 = -1;
     if (s.events == max_events) {
         trace_row<P, TRACE>(tr, EV_CAPPED, s, 0.0);
         return EV_CAPPED;
@@ -259,24 +290,24 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
     P l_b = INF;
     int face = -1;  // 0: x = 0, 1: x = L, 2: lateral
     if (s.w[0] > P(0)) {
-        l_b = (L - s.r[0]) / s.w[0];
+        l_b = (L - s.r[0]) * s.iw[0];
         face = 1;
     } else if (s.w[0] < P(0)) {
-        l_b = (P(0) - s.r[0]) / s.w[0];
+        l_b = (P(0) - s.r[0]) * s.iw[0];
         face = 0;
     }
     if (l_b < P(0)) l_b = P(0);
     P l_y = INF, l_z = INF;
     if (cp.d == 3) {
-        if (s.w[1] > P(0)) l_y = (L - s.r[1]) / s.w[1];
-        else if (s.w[1] < P(0)) l_y = (P(0) - s.r[1]) / s.w[1];
+        if (s.w[1] > P(0)) l_y = (L - s.r[1]) * s.iw[1];
+        else if (s.w[1] < P(0)) l_y = (P(0) - s.r[1]) * s.iw[1];
         if (l_y < P(0)) l_y = P(0);
         if (l_y < l_b) {
             l_b = l_y;
             face = 2;
         }
-        if (s.w[2] > P(0)) l_z = (L - s.r[2]) / s.w[2];
-        else if (s.w[2] < P(0)) l_z = (P(0) - s.r[2]) / s.w[2];
+        if (s.w[2] > P(0)) l_z = (L - s.r[2]) * s.iw[2];
+        else if (s.w[2] < P(0)) l_z = (P(0) - s.r[2]) * s.iw[2];
         if (l_z < P(0)) l_z = P(0);
         if (l_z < l_b) {
             l_b = l_z;
@@ -287,7 +318,7 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
     if (l_b <= l_c && l_b <= l_i) {
         if (face != 2) {
             const P xf = (face == 0) ? P(0) : L;
-            deposit<P, TALLY>(bins, cp, s, s.r[0], xf, s.w[0], l_b, m);
+            plan_flight(f, s, cp, s.r[0], xf, l_b, m);
             s.r[0] = xf;
             if (cp.d == 3) {
                 s.r[1] += l_b * s.w[1];
@@ -298,17 +329,19 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
             return ev;
         }
         const P x1 = s.r[0] + l_b * s.w[0];
-        deposit<P, TALLY>(bins, cp, s, s.r[0], x1, s.w[0], l_b, m);
+        plan_flight(f, s, cp, s.r[0], x1, l_b, m);
         s.r[0] = x1;
         if (l_y == l_b) {
             s.r[1] = (s.w[1] > P(0)) ? L : P(0);
             s.w[1] = -s.w[1];
+            s.iw[1] = -s.iw[1];
         } else {
             s.r[1] += l_b * s.w[1];
         }
         if (l_z == l_b) {
             s.r[2] = (s.w[2] > P(0)) ? L : P(0);
             s.w[2] = -s.w[2];
+            s.iw[2] = -s.iw[2];
         } else {
             s.r[2] += l_b * s.w[2];
         }
@@ -319,7 +352,7 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
 
     const P l = (l_c <= l_i) ? l_c : l_i;
     const P x1 = s.r[0] + l * s.w[0];
-    deposit<P, TALLY>(bins, cp, s, s.r[0], x1, s.w[0], l, m);
+    plan_flight(f, s, cp, s.r[0], x1, l, m);
     s.r[0] = x1;
     if (cp.d == 3) {
         s.r[1] += l * s.w[1];
@@ -329,15 +362,15 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
         ++s.n_coll;
         if (draw(s, key) < R::cscat(cp, m)) {
             if (cp.d == 1) {
-                s.w[0] = (draw(s, key) < P(0.5)) ? P(1) : P(-1);
+                const P w = (draw(s, key) < P(0.5)) ? P(1) : P(-1);
+                s.w[0] = w;
+                s.iw[0] = w;
             } else {
                 const P mu = P(2) * draw(s, key) - P(1);
                 P sn, cs;
                 R::sincos_2pi(draw(s, key), &sn, &cs);
                 const P st = sqrt(P(1) - mu * mu);
-                s.w[0] = st * cs;
-                s.w[1] = st * sn;
-                s.w[2] = mu;
+                set_direction(s, st * cs, st * sn, mu);
             }
             trace_row<P, TRACE>(tr, EV_SCATTER, s, (double)l);
             return -1;
@@ -352,16 +385,24 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
 }
 
 // ------------------------------------------------------- tally regions
-// A warp-private shared-memory region: nbins_stride flux doubles, then S_NUM
-// FP64 statistics, then C_NUM u64 counters.
+// A warp-private shared-memory region (layout: region_bytes() in
+// cls_internal.h): bins of Real<P>::Bin, FP64 statistics, u64 counters.
 template <typename P>
-__device__ __forceinline__ void finish_history(double *region, int nbs, const History<P> &s, int outcome) {
-    double *st = region + nbs;
+__device__ __forceinline__ double *region_stats(unsigned char *region, int nbs) {
+    return reinterpret_cast<double *>(region + region_bins_bytes((int)sizeof(typename Real<P>::Bin), nbs));
+}
+
+template <typename P>
+__device__ __forceinline__ void finish_history(unsigned char *region, int nbs, const History<P> &s, int outcome) {
+    double *st = region_stats<P>(region, nbs);
     unsigned long long *ct = reinterpret_cast<unsigned long long *>(st + S_NUM);
-    atomicAdd(&st[S_T], s.t);
-    atomicAdd(&st[S_T2], s.t * s.t);
-    if (s.track0 != 0.0) atomicAdd(&st[S_TRACK0], s.track0);
-    if (s.track1 != 0.0) atomicAdd(&st[S_TRACK1], s.track1);
+    const double t0 = (double)s.track0;
+    const double t1 = (double)s.track1;
+    const double t = t0 + t1;
+    atomicAdd(&st[S_T], t);
+    atomicAdd(&st[S_T2], t * t);
+    if (t0 != 0.0) atomicAdd(&st[S_TRACK0], t0);
+    if (t1 != 0.0) atomicAdd(&st[S_TRACK1], t1);
     const int c = (outcome == EV_LEAK_X0) ? C_R : (outcome == EV_LEAK_XL) ? C_T : (outcome == EV_ABSORB) ? C_A : C_CAPPED;
     atomicAdd(&ct[c], 1ull);
     if (s.n_coll) atomicAdd(&ct[C_COLL], (unsigned long long)s.n_coll);
@@ -371,29 +412,75 @@ __device__ __forceinline__ void finish_history(double *region, int nbs, const Hi
     atomicMax(&ct[C_MAXEV], (unsigned long long)s.events);
 }
 
-// Flush a warp region into the global tally block of (case, batch): one global
-// atomic per non-zero bin, statistic and counter; the region is zeroed.
-__device__ __forceinline__ void flush_region(double *region, const LaunchArgs &a, int case_index, uint32_t batch,
+// Score the warp's flights.  Each lane adds its two end bins; the interior
+// bins of all lanes' flights are then spread evenly over the 32 lanes (warp
+// prefix sum of the interior counts, and a 5-step shuffle search for the lane
+// that owns each interior bin), so long flights do not serialise the warp.
+template <typename P>
+__device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes, int lreg, const Flight<P> &f,
                                              int lane) {
-    const int nbs = a.t.nbins_stride;
-    const int nb = a.cases[case_index].nbins;
-    double *g = a.t.flux + ((size_t)case_index * a.t.nbatch + batch) * (size_t)nbs;
-    for (int k = lane; k < nb; k += 32) {
-        const double v = region[k];
-        if (v != 0.0) {
-            atomicAdd(&g[k], v);
-            region[k] = 0.0;
+    using B = typename Real<P>::Bin;
+    const bool has = f.k1 >= f.k0;
+    if (has) {
+        B *bins = reinterpret_cast<B *>(regions + lreg * rbytes);
+        atomicAdd(&bins[f.k0], (B)f.a0);
+        if (f.k1 > f.k0) atomicAdd(&bins[f.k1], (B)f.a1);
+    }
+    const int ni = has ? max(f.k1 - f.k0 - 1, 0) : 0;
+    int incl = ni;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(CLS_FULL_MASK, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(CLS_FULL_MASK, incl, 31);
+    if (total == 0) return;
+    const int base_bin = f.k0 + 1 - (incl - ni);  // interior task t of this lane goes to base_bin + t
+    for (int base = 0; base < total; base += 32) {
+        const int t = base + lane;
+        int o = 0;
+#pragma unroll
+        for (int sft = 16; sft >= 1; sft >>= 1) {
+            const int v = __shfl_sync(CLS_FULL_MASK, incl, o + sft - 1);
+            if (v <= t) o += sft;
+        }
+        const int ob = __shfl_sync(CLS_FULL_MASK, base_bin, o);
+        const P oc = __shfl_sync(CLS_FULL_MASK, f.c, o);
+        const int oreg = __shfl_sync(CLS_FULL_MASK, lreg, o);
+        if (t < total) {
+            B *bins = reinterpret_cast<B *>(regions + oreg * rbytes);
+            atomicAdd(&bins[ob + t], (B)oc);
         }
     }
+}
+
+// Flush a warp region into the global tally block of (case, batch): one global
+// FP64 atomic per non-zero bin, statistic and counter; the region is zeroed.
+template <typename P>
+__device__ __forceinline__ void flush_region(unsigned char *region, const LaunchArgs &a, int case_index,
+                                             uint32_t batch, int lane) {
+    using B = typename Real<P>::Bin;
+    const int nbs = a.t.nbins_stride;
+    const int nb = a.cases[case_index].nbins;
+    B *bins = reinterpret_cast<B *>(region);
+    double *g = a.t.flux + ((size_t)case_index * a.t.nbatch + batch) * (size_t)nbs;
+    for (int k = lane; k < nb; k += 32) {
+        const B v = bins[k];
+        if (v != B(0)) {
+            atomicAdd(&g[k], (double)v);
+            bins[k] = B(0);
+        }
+    }
+    double *st = region_stats<P>(region, nbs);
     if (lane < S_NUM) {
-        const double v = region[nbs + lane];
+        const double v = st[lane];
         if (v != 0.0) {
             atomicAdd(&a.t.stats[(size_t)case_index * S_NUM + lane], v);
-            region[nbs + lane] = 0.0;
+            st[lane] = 0.0;
         }
     } else if (lane < S_NUM + C_NUM) {
         const int c = lane - S_NUM;
-        unsigned long long *ct = reinterpret_cast<unsigned long long *>(region + nbs + S_NUM);
+        unsigned long long *ct = reinterpret_cast<unsigned long long *>(st + S_NUM);
         const unsigned long long v = ct[c];
         if (v != 0ull) {
             unsigned long long *gc = &a.t.counters[(size_t)case_index * C_NUM + c];
@@ -422,20 +509,21 @@ __device__ __forceinline__ int find_run(const LaunchArgs &a, uint64_t ch) {
 // of the warp's current chunk (ballot + prefix popcount), so lanes stay busy
 // across history and chunk boundaries.  Each warp owns two shared-memory tally
 // regions keyed by (case, batch); a region is flushed to global memory when
-// its key changes or the warp retires.
+// its key changes, after flush_every histories, or when the warp retires.
 template <typename P>
 __global__ void __launch_bounds__(256) history_kernel(const LaunchArgs a) {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int rs = a.region_stride;
-    double *regions = smem + (size_t)warp * 2 * rs;
-    for (int i = lane; i < 2 * rs; i += 32) regions[i] = 0.0;
+    const int rb = a.region_bytes;
+    unsigned char *regions = smem + (size_t)warp * 2 * rb;
+    for (int i = lane; i < 2 * rb / 8; i += 32) reinterpret_cast<unsigned long long *>(regions)[i] = 0ull;
     __syncwarp();
 
     // warp-uniform feeding state
-    int key_run[2] = {-1, -1};
-    uint32_t key_batch[2] = {0, 0};
+    int key_run0 = -1, key_run1 = -1;
+    uint32_t key_batch0 = 0, key_batch1 = 0;
+    int fed0 = 0, fed1 = 0;
     uint64_t cursor = 0, end = 0;  // history ids of the chunk being fed
     int feed_reg = 0, feed_run = 0;
     bool exhausted = false, have_pending = false;
@@ -443,9 +531,10 @@ __global__ void __launch_bounds__(256) history_kernel(const LaunchArgs a) {
 
     // lane state
     History<P> s;
+    Flight<P> f;
     bool alive = false;
     int lreg = 0, lcase = 0;
-    uint2 key = make_uint2(0u, 0u);
+    const uint2 key = seed_key(a.seed);
     const unsigned lt_mask = (1u << lane) - 1u;
 
     while (true) {
@@ -470,8 +559,8 @@ __global__ void __launch_bounds__(256) history_kernel(const LaunchArgs a) {
                 const uint64_t cnt = min((uint64_t)a.chunk, rc.n - local0);
                 const uint32_t batch = (uint32_t)(local0 / rc.batch_len);
                 int r = -1;
-                if (key_run[0] == run && key_batch[0] == batch) r = 0;
-                else if (key_run[1] == run && key_batch[1] == batch) r = 1;
+                if (key_run0 == run && key_batch0 == batch) r = 0;
+                else if (key_run1 == run && key_batch1 == batch) r = 1;
                 if (r < 0) {
                     const bool live0 = __any_sync(CLS_FULL_MASK, alive && lreg == 0);
                     const bool live1 = __any_sync(CLS_FULL_MASK, alive && lreg == 1);
@@ -483,9 +572,17 @@ __global__ void __launch_bounds__(256) history_kernel(const LaunchArgs a) {
                         have_pending = true;
                         break;
                     }
-                    if (key_run[r] >= 0) flush_region(regions + r * rs, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
-                    key_run[r] = run;
-                    key_batch[r] = batch;
+                    if (r == 0) {
+                        if (key_run0 >= 0) flush_region<P>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
+                        key_run0 = run;
+                        key_batch0 = batch;
+                        fed0 = 0;
+                    } else {
+                        if (key_run1 >= 0) flush_region<P>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
+                        key_run1 = run;
+                        key_batch1 = batch;
+                        fed1 = 0;
+                    }
                 }
                 feed_reg = r;
                 feed_run = run;
@@ -497,29 +594,42 @@ __global__ void __launch_bounds__(256) history_kernel(const LaunchArgs a) {
             const uint32_t take = (avail < nneed) ? (uint32_t)avail : nneed;
             const uint32_t rank = __popc(need & lt_mask);
             if (((need >> lane) & 1u) && rank < take) {
-                const RunCase &rc = a.runs[feed_run];
-                lcase = rc.case_index;
+                lcase = a.runs[feed_run].case_index;
                 lreg = feed_reg;
-                key = seed_key(a.seed);
                 source<P>(s, a.cases[lcase], key, cursor + rank);
                 alive = true;
             }
+            if (feed_reg == 0) fed0 += (int)take;
+            else fed1 += (int)take;
             cursor += take;
             need = __ballot_sync(CLS_FULL_MASK, !alive);
         }
         if (!__any_sync(CLS_FULL_MASK, alive)) break;
-        if (alive) {
-            double *region = regions + lreg * rs;
-            const int out = step<P, true, false>(s, a.cases[lcase], key, a.max_events, region, nullptr);
-            if (out >= 0) {
-                finish_history<P>(region, a.t.nbins_stride, s, out);
-                alive = false;
+        f.k0 = 0;
+        f.k1 = -1;
+        int out = -1;
+        if (alive) out = step<P, false>(s, a.cases[lcase], key, a.max_events, f, nullptr);
+        warp_deposit<P>(regions, rb, lreg, f, lane);
+        if (out >= 0) {
+            finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, out);
+            alive = false;
+        }
+        if (a.flush_every) {
+            if (fed0 >= a.flush_every) {
+                __syncwarp();
+                flush_region<P>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
+                fed0 = 0;
+            }
+            if (fed1 >= a.flush_every) {
+                __syncwarp();
+                flush_region<P>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
+                fed1 = 0;
             }
         }
     }
     __syncwarp();
-    for (int r = 0; r < 2; ++r)
-        if (key_run[r] >= 0) flush_region(regions + r * rs, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
+    if (key_run0 >= 0) flush_region<P>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
+    if (key_run1 >= 0) flush_region<P>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
 }
 
 // ------------------------------------------------------------ trace kernel
@@ -529,9 +639,10 @@ __global__ void trace_kernel(const TraceArgs a) {
     const CaseParams &cp = a.cases[a.case_index];
     const uint2 key = seed_key(a.seed);
     History<P> s;
+    Flight<P> f;
     source<P>(s, cp, key, a.history);
     TraceSink tr{a.rows, a.cap, 0};
-    while (step<P, false, true>(s, cp, key, a.max_events, nullptr, &tr) < 0) {
+    while (step<P, true>(s, cp, key, a.max_events, f, &tr) < 0) {
     }
     *a.n_rows = tr.n;
 }

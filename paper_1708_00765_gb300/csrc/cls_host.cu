@@ -125,6 +125,7 @@ CaseParams make_case(const double *p, uint32_t case_id) {
     std::memset(&c, 0, sizeof(c));
     for (int i = 0; i < 2; ++i) {
         c.sigma[i] = p[i];
+        c.inv_sigma[i] = p[i] > 0 ? 1.0 / p[i] : 0.0;
         c.lambda[i] = p[2 + i];
         c.c[i] = p[4 + i];
         c.sigma_f[i] = (float)p[i];
@@ -248,10 +249,14 @@ uint64_t batch_len_for(uint64_t n, int nbatch) {
     return (uint64_t)kBatchQuantum * std::max<uint64_t>(1, (n + q - 1) / q);
 }
 
-size_t region_stride(const cls_handle *h) {
-    size_t rs = (size_t)h->nbins_stride + S_NUM + C_NUM;
-    return (rs + 1) & ~(size_t)1;
+int region_bytes_for(const cls_handle *h) {
+    const int bin = (h->opt.precision == CLS_PREC_FP64) ? 8 : 4;
+    return region_bytes(bin, h->nbins_stride);
 }
+
+// FP32 tally bins are flushed into the FP64 global tallies after this many
+// histories per region, which bounds the FP32 partial sums.
+constexpr int kFp32FlushHistories = 256;
 
 // Fill the pinned work list for n histories per case and describe the launch.
 int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, LaunchArgs *a) {
@@ -280,7 +285,8 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, LaunchArgs *a) {
     a->t = Tallies{h->d_flux, h->d_stats, h->d_counters, h->nbatch, h->nbins_stride};
     a->seed = seed;
     a->max_events = h->opt.max_events;
-    a->region_stride = (int)region_stride(h);
+    a->region_bytes = region_bytes_for(h);
+    a->flush_every = (h->opt.precision == CLS_PREC_FP32) ? kFp32FlushHistories : 0;
     return CLS_OK;
 }
 
@@ -294,29 +300,76 @@ void account_run(cls_handle *h, uint64_t n) {
     h->ran = true;
 }
 
-int launch_tracker(cls_handle *h, const LaunchArgs &a, cudaStream_t s) {
-    // each warp owns two tally regions; wide meshes get fewer warps per block
-    const size_t per_warp = 2 * (size_t)a.region_stride * sizeof(double);
-    const int fit_warps = (int)std::min<size_t>(kMaxSmemPerBlock / per_warp, 8);
-    if (fit_warps < 1) return CLS_E_INVAL;
-    const int block = 32 * std::min(h->opt.block / 32, fit_warps);
-    const size_t smem = (size_t)(block / 32) * per_warp;
+// Launch shape of the tracker for the handle's options.
+struct Shape {
+    int grid, block;
+    size_t smem;
+    uint32_t bank_slots;  // event schedule: slots per block and buffer
+};
+
+int tracker_shape(cls_handle *h, int region_bytes, Shape *out) {
+    const bool event = h->opt.schedule == CLS_SCHED_EVENT;
+    const bool fp64 = h->opt.precision == CLS_PREC_FP64;
+    int block;
+    size_t smem;
+    if (event) {
+        // two block-shared regions plus the block's bookkeeping
+        block = h->opt.block;
+        smem = 2 * (size_t)region_bytes + event_block_bytes();
+        if (smem > kMaxSmemPerBlock) return CLS_E_INVAL;
+    } else {
+        // each warp owns two tally regions; wide meshes get fewer warps per block
+        const size_t per_warp = 2 * (size_t)region_bytes;
+        const int fit_warps = (int)std::min<size_t>(kMaxSmemPerBlock / per_warp, 8);
+        if (fit_warps < 1) return CLS_E_INVAL;
+        block = 32 * std::min(h->opt.block / 32, fit_warps);
+        smem = (size_t)(block / 32) * per_warp;
+    }
     int bps = h->opt.blocks_per_sm;
     if (bps <= 0) {
-        cudaError_t e = (h->opt.precision == CLS_PREC_FP64) ? occupancy_history_fp64(block, smem, &bps)
-                                                             : occupancy_history_fp32(block, smem, &bps);
+        cudaError_t e = event ? (fp64 ? occupancy_event_fp64(block, smem, &bps) : occupancy_event_fp32(block, smem, &bps))
+                              : (fp64 ? occupancy_history_fp64(block, smem, &bps)
+                                      : occupancy_history_fp32(block, smem, &bps));
         if (e != cudaSuccess) return CLS_E_CUDA;
         if (bps < 1) return CLS_E_INVAL;  // the block does not fit on an SM
     }
     h->used_blocks_per_sm = bps;
-    const int grid = h->sm_count * bps;
+    out->grid = h->sm_count * bps;
+    out->block = block;
+    out->smem = smem;
+    out->bank_slots = event ? (uint32_t)(h->opt.bank > 0 ? h->opt.bank : 16 * block) : 0u;
+    return CLS_OK;
+}
+
+// Event schedule: make sure the particle bank (grid x 2 buffers x slots x
+// fields x 16 B) is allocated.  Done before any graph capture.
+int ensure_bank(cls_handle *h, const Shape &sh) {
+    if (h->opt.schedule != CLS_SCHED_EVENT) return CLS_OK;
+    const size_t need = (size_t)sh.grid * 2 * sh.bank_slots * (size_t)event_bank_fields(h->opt.precision) * 16;
+    if (need <= h->bank_bytes) return CLS_OK;
+    CLS_CUDA(cudaDeviceSynchronize());
+    cudaFree(h->d_bank);
+    h->d_bank = nullptr;
+    h->bank_bytes = 0;
+    if (cudaMalloc(&h->d_bank, need) != cudaSuccess) {
+        cudaGetLastError();
+        return CLS_E_NOMEM;
+    }
+    h->bank_bytes = need;
+    return CLS_OK;
+}
+
+int launch_tracker(cls_handle *h, LaunchArgs a, const Shape &sh, cudaStream_t s) {
     cudaError_t e;
+    const bool fp64 = h->opt.precision == CLS_PREC_FP64;
     if (h->opt.schedule == CLS_SCHED_EVENT) {
-        e = (h->opt.precision == CLS_PREC_FP64) ? launch_event_fp64(a, grid, block, smem, s)
-                                                 : launch_event_fp32(a, grid, block, smem, s);
+        a.bank = h->d_bank;
+        a.bank_slots = sh.bank_slots;
+        a.events_per_pass = (uint32_t)h->opt.events_per_pass;
+        e = fp64 ? launch_event_fp64(a, sh.grid, sh.block, sh.smem, s) : launch_event_fp32(a, sh.grid, sh.block, sh.smem, s);
     } else {
-        e = (h->opt.precision == CLS_PREC_FP64) ? launch_history_fp64(a, grid, block, smem, s)
-                                                 : launch_history_fp32(a, grid, block, smem, s);
+        e = fp64 ? launch_history_fp64(a, sh.grid, sh.block, sh.smem, s)
+                 : launch_history_fp32(a, sh.grid, sh.block, sh.smem, s);
     }
     return cuda_fail(e);
 }
@@ -529,12 +582,16 @@ int cls_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
     LaunchArgs a;
     int rc = prepare_run(h, n, seed, &a);
     if (rc) return rc;
+    Shape sh;
+    rc = tracker_shape(h, a.region_bytes, &sh);
+    if (!rc) rc = ensure_bank(h, sh);
+    if (rc) return rc;
     rc = record_pair(h, s, true);
     if (rc) return rc;
     CLS_CUDA(cudaMemcpyAsync(h->d_runs, h->h_runs, h->cases.size() * sizeof(RunCase), cudaMemcpyHostToDevice, s));
     CLS_CUDA(cudaEventRecord(h->runs_copied, s));
     CLS_CUDA(cudaMemsetAsync(h->d_chunk_counter, 0, sizeof(unsigned long long), s));
-    rc = launch_tracker(h, a, s);
+    rc = launch_tracker(h, a, sh, s);
     if (rc) return rc;
     rc = record_pair(h, s, false);
     if (rc) return rc;
@@ -557,10 +614,14 @@ int cls_batch_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
     if (h->graph_exec && (a.total_chunks != h->graph_total_chunks || std::memcmp(key, h->graph_key, sizeof(key))))
         destroy_graph(h);
     if (!h->graph_exec) {
+        Shape sh;
+        rc = tracker_shape(h, a.region_bytes, &sh);
+        if (!rc) rc = ensure_bank(h, sh);
+        if (rc) return rc;
         if (!h->capture_stream) CLS_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
         CLS_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemsetAsync(h->d_chunk_counter, 0, sizeof(unsigned long long), h->capture_stream);
-        int lrc = (e == cudaSuccess) ? launch_tracker(h, a, h->capture_stream) : CLS_E_CUDA;
+        int lrc = (e == cudaSuccess) ? launch_tracker(h, a, sh, h->capture_stream) : CLS_E_CUDA;
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
         if (lrc || e2 != cudaSuccess) {

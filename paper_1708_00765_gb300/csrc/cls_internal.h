@@ -10,6 +10,7 @@ namespace cls {
 // p_i = Lambda_i / (Lambda_0 + Lambda_1); box side L; uniform x mesh).
 struct CaseParams {
     double sigma[2];
+    double inv_sigma[2];  // 1 / Sigma_i (0 when Sigma_i = 0, unused then)
     double lambda[2];
     double c[2];
     double L;
@@ -69,7 +70,8 @@ struct LaunchArgs {
     Tallies t;
     uint64_t seed;
     uint32_t max_events;
-    int region_stride;    // doubles per smem region (>= nbins_max + S_NUM + C_NUM, even)
+    int region_bytes;     // bytes per warp tally region (see region_bytes())
+    int flush_every;      // flush a region after this many histories were fed into it (0: never)
     // event schedule only
     void *bank;
     uint32_t bank_slots;
@@ -88,6 +90,14 @@ struct TraceArgs {
     int *n_rows;
 };
 
+// A warp tally region: nbins_stride bins of the precision's tally type (FP64
+// for the FP64 walk, FP32 for FP32 tracking), padded to 8 bytes, then S_NUM
+// FP64 statistics and C_NUM u64 counters; padded to 16 bytes.
+__host__ __device__ inline int region_bins_bytes(int bin_size, int nbins_stride) { return (nbins_stride * bin_size + 7) & ~7; }
+__host__ __device__ inline int region_bytes(int bin_size, int nbins_stride) {
+    return (region_bins_bytes(bin_size, nbins_stride) + 8 * (S_NUM + C_NUM) + 15) & ~15;
+}
+
 // Launchers, one set per precision translation unit.
 cudaError_t launch_history_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_history_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s);
@@ -97,5 +107,9 @@ cudaError_t launch_trace_fp64(const TraceArgs &a, cudaStream_t s);
 cudaError_t launch_trace_fp32(const TraceArgs &a, cudaStream_t s);
 cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm);
 cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm);
+cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm);
+cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm);
+size_t event_block_bytes();           // block-shared bookkeeping of the event tracker
+int event_bank_fields(int precision); // 16-byte SoA fields per particle (0 = FP64)
 
 }  // namespace cls

@@ -106,6 +106,7 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
         CaseParams &c = host.cases[k];
         for (int i = 0; i < 2; ++i) {
             c.sigma[i] = p[i];
+            c.inv_sigma[i] = p[i] > 0 ? 1.0 / p[i] : 0.0;
             c.lambda[i] = p[2 + i];
             c.c[i] = p[4 + i];
             c.sigma_f[i] = (float)p[i];
@@ -154,10 +155,10 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
     a.t = Tallies{d_flux, d_stats, d_counters, nbatch, nbins_stride};
     a.seed = seed;
     a.max_events = 100000000u;
-    int rs = nbins_stride + S_NUM + C_NUM;
-    a.region_stride = (rs + 1) & ~1;
+    a.region_bytes = region_bytes((int)sizeof(double), nbins_stride);
+    a.flush_every = 0;
 
-    const size_t per_warp = 2 * (size_t)a.region_stride * sizeof(double);
+    const size_t per_warp = 2 * (size_t)a.region_bytes;
     int warps = (int)((200 * 1024) / per_warp);
     warps = warps > 8 ? 8 : warps;
     if (warps < 1) return CLS_E_INVAL;
