@@ -29,4 +29,8 @@ cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<float>, block, smem);
 }
 
+cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm) {
+    return occupancy_event_impl<float>(block, smem, blocks_per_sm);
+}
+
 }  // namespace cls

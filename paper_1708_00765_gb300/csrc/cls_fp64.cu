@@ -31,4 +31,14 @@ cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double>, block, smem);
 }
 
+size_t event_block_bytes() { return (sizeof(EventBlock) + 15) & ~(size_t)15; }
+
+int event_bank_fields(int precision) {
+    return precision == 0 ? BankLayout<double>::kFields : BankLayout<float>::kFields;
+}
+
+cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm) {
+    return occupancy_event_impl<double>(block, smem, blocks_per_sm);
+}
+
 }  // namespace cls

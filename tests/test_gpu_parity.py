@@ -231,3 +231,39 @@ def test_batch_cases_match_oracle_exactly():
             assert raw_g[GPU_KEYS.get(key, key)] == ref, (k, key)
         assert raw_g["sum_t"] == pytest.approx(a["sum_t"] + b["sum_t"], rel=RTOL)
     prob.close()
+
+
+# ------------------------------------------------------- event schedule
+
+@pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10])
+@pytest.mark.parametrize("epp,bank,block", [(1, 0, 256), (4, 256, 64), (16, 1024, 128)])
+def test_event_schedule_fp64_parity(params, epp, bank, block):
+    """The event-based tracker walks the same histories draw for draw: counts bit-exact."""
+    n = 20_011
+    raw_g, _ = gpu_raw(params, n, 13, schedule="event", events_per_pass=epp, bank=bank, block=block)
+    raw_o = oracle.run(ocase(params), 13, 0, n)
+    assert_parity(raw_g, raw_o)
+
+
+def test_event_schedule_batch_parity():
+    params = workloads.batch_sweep(12, seed=7, nbins=16)
+    prob = cls.Problem(params, batch=True)
+    prob.set_option("schedule", "event")
+    prob.set_option("bank", 512)
+    prob.run(1500, 9)
+    for k in range(params.shape[0]):
+        raw_g = prob.raw_tallies(k)
+        raw_o = oracle.run(ocase(params[k]), 9, 0, 1500, case_id=k)
+        assert_parity(raw_g, raw_o)
+    prob.close()
+
+
+def test_event_schedule_fp32_statistics():
+    params = workloads.BOX_L10
+    n = 200_000
+    _, t_ev = gpu_raw(params, n, 31, precision="fp32", schedule="event")
+    lp = lp_ado.solve(params[0:2], params[2:4], params[4:6], params[6], "box3d", nbins=int(params[8]))
+    for key in ("R", "T", "A"):
+        assert abs(t_ev[key] - lp[key]) < 4 * t_ev["sigma_" + key]
+    z = (t_ev["flux"] - lp["flux"]) / t_ev["flux_sigma"]
+    assert np.max(np.abs(z)) < 5 and np.mean(z * z) < 1.6
