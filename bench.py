@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-tracking arm")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 arm (profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="box", choices=["box", "diffusive", "batch"],
+                    help="box: L=10 box (default, the headline line); diffusive: L=100 box, c=0.999, "
+                         "history vs event schedule; batch: 256-case sweep, FP64 plain vs FP32 batched")
     return ap.parse_args()
 
 
@@ -189,11 +192,146 @@ def reference_arm(args, rank, world, pg):
 
 
 # ------------------------------------------------------------------ our arm
+def timed_runs(prob, n, seed, steps, warmup, flush, torch, stream, first_base=0):
+    """Device seconds of `steps` runs of n histories after `warmup` untimed ones."""
+    times = []
+    for i in range(warmup + steps):
+        flush.zero_()
+        if i == warmup:
+            prob.reset()
+            if first_base:
+                prob.set_option("first_history", first_base)
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        prob.run(n, seed, stream=stream)
+        stop.record(stream)
+        if i >= warmup:
+            times.append((start, stop))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in times) * 1e-3
+
+
+def diffusive_workload(args, rank, world, pg):
+    """L=100 box, c=0.999, 500 bins, FP32 tracking: history vs event schedule."""
+    import torch
+    import paper_1708_00765_gb300 as cls
+    from paper_1708_00765_gb300 import workloads
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    params = workloads.BOX_DIFFUSIVE
+    n = args.histories or workloads.BOX_DIFFUSIVE_HISTORIES
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    with sampler:
+        for sched in ("history", "event"):
+            prob = cls.Problem(params)
+            prob.set_option("precision", "fp32")
+            prob.set_option("schedule", sched)
+            dev = timed_runs(prob, n, 1, args.steps, args.warmup, flush, torch, stream,
+                             first_base=rank * (args.warmup + args.steps) * n)
+            tal = prob.tallies()
+            dev = max_over_ranks(pg, dev)
+            rel = tal["sigma_total_flux"] / tal["total_flux"]
+            out[sched] = {"histories_per_s": world * args.steps * n / dev, "ms_per_step": 1e3 * dev / args.steps,
+                          "events_per_s": world * tal["n_events"] / dev,
+                          "events_per_history": tal["n_events"] / tal["n_histories"],
+                          "max_events": tal["max_events"], "R": tal["R"], "total_flux": tal["total_flux"],
+                          "fom_total_flux": 1.0 / (rel * rel * dev / world)}
+            prob.close()
+    if rank == 0:
+        h = out["history"]
+        print(json.dumps({
+            "metric": METRIC, "value": h["histories_per_s"], "unit": "histories/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "diffusive box L=100, Sigma=(1,10), Lambda=(0.5,0.2), c=0.999, 500 bins, FP32 tracking",
+                       "histories_per_step_per_gpu": n, "l2": "flushed between steps"},
+            "clocks": sampler.summary(), "history": h, "event": out["event"],
+            "event_over_history": out["event"]["histories_per_s"] / h["histories_per_s"]}), flush=True)
+
+
+def batch_workload(args, rank, world, pg):
+    """256-case sweep: FP64 plain (one launch per case, no graph) vs FP32 batched
+    (all cases in one persistent launch replayed from a CUDA graph), equal N per case."""
+    import torch
+    import paper_1708_00765_gb300 as cls
+    from paper_1708_00765_gb300 import workloads
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cases = workloads.batch_sweep(256, seed=7, nbins=100)
+    n = args.histories or 1_000_000
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    with sampler:
+        # FP64 plain: one handle and one launch per case
+        plain = [cls.Problem(c) for c in cases]
+        for p in plain:
+            p.run(min(n, 20_000), 1, stream=stream)  # warm-up
+            p.reset()
+        torch.cuda.synchronize()
+        flush.zero_()
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for p in plain:
+            p.run(n, 1, stream=stream)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        t64 = max_over_ranks(pg, start.elapsed_time(stop) * 1e-3)
+        tal64 = [p.tallies() for p in plain]
+        for p in plain:
+            p.close()
+        arms = {}
+        for prec in ("fp32", "fp64"):
+            b = cls.Problem(cases, batch=True)
+            b.set_option("precision", prec)
+            dev = timed_runs(b, n, 1, args.steps, args.warmup, flush, torch, stream)
+            arms[prec] = (max_over_ranks(pg, dev) / args.steps, [b.tallies(k) for k in range(len(cases))])
+            b.close()
+    if rank == 0:
+        t32, tal32 = arms["fp32"]
+        t64b, tal64b = arms["fp64"]
+        ratios = []
+        zs = []
+        for a, b in zip(tal64, tal32):
+            s64 = a["sigma_total_flux"]
+            s32 = b["sigma_total_flux"]
+            if s64 > 0 and s32 > 0:
+                ratios.append((s64 * s64 * t64) / (s32 * s32 * t32))
+                zs.append((b["total_flux"] - a["total_flux"]) / math.hypot(s64, s32))
+        ratios.sort()
+        events64 = sum(a["n_events"] for a in tal64)
+        print(json.dumps({
+            "metric": METRIC, "value": world * len(cases) * n / t32, "unit": "histories/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t32, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched sweep, 256 cases (seed 7), 100 bins", "histories_per_case": n,
+                       "l2": "flushed between steps"},
+            "clocks": sampler.summary(),
+            "fp32_batched": {"histories_per_s": world * len(cases) * n / t32, "s_per_replay": t32},
+            "fp64_batched": {"histories_per_s": world * len(cases) * n / t64b, "s_per_replay": t64b},
+            "fp64_plain": {"histories_per_s": world * len(cases) * n / t64, "s_total": t64,
+                           "events_per_s": events64 / t64},
+            "fom_ratio_fp32_batched_over_fp64_plain": {"median": ratios[len(ratios) // 2], "min": ratios[0],
+                                                       "max": ratios[-1], "cases": len(ratios)},
+            "fp32_vs_fp64_z": {"max_abs": max(abs(z) for z in zs), "rms": math.sqrt(sum(z * z for z in zs) / len(zs)),
+                               "note": "same seed: correlated draws, so this z is conservative"},
+        }), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local, pg = dist_setup()
     if args.impl == "reference":
         reference_arm(args, rank, world, pg)
+        return
+    if args.workload != "box":
+        import paper_1708_00765_gb300 as cls
+        cls.load(build_if_missing=True)
+        (diffusive_workload if args.workload == "diffusive" else batch_workload)(args, rank, world, pg)
+        barrier(pg)
         return
     import torch
     import paper_1708_00765_gb300 as cls
