@@ -150,8 +150,11 @@ static double edge(const orc_case_t *cs, int k) { return ((double)k * cs->L) / (
 
 /* Track-length estimator: a flight of length l in material m from x0 to x1
  * with direction cosine wx deposits in bin k the path length inside the slab
- * e_k <= x < e_{k+1}: overlap(x-extent) / |wx|.  A flight with wx == 0 puts its
- * whole length into the bin containing x0. */
+ * e_k <= x < e_{k+1}: overlap(x-extent) / |wx|.  A flight that lies inside one
+ * bin deposits its length l itself (the same path length, free of the
+ * cancellation overlap/|wx| suffers for grazing flights, |wx| -> 0).  The
+ * x-extent is clipped to the box [0, L].  A flight with wx == 0 puts its whole
+ * length into the bin containing x0. */
 static void tally_flight(orc_tally_t *t, double x0, double x1, double wx, double l, int m)
 {
     const orc_case_t *cs = t->cs;
@@ -168,6 +171,8 @@ static void tally_flight(orc_tally_t *t, double x0, double x1, double wx, double
     }
     double lo = x0 < x1 ? x0 : x1;
     double hi = x0 < x1 ? x1 : x0;
+    if (lo < 0.0) lo = 0.0;
+    if (hi > cs->L) hi = cs->L;
     double aw = fabs(wx);
     /* only bins whose edges can overlap [lo, hi] are visited; the overlap
      * formula itself is the definition */
@@ -179,7 +184,7 @@ static void tally_flight(orc_tally_t *t, double x0, double x1, double wx, double
         double a = lo > edge(cs, k) ? lo : edge(cs, k);
         double b = hi < edge(cs, k + 1) ? hi : edge(cs, k + 1);
         if (b > a)
-            nsum_add(&t->bins[k], (b - a) / aw);
+            nsum_add(&t->bins[k], (a == lo && b == hi) ? l : (b - a) / aw);
     }
 }
 
