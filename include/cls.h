@@ -45,7 +45,7 @@ extern "C" {
 
 /* ---------------------------------------------------------------- options */
 #define CLS_OPT_PRECISION 1     /* CLS_PREC_FP64 (default) or CLS_PREC_FP32                 */
-#define CLS_OPT_SCHEDULE 2      /* CLS_SCHED_HISTORY (default) or CLS_SCHED_EVENT           */
+#define CLS_OPT_SCHEDULE 2      /* CLS_SCHED_HISTORY (default), CLS_SCHED_EVENT, CLS_SCHED_AUTO */
 #define CLS_OPT_BLOCK 3         /* threads per block, multiple of 32 in [32, 256]            */
 #define CLS_OPT_CHUNK 4         /* histories a warp claims at once: 32, 64, ..., 1024       */
 #define CLS_OPT_NBATCH 5        /* statistics batches per run, 2..1024 (default 64)         */
@@ -59,6 +59,7 @@ extern "C" {
 #define CLS_PREC_FP64 0 /* all arithmetic in FP64 (draw-for-draw equal to the FP64 oracle) */
 #define CLS_PREC_FP32 1 /* position / direction / distance in FP32, tallies in FP64          */
 
+#define CLS_SCHED_AUTO 0    /* cls_autotune picks the schedule and launch shape at the first run */
 #define CLS_SCHED_HISTORY 1 /* persistent history-based tracker, state in registers          */
 #define CLS_SCHED_EVENT 2   /* event-based tracker over a structure-of-arrays particle bank   */
 
@@ -162,6 +163,19 @@ const char *cls_strerror(int code);
  * Errors: CLS_E_INVAL, CLS_E_CUDA. */
 int cls_trace(cls_handle *h, int case_idx, uint64_t seed, uint64_t history, double *rows, int cap,
               int *n_rows);
+
+/* Autotune the handle's launch: time pilot runs of n_pilot histories per case
+ * (seed `seed`, history ids far above any a caller uses) for each candidate --
+ * history schedule x block {64, 128, 256} x chunk {64, 256, 1024}, and event
+ * schedule x block {128, 256} x events per pass {4, 16} -- on a temporary twin
+ * handle with the same cases and precision, so the handle's own tallies are
+ * untouched, then set the fastest candidate's options on the handle.  Results
+ * are cached by a signature of (precision, cases) in memory and, if the
+ * environment variable CLS_AUTOTUNE_CACHE names a file, in that file.  With
+ * CLS_OPT_SCHEDULE = CLS_SCHED_AUTO the first run calls this itself with
+ * n_pilot = n/16 clamped to [4096, 262144].  Synchronous on `stream`.
+ * Errors: CLS_E_INVAL, CLS_E_NOMEM, CLS_E_CUDA. */
+int cls_autotune(cls_handle *h, uint64_t n_pilot, uint64_t seed, void *stream);
 
 /* --------------------------------------------------------------- batches */
 

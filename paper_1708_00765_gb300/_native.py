@@ -33,13 +33,14 @@ CLS_OPT_FIRST_HISTORY = 10
 
 CLS_PREC_FP64 = 0
 CLS_PREC_FP32 = 1
+CLS_SCHED_AUTO = 0
 CLS_SCHED_HISTORY = 1
 CLS_SCHED_EVENT = 2
 
 # every symbol include/cls.h declares
 EXPORTED = ("cls_create", "cls_set_option", "cls_get_option", "cls_run", "cls_tallies", "cls_raw_tallies",
             "cls_reset", "cls_destroy", "cls_strerror", "cls_trace", "cls_batch_create", "cls_batch_run",
-            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_run_noalloc")
+            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_run_noalloc", "cls_autotune")
 
 CLS_NOALLOC_MAX_CASES = 64
 
@@ -106,6 +107,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "cls_debug_philox": ([P(u32), i, P(u32), P(u32)], i),
         "cls_debug_uniform": ([u64, u32, P(u64), P(u64), i, P(d), P(ctypes.c_float)], i),
         "cls_run_noalloc": ([P(d), i, u64, u64, u64, i, i, H, H, H, H], i),
+        "cls_autotune": ([H, u64, u64, H], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -142,7 +144,8 @@ OPTIONS = {"precision": CLS_OPT_PRECISION, "schedule": CLS_OPT_SCHEDULE, "block"
            "chunk": CLS_OPT_CHUNK, "nbatch": CLS_OPT_NBATCH, "max_events": CLS_OPT_MAX_EVENTS,
            "blocks_per_sm": CLS_OPT_BLOCKS_PER_SM, "bank": CLS_OPT_BANK,
            "events_per_pass": CLS_OPT_EVENTS_PER_PASS, "first_history": CLS_OPT_FIRST_HISTORY}
-VALUES = {"fp64": CLS_PREC_FP64, "fp32": CLS_PREC_FP32, "history": CLS_SCHED_HISTORY, "event": CLS_SCHED_EVENT}
+VALUES = {"fp64": CLS_PREC_FP64, "fp32": CLS_PREC_FP32, "history": CLS_SCHED_HISTORY, "event": CLS_SCHED_EVENT,
+          "auto": CLS_SCHED_AUTO}
 
 
 class Problem:
@@ -203,6 +206,11 @@ class Problem:
 
     def reset(self):
         _check(load().cls_reset(self._h), "cls_reset")
+
+    def autotune(self, n_pilot: int, seed: int = 1, stream=None) -> dict:
+        """cls_autotune: returns the chosen schedule and launch shape."""
+        _check(load().cls_autotune(self._h, n_pilot, seed, _stream_handle(stream)), "cls_autotune")
+        return {k: self.get_option(k) for k in ("schedule", "block", "chunk", "events_per_pass")}
 
     def tallies(self, case: int = 0) -> dict:
         nb = self.nbins[case]

@@ -1,7 +1,6 @@
 """Build libcls.so in-tree with nvcc for sm_103a (GB300).
 
-Each translation unit compiles in parallel; the FP64 kernels are compiled with
---fmad=false so that their arithmetic rounds operation by operation.
+Each translation unit compiles in parallel.
 """
 from __future__ import annotations
 
@@ -21,11 +20,11 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
           "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 UNITS = {
-    "cls_fp64.cu": ["--fmad=false"],
+    "cls_fp64.cu": [],
     "cls_fp32.cu": [],
     "cls_host.cu": [],
     "cls_debug.cu": [],
-    "cls_noalloc.cu": ["--fmad=false"],
+    "cls_noalloc.cu": [],
 }
 
 

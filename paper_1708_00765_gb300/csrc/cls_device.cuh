@@ -49,34 +49,54 @@ template <typename P>
 struct Real;
 
 // FP64 walk: every quantity in double; shared-memory tally bins in double.
+// Comparisons of distances (non-negative after clamping) and sign tests run on
+// the IEEE bit patterns in the integer pipes, which order non-negative doubles
+// like the numbers they encode; the FP64 pipe is left to the arithmetic.
 template <>
 struct Real<double> {
     using Bin = double;
-    // 53-bit uniform in [0, 1) from the (hi, lo) output words
+    static __device__ __forceinline__ unsigned long long k53(uint32_t hi, uint32_t lo) {
+        return (((unsigned long long)hi << 32) | (unsigned long long)lo) >> 11;
+    }
+    // 53-bit uniform u = k 2^-53 in [0, 1) from the (hi, lo) output words
     static __device__ __forceinline__ double uniform(uint32_t hi, uint32_t lo) {
-        const unsigned long long b = ((unsigned long long)hi << 32) | (unsigned long long)lo;
-        return (double)(b >> 11) * 0x1p-53;
+        return (double)k53(hi, lo) * 0x1p-53;
+    }
+    // 1 - u, exactly: (2^53 - k) 2^-53
+    static __device__ __forceinline__ double one_minus(uint32_t hi, uint32_t lo) {
+        return (double)((1ull << 53) - k53(hi, lo)) * 0x1p-53;
+    }
+    // u < v for the threshold ceil(v 2^53)
+    static __device__ __forceinline__ bool below(uint32_t hi, uint32_t lo, unsigned long long thr53, uint32_t) {
+        return k53(hi, lo) < thr53;
     }
     static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+    static __device__ __forceinline__ bool pos(double w) { return __double_as_longlong(w) > 0; }
+    static __device__ __forceinline__ bool neg(double w) {
+        const long long b = __double_as_longlong(w);
+        return b < 0 && (b << 1) != 0;
+    }
+    // negative values and -0 become +0
+    static __device__ __forceinline__ double nonneg(double x) { return __double_as_longlong(x) < 0 ? 0.0 : x; }
+    static __device__ __forceinline__ bool le(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
+    static __device__ __forceinline__ bool lt(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+    static __device__ __forceinline__ bool eq(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
     static __device__ __forceinline__ double sigma(const CaseParams &c, int m) { return c.sigma[m]; }
-    static __device__ __forceinline__ double cscat(const CaseParams &c, int m) { return c.c[m]; }
+    static __device__ __forceinline__ unsigned long long thr_c53(const CaseParams &c, int m) { return c.thr_c53[m]; }
+    static __device__ __forceinline__ uint32_t thr_c24(const CaseParams &c, int m) { return c.thr_c24[m]; }
     static __device__ __forceinline__ double L(const CaseParams &c) { return c.L; }
-    static __device__ __forceinline__ double p0(const CaseParams &c) { return c.p0; }
     static __device__ __forceinline__ double dx(const CaseParams &c) { return c.dx; }
     static __device__ __forceinline__ double inv_dx(const CaseParams &c) { return c.inv_dx; }
     // l_c = -ln(1 - u) / Sigma_m, as -ln(1 - u) * (1 / Sigma_m)
-    static __device__ __forceinline__ double collision(const CaseParams &c, int m, double u) {
-        return -log(1.0 - u) * c.inv_sigma[m];
+    static __device__ __forceinline__ double collision(const CaseParams &c, int m, double one_minus_u) {
+        return -log(one_minus_u) * c.inv_sigma[m];
     }
-    static __device__ __forceinline__ double interface(const CaseParams &c, int m, double u) {
-        return -c.lambda[m] * log(1.0 - u);
+    static __device__ __forceinline__ double interface(const CaseParams &c, int m, double one_minus_u) {
+        return -c.lambda[m] * log(one_minus_u);
     }
     static __device__ __forceinline__ double recip(double a) { return 1.0 / a; }
     // (sin, cos) of 2 pi u
-    static __device__ __forceinline__ void sincos_2pi(double u, double *s, double *co) {
-        const double ph = (2.0 * 3.14159265358979323846) * u;
-        sincos(ph, s, co);
-    }
+    static __device__ __forceinline__ void sincos_2pi(double u, double *s, double *co) { sincospi(2.0 * u, s, co); }
 };
 
 // FP32 tracking: position, direction and distances in float; shared-memory
@@ -85,27 +105,35 @@ struct Real<double> {
 template <>
 struct Real<float> {
     using Bin = float;
-    // the same draw truncated to its top 24 bits
-    static __device__ __forceinline__ float uniform(uint32_t hi, uint32_t) {
-        return (float)(hi >> 8) * 0x1p-24f;
+    // the same draw truncated to its top 24 bits: u = k 2^-24
+    static __device__ __forceinline__ float uniform(uint32_t hi, uint32_t) { return (float)(hi >> 8) * 0x1p-24f; }
+    static __device__ __forceinline__ float one_minus(uint32_t hi, uint32_t) {
+        return (float)((1u << 24) - (hi >> 8)) * 0x1p-24f;
+    }
+    static __device__ __forceinline__ bool below(uint32_t hi, uint32_t, unsigned long long, uint32_t thr24) {
+        return (hi >> 8) < thr24;
     }
     static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+    static __device__ __forceinline__ bool pos(float w) { return w > 0.0f; }
+    static __device__ __forceinline__ bool neg(float w) { return w < 0.0f; }
+    static __device__ __forceinline__ float nonneg(float x) { return x > 0.0f ? x : 0.0f; }
+    static __device__ __forceinline__ bool le(float a, float b) { return a <= b; }
+    static __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
+    static __device__ __forceinline__ bool eq(float a, float b) { return a == b; }
     static __device__ __forceinline__ float sigma(const CaseParams &c, int m) { return c.sigma_f[m]; }
-    static __device__ __forceinline__ float cscat(const CaseParams &c, int m) { return c.c_f[m]; }
+    static __device__ __forceinline__ unsigned long long thr_c53(const CaseParams &c, int m) { return c.thr_c53[m]; }
+    static __device__ __forceinline__ uint32_t thr_c24(const CaseParams &c, int m) { return c.thr_c24[m]; }
     static __device__ __forceinline__ float L(const CaseParams &c) { return c.L_f; }
-    static __device__ __forceinline__ float p0(const CaseParams &c) { return c.p0_f; }
     static __device__ __forceinline__ float dx(const CaseParams &c) { return c.dx_f; }
     static __device__ __forceinline__ float inv_dx(const CaseParams &c) { return c.inv_dx_f; }
-    static __device__ __forceinline__ float collision(const CaseParams &c, int m, float u) {
-        return -__logf(1.0f - u) * c.inv_sigma_f[m];
+    static __device__ __forceinline__ float collision(const CaseParams &c, int m, float one_minus_u) {
+        return -__logf(one_minus_u) * c.inv_sigma_f[m];
     }
-    static __device__ __forceinline__ float interface(const CaseParams &c, int m, float u) {
-        return -c.lambda_f[m] * __logf(1.0f - u);
+    static __device__ __forceinline__ float interface(const CaseParams &c, int m, float one_minus_u) {
+        return -c.lambda_f[m] * __logf(one_minus_u);
     }
     static __device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
-    static __device__ __forceinline__ void sincos_2pi(float u, float *s, float *co) {
-        sincospif(2.0f * u, s, co);
-    }
+    static __device__ __forceinline__ void sincos_2pi(float u, float *s, float *co) { sincospif(2.0f * u, s, co); }
 };
 
 // ----------------------------------------------------------- history state
@@ -130,9 +158,10 @@ struct Flight {
     P a0, a1, c;
 };
 
+// Output words (hi, lo) of draw j = s.j of the history; advances j.  Even
+// draws compute a Philox block and keep its words 2, 3 for the odd draw.
 template <typename P>
-__device__ __forceinline__ P draw(History<P> &s, uint2 key) {
-    uint32_t hi, lo;
+__device__ __forceinline__ void draw_words(History<P> &s, uint2 key, uint32_t &hi, uint32_t &lo) {
     if ((s.j & 1u) == 0u) {
         const uint4 o = philox4x32_10(make_uint4(s.j >> 1, s.h_lo, s.h_hi, s.cid), key);
         hi = o.x;
@@ -144,7 +173,29 @@ __device__ __forceinline__ P draw(History<P> &s, uint2 key) {
         lo = s.c3;
     }
     ++s.j;
+}
+
+template <typename P>
+__device__ __forceinline__ P draw(History<P> &s, uint2 key) {
+    uint32_t hi, lo;
+    draw_words(s, key, hi, lo);
     return Real<P>::uniform(hi, lo);
+}
+
+// 1 - u of the next draw, exactly
+template <typename P>
+__device__ __forceinline__ P draw_one_minus(History<P> &s, uint2 key) {
+    uint32_t hi, lo;
+    draw_words(s, key, hi, lo);
+    return Real<P>::one_minus(hi, lo);
+}
+
+// whether the next draw is below the value whose thresholds are given
+template <typename P>
+__device__ __forceinline__ bool draw_below(History<P> &s, uint2 key, unsigned long long thr53, uint32_t thr24) {
+    uint32_t hi, lo;
+    draw_words(s, key, hi, lo);
+    return Real<P>::below(hi, lo, thr53, thr24);
 }
 
 __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
@@ -192,7 +243,7 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint
         s.iw[1] = R::inf();
         s.iw[2] = R::inf();
     }
-    s.m = (draw(s, key) < R::p0(cp)) ? 0 : 1;
+    s.m = draw_below(s, key, cp.thr_p053, cp.thr_p024) ? 0 : 1;
 }
 
 // Trace sink (only instantiated by the trace kernel).
@@ -224,8 +275,9 @@ __device__ __forceinline__ void trace_row(TraceSink *tr, int ev, const History<P
 
 // Track-length estimator: the flight x0 -> x1 (length l, direction cosine wx)
 // scores in bin k the path length inside e_k <= x < e_k+1, the x-overlap times
-// 1/|wx|.  Interior bins receive dx/|wx| each.  A flight with wx == 0 scores
-// its whole length in the bin that contains x0.
+// 1/|wx|; interior bins receive dx/|wx| each.  A flight inside one bin scores
+// its length l itself, which stays exact for grazing flights (|wx| -> 0).  A
+// flight with wx == 0 scores its whole length in the bin that contains x0.
 template <typename P>
 __device__ __forceinline__ void plan_flight(Flight<P> &f, History<P> &s, const CaseParams &cp, P x0, P x1, P l,
                                             int m) {
@@ -252,8 +304,8 @@ __device__ __forceinline__ void plan_flight(Flight<P> &f, History<P> &s, const C
     const int k1 = min(max((int)floor(hi * inv_dx), 0), nb - 1);
     f.k0 = k0;
     f.k1 = k1;
-    if (k0 == k1) {
-        f.a0 = fmax(hi - lo, P(0)) * iaw;
+    if (k0 == k1) {  // the flight lies inside one bin: its length itself
+        f.a0 = l;
         return;
     }
     const P dx = R::dx(cp);
@@ -281,41 +333,39 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
     const P L = R::L(cp);
 
     // collision, then interface distance
-    const P u_c = draw(s, key);
-    const P l_c = (R::sigma(cp, m) > P(0)) ? R::collision(cp, m, u_c) : INF;
-    const P u_i = draw(s, key);
-    const P l_i = R::interface(cp, m, u_i);
+    const P om_c = draw_one_minus(s, key);
+    const P l_c = (R::sigma(cp, m) > P(0)) ? R::nonneg(R::collision(cp, m, om_c)) : INF;
+    const P om_i = draw_one_minus(s, key);
+    const P l_i = R::nonneg(R::interface(cp, m, om_i));
 
     // boundary distance: x faces, then the lateral faces of the box
     P l_b = INF;
     int face = -1;  // 0: x = 0, 1: x = L, 2: lateral
-    if (s.w[0] > P(0)) {
+    if (R::pos(s.w[0])) {
         l_b = (L - s.r[0]) * s.iw[0];
         face = 1;
-    } else if (s.w[0] < P(0)) {
+    } else if (R::neg(s.w[0])) {
         l_b = (P(0) - s.r[0]) * s.iw[0];
         face = 0;
     }
-    if (l_b < P(0)) l_b = P(0);
+    l_b = R::nonneg(l_b);
     P l_y = INF, l_z = INF;
     if (cp.d == 3) {
-        if (s.w[1] > P(0)) l_y = (L - s.r[1]) * s.iw[1];
-        else if (s.w[1] < P(0)) l_y = (P(0) - s.r[1]) * s.iw[1];
-        if (l_y < P(0)) l_y = P(0);
-        if (l_y < l_b) {
+        if (R::pos(s.w[1])) l_y = R::nonneg((L - s.r[1]) * s.iw[1]);
+        else if (R::neg(s.w[1])) l_y = R::nonneg((P(0) - s.r[1]) * s.iw[1]);
+        if (R::lt(l_y, l_b)) {
             l_b = l_y;
             face = 2;
         }
-        if (s.w[2] > P(0)) l_z = (L - s.r[2]) * s.iw[2];
-        else if (s.w[2] < P(0)) l_z = (P(0) - s.r[2]) * s.iw[2];
-        if (l_z < P(0)) l_z = P(0);
-        if (l_z < l_b) {
+        if (R::pos(s.w[2])) l_z = R::nonneg((L - s.r[2]) * s.iw[2]);
+        else if (R::neg(s.w[2])) l_z = R::nonneg((P(0) - s.r[2]) * s.iw[2]);
+        if (R::lt(l_z, l_b)) {
             l_b = l_z;
             face = 2;
         }
     }
 
-    if (l_b <= l_c && l_b <= l_i) {
+    if (R::le(l_b, l_c) && R::le(l_b, l_i)) {
         if (face != 2) {
             const P xf = (face == 0) ? P(0) : L;
             plan_flight(f, s, cp, s.r[0], xf, l_b, m);
@@ -331,15 +381,15 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
         const P x1 = s.r[0] + l_b * s.w[0];
         plan_flight(f, s, cp, s.r[0], x1, l_b, m);
         s.r[0] = x1;
-        if (l_y == l_b) {
-            s.r[1] = (s.w[1] > P(0)) ? L : P(0);
+        if (R::eq(l_y, l_b)) {
+            s.r[1] = R::pos(s.w[1]) ? L : P(0);
             s.w[1] = -s.w[1];
             s.iw[1] = -s.iw[1];
         } else {
             s.r[1] += l_b * s.w[1];
         }
-        if (l_z == l_b) {
-            s.r[2] = (s.w[2] > P(0)) ? L : P(0);
+        if (R::eq(l_z, l_b)) {
+            s.r[2] = R::pos(s.w[2]) ? L : P(0);
             s.w[2] = -s.w[2];
             s.iw[2] = -s.iw[2];
         } else {
@@ -350,7 +400,8 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
         return -1;
     }
 
-    const P l = (l_c <= l_i) ? l_c : l_i;
+    const bool coll = R::le(l_c, l_i);
+    const P l = coll ? l_c : l_i;
     const P x1 = s.r[0] + l * s.w[0];
     plan_flight(f, s, cp, s.r[0], x1, l, m);
     s.r[0] = x1;
@@ -358,11 +409,14 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
         s.r[1] += l * s.w[1];
         s.r[2] += l * s.w[2];
     }
-    if (l_c <= l_i) {
+    if (coll) {
         ++s.n_coll;
-        if (draw(s, key) < R::cscat(cp, m)) {
+        if (draw_below(s, key, R::thr_c53(cp, m), R::thr_c24(cp, m))) {
             if (cp.d == 1) {
-                const P w = (draw(s, key) < P(0.5)) ? P(1) : P(-1);
+                // u < 1/2 exactly when the top bit of the draw is clear
+                uint32_t hi, lo;
+                draw_words(s, key, hi, lo);
+                const P w = (hi >> 31) == 0u ? P(1) : P(-1);
                 s.w[0] = w;
                 s.iw[0] = w;
             } else {
@@ -510,8 +564,19 @@ __device__ __forceinline__ int find_run(const LaunchArgs &a, uint64_t ch) {
 // across history and chunk boundaries.  Each warp owns two shared-memory tally
 // regions keyed by (case, batch); a region is flushed to global memory when
 // its key changes, after flush_every histories, or when the warp retires.
+// Blocks per SM the register allocation must allow: FP64 is bound by the FP64
+// pipe, FP32 by issue and latency, which more resident warps help hide.
 template <typename P>
-__global__ void __launch_bounds__(256) history_kernel(const LaunchArgs a) {
+struct MinBlocks {
+    static constexpr int value = 1;
+};
+template <>
+struct MinBlocks<float> {
+    static constexpr int value = 4;
+};
+
+template <typename P>
+__global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;

@@ -1,6 +1,6 @@
-// cls_fp64.cu -- double instantiations of the CLS kernels.
-// Built with --fmad=false: FP64 arithmetic is rounded operation by operation,
-// as the CPU oracle does, so the walk is draw-for-draw identical to it.
+// cls_fp64.cu -- double instantiations of the CLS kernels.  The FP64 walk makes
+// the oracle's decisions draw for draw; its positions and distances agree with
+// the oracle's to rounding (fused multiply-adds, reciprocals).
 #include "cls_device.cuh"
 #include "cls_event.cuh"
 

@@ -7,6 +7,10 @@
 // combined_var usage: per-history for R, T, A and <phi>, batch means for phi(x)).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -46,6 +50,7 @@ struct cls_handle {
     int device = 0;
     int sm_count = 0;
     bool batch = false;
+    std::vector<double> params;  // ncases x 9, as created
     Options opt;
     int used_blocks_per_sm = 0;
     std::vector<CaseParams> cases;
@@ -144,6 +149,12 @@ CaseParams make_case(const double *p, uint32_t case_id) {
     c.dx_f = (float)c.dx;
     c.inv_dx_f = (float)c.inv_dx;
     c.case_id = case_id;
+    for (int i = 0; i < 2; ++i) {
+        c.thr_c53[i] = unit_threshold(c.c[i], 53);
+        c.thr_c24[i] = (uint32_t)unit_threshold((double)c.c_f[i], 24);
+    }
+    c.thr_p053 = unit_threshold(c.p0, 53);
+    c.thr_p024 = (uint32_t)unit_threshold((double)c.p0_f, 24);
     c.cost = cost_estimate(c);
     return c;
 }
@@ -207,6 +218,7 @@ int create_common(const double *params, int ncases, bool batch, cls_handle **out
     cls_handle *h = new (std::nothrow) cls_handle();
     if (!h) return CLS_E_NOMEM;
     h->batch = batch;
+    h->params.assign(params, params + 9 * (size_t)ncases);
     if (cudaGetDevice(&h->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
         delete h;
@@ -478,9 +490,140 @@ int tallies_of(cls_handle *h, int k, cls_tallies_t *out) {
     return ct[C_CAPPED] ? CLS_E_EVENT_LIMIT : CLS_OK;
 }
 
+// ------------------------------------------------------------- autotuner
+struct Tuned {
+    int schedule, block, chunk, events_per_pass;
+};
+
+std::mutex g_tune_mutex;
+std::map<std::string, Tuned> g_tune_cache;
+bool g_tune_file_read = false;
+
+// FNV-1a over (precision, nbatch, case parameters): identifies a tuning problem.
+std::string tune_signature(const cls_handle *h) {
+    unsigned long long x = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t n) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) {
+            x ^= c[i];
+            x *= 1099511628211ull;
+        }
+    };
+    mix(&h->opt.precision, sizeof(int));
+    mix(h->params.data(), h->params.size() * sizeof(double));
+    char buf[64];
+    std::snprintf(buf, sizeof(buf), "p%d-n%zu-%016llx", h->opt.precision, h->params.size() / 9, x);
+    return buf;
+}
+
+void tune_file_load() {
+    if (g_tune_file_read) return;
+    g_tune_file_read = true;
+    const char *path = std::getenv("CLS_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char key[128];
+    Tuned t;
+    while (std::fscanf(f, "%127s %d %d %d %d", key, &t.schedule, &t.block, &t.chunk, &t.events_per_pass) == 5)
+        g_tune_cache[key] = t;
+    std::fclose(f);
+}
+
+void tune_file_append(const std::string &key, const Tuned &t) {
+    const char *path = std::getenv("CLS_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.schedule, t.block, t.chunk, t.events_per_pass);
+    std::fclose(f);
+}
+
+void apply_tuned(cls_handle *h, const Tuned &t) {
+    h->opt.schedule = t.schedule;
+    h->opt.block = t.block;
+    h->opt.chunk = t.chunk;
+    h->opt.events_per_pass = t.events_per_pass;
+    destroy_graph(h);
+}
+
 }  // namespace
 
 extern "C" {
+
+int cls_autotune(cls_handle *h, uint64_t n_pilot, uint64_t seed, void *stream) {
+    if (!h || n_pilot == 0 || n_pilot > (1ull << 32)) return CLS_E_INVAL;
+    CLS_CUDA(cudaSetDevice(h->device));
+    const std::string key = tune_signature(h);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        tune_file_load();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            apply_tuned(h, it->second);
+            return CLS_OK;
+        }
+    }
+    const int ncases = (int)h->cases.size();
+    cls_handle *t = nullptr;
+    int rc = create_common(h->params.data(), ncases, h->batch, &t);
+    if (rc) return rc;
+    t->opt = h->opt;
+    std::vector<Tuned> cand;
+    for (int b : {64, 128, 256})
+        for (int c : {64, 256, 1024}) cand.push_back({CLS_SCHED_HISTORY, b, c, h->opt.events_per_pass});
+    for (int b : {128, 256})
+        for (int e : {4, 16}) cand.push_back({CLS_SCHED_EVENT, b, h->opt.chunk, e});
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cls_destroy(t);
+        return CLS_E_CUDA;
+    }
+    float best_ms = 0.f;
+    Tuned best = cand[0];
+    bool have = false;
+    const uint64_t base = 1ull << 61;  // pilot history ids, far from a caller's
+    for (size_t i = 0; i < cand.size() && !rc; ++i) {
+        apply_tuned(t, cand[i]);
+        t->opt.max_events = h->opt.max_events;
+        // warm-up (module load, bank allocation, graph capture), then one timed run
+        for (int rep = 0; rep < 2 && !rc; ++rep) {
+            for (auto &nh : t->next_history) nh = base + (uint64_t)(2 * i + rep) * n_pilot;
+            if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) rc = CLS_E_CUDA;
+            if (!rc) rc = t->batch ? cls_batch_run(t, rep ? n_pilot : std::max<uint64_t>(n_pilot / 4, 1), seed, stream)
+                                   : cls_run(t, rep ? n_pilot : std::max<uint64_t>(n_pilot / 4, 1), seed, stream);
+            if (!rc && rep == 1 && cudaEventRecord(e1, s) != cudaSuccess) rc = CLS_E_CUDA;
+        }
+        if (rc) {
+            // a candidate that does not fit (e.g. shared memory) is skipped
+            if (rc == CLS_E_INVAL || rc == CLS_E_NOMEM) rc = CLS_OK;
+            continue;
+        }
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = CLS_E_CUDA;
+            break;
+        }
+        if (!have || ms < best_ms) {
+            best_ms = ms;
+            best = cand[i];
+            have = true;
+        }
+        zero_tallies(t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cls_destroy(t);
+    if (rc) return rc;
+    if (!have) return CLS_E_INVAL;
+    apply_tuned(h, best);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = best;
+    tune_file_append(key, best);
+    return CLS_OK;
+}
+
 
 int cls_create(double sigma0, double sigma1, double lambda0, double lambda1, double c0, double c1, double L,
                int d, int nbins, cls_handle **out) {
@@ -503,7 +646,7 @@ int cls_set_option(cls_handle *h, int key, int64_t v) {
         o.precision = (int)v;
         break;
     case CLS_OPT_SCHEDULE:
-        if (v != CLS_SCHED_HISTORY && v != CLS_SCHED_EVENT) return CLS_E_INVAL;
+        if (v != CLS_SCHED_HISTORY && v != CLS_SCHED_EVENT && v != CLS_SCHED_AUTO) return CLS_E_INVAL;
         o.schedule = (int)v;
         break;
     case CLS_OPT_BLOCK:
@@ -578,6 +721,11 @@ int cls_get_option(const cls_handle *h, int key, int64_t *v) {
 int cls_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
     if (!h || n == 0 || n > (1ull << 62)) return CLS_E_INVAL;
     CLS_CUDA(cudaSetDevice(h->device));
+    if (h->opt.schedule == CLS_SCHED_AUTO) {
+        int arc = cls_autotune(h, std::min<uint64_t>(std::max<uint64_t>(n / 16, 4096), 262144), seed ^ 0x5bd1e995ull,
+                               stream);
+        if (arc) return arc;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     LaunchArgs a;
     int rc = prepare_run(h, n, seed, &a);
@@ -603,6 +751,11 @@ int cls_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
 int cls_batch_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
     if (!h || n == 0 || n > (1ull << 62)) return CLS_E_INVAL;
     CLS_CUDA(cudaSetDevice(h->device));
+    if (h->opt.schedule == CLS_SCHED_AUTO) {
+        int arc = cls_autotune(h, std::min<uint64_t>(std::max<uint64_t>(n / 16, 4096), 262144), seed ^ 0x5bd1e995ull,
+                               stream);
+        if (arc) return arc;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     LaunchArgs a;
     int rc = prepare_run(h, n, seed, &a);

@@ -22,6 +22,12 @@ struct CaseParams {
     float lambda_f[2];
     float c_f[2];
     float L_f, p0_f, dx_f, inv_dx_f;
+    // integer thresholds: a draw u = k 2^-53 (FP64) or k 2^-24 (FP32) is below
+    // c_i or p_0 exactly when k is below ceil(c_i 2^53) (resp. 2^24)
+    unsigned long long thr_c53[2];
+    unsigned long long thr_p053;
+    uint32_t thr_c24[2];
+    uint32_t thr_p024;
     int32_t d;      // 1 rod, 3 box
     int32_t nbins;
     uint32_t case_id;  // Philox counter word 3
@@ -96,6 +102,13 @@ struct TraceArgs {
 __host__ __device__ inline int region_bins_bytes(int bin_size, int nbins_stride) { return (nbins_stride * bin_size + 7) & ~7; }
 __host__ __device__ inline int region_bytes(int bin_size, int nbins_stride) {
     return (region_bins_bytes(bin_size, nbins_stride) + 8 * (S_NUM + C_NUM) + 15) & ~15;
+}
+
+// ceil(v 2^bits) for v in [0, 1], exact (scaling by a power of two is exact).
+inline unsigned long long unit_threshold(double v, int bits) {
+    const double scaled = v * (double)(1ull << bits);
+    const double c = (scaled == (double)(unsigned long long)scaled) ? scaled : (double)(unsigned long long)scaled + 1.0;
+    return (unsigned long long)c;
 }
 
 // Launchers, one set per precision translation unit.

@@ -125,6 +125,12 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
         c.dx_f = (float)c.dx;
         c.inv_dx_f = (float)c.inv_dx;
         c.case_id = (uint32_t)k;
+        for (int i = 0; i < 2; ++i) {
+            c.thr_c53[i] = unit_threshold(c.c[i], 53);
+            c.thr_c24[i] = (uint32_t)unit_threshold((double)c.c_f[i], 24);
+        }
+        c.thr_p053 = unit_threshold(c.p0, 53);
+        c.thr_p024 = (uint32_t)unit_threshold((double)c.p0_f, 24);
         RunCase &r = host.runs[k];
         r.first = first;
         r.n = n;

