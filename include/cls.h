@@ -144,6 +144,16 @@ int cls_tallies(cls_handle *h, cls_tallies_t *out);
 int cls_raw_tallies(cls_handle *h, int case_idx, cls_raw_t *out, double *flux_batches,
                     uint64_t *batch_histories);
 
+/* Normalise raw accumulators on the host, exactly as cls_tallies does: for
+ * merging runs made on several devices or processes, sum their cls_raw_t
+ * fields (max_events: maximum), their flux_batches and their batch_histories,
+ * then call this.  flux_batches: [raw->nbatch][raw->nbins]; batch_histories:
+ * [raw->nbatch]; L: the case's length.  Needs no GPU.
+ * Errors: CLS_E_INVAL (no histories, bad sizes), CLS_E_EVENT_LIMIT (out is
+ * filled; some histories were capped). */
+int cls_finalize_raw(const cls_raw_t *raw, const double *flux_batches, const uint64_t *batch_histories, double L,
+                     cls_tallies_t *out);
+
 /* Zero the tallies and restart history numbering at 0 (synchronous). */
 int cls_reset(cls_handle *h);
 

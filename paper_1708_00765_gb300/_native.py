@@ -40,7 +40,7 @@ CLS_SCHED_EVENT = 2
 # every symbol include/cls.h declares
 EXPORTED = ("cls_create", "cls_set_option", "cls_get_option", "cls_run", "cls_tallies", "cls_raw_tallies",
             "cls_reset", "cls_destroy", "cls_strerror", "cls_trace", "cls_batch_create", "cls_batch_run",
-            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_run_noalloc", "cls_autotune")
+            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_run_noalloc", "cls_autotune", "cls_finalize_raw")
 
 CLS_NOALLOC_MAX_CASES = 64
 
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "cls_debug_uniform": ([u64, u32, P(u64), P(u64), i, P(d), P(ctypes.c_float)], i),
         "cls_run_noalloc": ([P(d), i, u64, u64, u64, i, i, H, H, H, H], i),
         "cls_autotune": ([H, u64, u64, H], i),
+        "cls_finalize_raw": ([P(cls_raw_t), P(d), P(u64), d, P(cls_tallies_t)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -279,3 +280,30 @@ def run_noalloc(params, first: int, n: int, seed: int, nbatch: int, nbins_stride
     params = np.ascontiguousarray(np.atleast_2d(np.asarray(params, dtype=np.float64)))
     return load().cls_run_noalloc(_ptr(params), params.shape[0], first, n, seed, nbatch, nbins_stride, d_flux,
                                   d_stats, d_counters, _stream_handle(stream))
+
+
+RAW_COUNT_KEYS = ("n_histories", "nR", "nT", "nA", "n_coll", "n_interface", "n_reflect", "n_events", "max_events",
+                  "n_capped")
+
+
+def finalize_raw(raw: dict, L: float) -> dict:
+    """cls_finalize_raw: normalise (possibly merged) raw tallies on the host."""
+    r = cls_raw_t()
+    for k in RAW_COUNT_KEYS:
+        setattr(r, k, int(raw[k]))
+    r.sum_t, r.sum_t2 = float(raw["sum_t"]), float(raw["sum_t2"])
+    r.track[0], r.track[1] = float(raw["track"][0]), float(raw["track"][1])
+    flux = np.ascontiguousarray(raw["flux"], dtype=np.float64)
+    r.nbatch, r.nbins = flux.shape
+    bh = np.ascontiguousarray(raw["batch_histories"], dtype=np.uint64)
+    out_flux = np.zeros(r.nbins)
+    out_sig = np.zeros(r.nbins)
+    t = cls_tallies_t()
+    t.flux = _ptr(out_flux)
+    t.flux_sigma = _ptr(out_sig)
+    rc = load().cls_finalize_raw(ctypes.byref(r), _ptr(flux), _ptr(bh, ctypes.c_uint64), float(L), ctypes.byref(t))
+    _check(rc, "cls_finalize_raw", ok=(CLS_OK, CLS_E_EVENT_LIMIT))
+    out = {n: getattr(t, n) for n, _ in cls_tallies_t._fields_ if n not in ("flux", "flux_sigma")}
+    out["flux"] = out_flux
+    out["flux_sigma"] = out_sig
+    return out

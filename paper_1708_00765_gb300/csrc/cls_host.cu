@@ -425,17 +425,66 @@ int fetch_case(cls_handle *h, int k, std::vector<double> &flux, double stats[S_N
     return CLS_OK;
 }
 
-int tallies_of(cls_handle *h, int k, cls_tallies_t *out) {
-    if (!h || !out || k < 0 || k >= (int)h->cases.size()) return CLS_E_INVAL;
-    int rc = sync_and_time(h);
-    if (rc) return rc;
-    std::vector<double> flux;
-    double st[S_NUM];
-    unsigned long long ct[C_NUM];
-    rc = fetch_case(h, k, flux, st, ct);
-    if (rc) return rc;
-    const CaseParams &cp = h->cases[k];
-    const double N = (double)h->n_hist[k];
+// FP64 normalisation of raw accumulators (paper Sec. 2 observables):
+// R, T, A per-history Bernoulli means with sqrt(p(1-p)/(N-1)); <phi> the mean
+// track length with its per-history standard error; phi_k = sum_b flux[b][k] /
+// (N dx) with the batch-means error B/(B-1) sum_b (n_b/N)^2 (X_b - X)^2.
+int finalize_raw(const cls_raw_t &raw, const double *flux, int flux_stride, const uint64_t *bh, double L,
+                 cls_tallies_t *out) {
+    const double N = (double)raw.n_histories;
+    if (!(N > 0) || raw.nbins < 1 || raw.nbatch < 1 || !(L > 0)) return CLS_E_INVAL;
+    out->n_histories = raw.n_histories;
+    out->nR = raw.nR;
+    out->nT = raw.nT;
+    out->nA = raw.nA;
+    out->n_coll = raw.n_coll;
+    out->n_interface = raw.n_interface;
+    out->n_reflect = raw.n_reflect;
+    out->n_events = raw.n_events;
+    out->max_events = raw.max_events;
+    out->n_capped = raw.n_capped;
+    auto bern = [&](uint64_t c, double *p, double *sd) {
+        *p = (double)c / N;
+        *sd = N > 1 ? std::sqrt(*p * (1.0 - *p) / (N - 1.0)) : NAN;
+    };
+    bern(raw.nR, &out->R, &out->sigma_R);
+    bern(raw.nT, &out->T, &out->sigma_T);
+    bern(raw.nA, &out->A, &out->sigma_A);
+    const double mean = raw.sum_t / N;
+    out->total_flux = mean;
+    const double var = std::max(raw.sum_t2 / N - mean * mean, 0.0);
+    out->sigma_total_flux = N > 1 ? std::sqrt(var / (N - 1.0)) : NAN;
+    out->track0 = raw.track[0] / N;
+    out->track1 = raw.track[1] / N;
+    const int nb = raw.nbins;
+    const double dx = L / nb;
+    int B = 0;
+    for (int b = 0; b < raw.nbatch; ++b) B += bh[b] > 0;
+    for (int j = 0; j < nb; ++j) {
+        double tot = 0.0;
+        for (int b = 0; b < raw.nbatch; ++b) tot += flux[(size_t)b * flux_stride + j];
+        const double phi = tot / (N * dx);
+        if (out->flux) out->flux[j] = phi;
+        if (out->flux_sigma) {
+            if (B < 2) {
+                out->flux_sigma[j] = NAN;
+                continue;
+            }
+            double acc = 0.0;
+            for (int b = 0; b < raw.nbatch; ++b) {
+                if (!bh[b]) continue;
+                const double nbh = (double)bh[b];
+                const double xb = flux[(size_t)b * flux_stride + j] / (nbh * dx);
+                const double wgt = nbh / N;
+                acc += wgt * wgt * (xb - phi) * (xb - phi);
+            }
+            out->flux_sigma[j] = std::sqrt(acc * B / (B - 1.0));
+        }
+    }
+    return raw.n_capped ? CLS_E_EVENT_LIMIT : CLS_OK;
+}
+
+void raw_of(const cls_handle *h, int k, const double st[S_NUM], const unsigned long long ct[C_NUM], cls_raw_t *out) {
     out->n_histories = h->n_hist[k];
     out->nR = ct[C_R];
     out->nT = ct[C_T];
@@ -446,48 +495,28 @@ int tallies_of(cls_handle *h, int k, cls_tallies_t *out) {
     out->n_events = ct[C_EVENTS];
     out->max_events = ct[C_MAXEV];
     out->n_capped = ct[C_CAPPED];
-    auto bern = [&](unsigned long long c, double *p, double *sd) {
-        *p = c / N;
-        *sd = N > 1 ? std::sqrt(*p * (1.0 - *p) / (N - 1.0)) : NAN;
-    };
-    bern(ct[C_R], &out->R, &out->sigma_R);
-    bern(ct[C_T], &out->T, &out->sigma_T);
-    bern(ct[C_A], &out->A, &out->sigma_A);
-    const double mean = st[S_T] / N;
-    out->total_flux = mean;
-    const double var = std::max(st[S_T2] / N - mean * mean, 0.0);
-    out->sigma_total_flux = N > 1 ? std::sqrt(var / (N - 1.0)) : NAN;
-    out->track0 = st[S_TRACK0] / N;
-    out->track1 = st[S_TRACK1] / N;
+    out->sum_t = st[S_T];
+    out->sum_t2 = st[S_T2];
+    out->track[0] = st[S_TRACK0];
+    out->track[1] = st[S_TRACK1];
+    out->nbins = h->cases[k].nbins;
+    out->nbatch = h->nbatch;
+}
+
+int tallies_of(cls_handle *h, int k, cls_tallies_t *out) {
+    if (!h || !out || k < 0 || k >= (int)h->cases.size()) return CLS_E_INVAL;
+    int rc = sync_and_time(h);
+    if (rc) return rc;
+    std::vector<double> flux;
+    double st[S_NUM];
+    unsigned long long ct[C_NUM];
+    rc = fetch_case(h, k, flux, st, ct);
+    if (rc) return rc;
+    cls_raw_t raw;
+    raw_of(h, k, st, ct, &raw);
+    rc = finalize_raw(raw, flux.data(), h->nbins_stride, h->batch_hist[k].data(), h->cases[k].L, out);
     out->seconds = h->seconds;
-    // phi_k = sum_b flux[b][k] / (N dx); sigma from batch means weighted by batch size:
-    // var = B/(B-1) sum_b (n_b/N)^2 (X_b - X)^2 over the B non-empty batches
-    const int nb = cp.nbins;
-    const std::vector<uint64_t> &bh = h->batch_hist[k];
-    int B = 0;
-    for (int b = 0; b < h->nbatch; ++b) B += bh[b] > 0;
-    for (int j = 0; j < nb; ++j) {
-        double tot = 0.0;
-        for (int b = 0; b < h->nbatch; ++b) tot += flux[(size_t)b * h->nbins_stride + j];
-        const double phi = tot / (N * cp.dx);
-        if (out->flux) out->flux[j] = phi;
-        if (out->flux_sigma) {
-            if (B < 2) {
-                out->flux_sigma[j] = NAN;
-                continue;
-            }
-            double acc = 0.0;
-            for (int b = 0; b < h->nbatch; ++b) {
-                if (!bh[b]) continue;
-                const double nbh = (double)bh[b];
-                const double xb = flux[(size_t)b * h->nbins_stride + j] / (nbh * cp.dx);
-                const double wgt = nbh / N;
-                acc += wgt * wgt * (xb - phi) * (xb - phi);
-            }
-            out->flux_sigma[j] = std::sqrt(acc * B / (B - 1.0));
-        }
-    }
-    return ct[C_CAPPED] ? CLS_E_EVENT_LIMIT : CLS_OK;
+    return rc;
 }
 
 // ------------------------------------------------------------- autotuner
@@ -815,22 +844,7 @@ int cls_raw_tallies(cls_handle *h, int k, cls_raw_t *out, double *flux_batches, 
     unsigned long long ct[C_NUM];
     rc = fetch_case(h, k, flux, st, ct);
     if (rc) return rc;
-    out->n_histories = h->n_hist[k];
-    out->nR = ct[C_R];
-    out->nT = ct[C_T];
-    out->nA = ct[C_A];
-    out->n_coll = ct[C_COLL];
-    out->n_interface = ct[C_INT];
-    out->n_reflect = ct[C_REFL];
-    out->n_events = ct[C_EVENTS];
-    out->max_events = ct[C_MAXEV];
-    out->n_capped = ct[C_CAPPED];
-    out->sum_t = st[S_T];
-    out->sum_t2 = st[S_T2];
-    out->track[0] = st[S_TRACK0];
-    out->track[1] = st[S_TRACK1];
-    out->nbins = h->cases[k].nbins;
-    out->nbatch = h->nbatch;
+    raw_of(h, k, st, ct, out);
     if (flux_batches)
         for (int b = 0; b < h->nbatch; ++b)
             std::memcpy(flux_batches + (size_t)b * out->nbins, flux.data() + (size_t)b * h->nbins_stride,
@@ -838,6 +852,14 @@ int cls_raw_tallies(cls_handle *h, int k, cls_raw_t *out, double *flux_batches, 
     if (batch_histories)
         for (int b = 0; b < h->nbatch; ++b) batch_histories[b] = h->batch_hist[k][b];
     return CLS_OK;
+}
+
+int cls_finalize_raw(const cls_raw_t *raw, const double *flux_batches, const uint64_t *batch_histories, double L,
+                     cls_tallies_t *out) {
+    if (!raw || !flux_batches || !batch_histories || !out) return CLS_E_INVAL;
+    const int rc = finalize_raw(*raw, flux_batches, raw->nbins, batch_histories, L, out);
+    out->seconds = 0.0;
+    return rc;
 }
 
 int cls_reset(cls_handle *h) {
