@@ -568,7 +568,7 @@ __device__ __forceinline__ int find_run(const LaunchArgs &a, uint64_t ch) {
 // pipe, FP32 by issue and latency, which more resident warps help hide.
 template <typename P>
 struct MinBlocks {
-    static constexpr int value = 1;
+    static constexpr int value = 2;
 };
 template <>
 struct MinBlocks<float> {

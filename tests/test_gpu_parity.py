@@ -324,3 +324,38 @@ def test_autotune_file_cache(tmp_path):
     assert len(lines) == 1  # the second process found the first one's result
     key, sched, block, chunk, epp = lines[0].split()
     assert int(sched) in (1, 2) and int(block) in (64, 128, 256)
+
+
+# ------------------------------------------------ the paper's printed values
+
+def _paper_rows():
+    import json
+    import os
+    from fractions import Fraction
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_cls_suite1.json")) as f:
+        g = json.load(f)
+    out = []
+    for r in g["rows"]:
+        if r["d"] != 3:
+            continue
+        m = g["materials"]
+        sig = [float(Fraction(v)) for v in m[r["case"][0]]["sigma"]]
+        lam = [float(Fraction(v)) for v in m[r["case"][0]]["lambda"]]
+        c = [float(v) for v in m[r["case"][1]]["c"]]
+        out.append((r, (sig[0], sig[1], lam[0], lam[1], c[0], c[1], 10.0, 3, 100)))
+    return out
+
+
+@pytest.mark.parametrize("row,params", _paper_rows(), ids=lambda v: v["case"] if isinstance(v, dict) else "")
+def test_fp64_box_reproduces_paper_tables(row, params):
+    """Tables 3-5, d = 3: the paper's Tripoli-4 CLS results (1e9 histories) against
+    1e8 FP64 GPU histories, within 4 combined standard errors (Eq. combined_var)."""
+    prob = cls.Problem(params)
+    prob.run(100_000_000, 2017)
+    t = prob.tallies()
+    prob.close()
+    for key, ours, sd in (("R", t["R"], t["sigma_R"]), ("T", t["T"], t["sigma_T"]),
+                          ("phi", t["total_flux"], t["sigma_total_flux"])):
+        val, psd = float(row[key][0]), float(row[key][1])
+        unit = 10.0 ** -len(row[key][0].split(".")[1])
+        assert abs(ours - val) <= 4 * math.sqrt(sd * sd + psd * psd + (0.5 * unit) ** 2), (row["case"], key, ours, val)
