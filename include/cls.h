@@ -3,11 +3,16 @@
  *
  * The library runs CLS "Algorithm A" random walks (paper Sec. 4) for
  * single-speed transport with isotropic scattering through a binary Markov
- * mixture.  Two geometries: the rod (d = 1, directions +-1) and the 3D box
- * (d = 3, paper Sec. 4.3) of side L with leakage on the faces normal to x and
- * specular reflection on the four lateral faces (paper Sec. 2).  Particles
- * enter through x = 0 with the isotropic incident flux of benchmark suite I
- * (cosine law, paper Sec. 4.3).  Estimators: reflection R = J(x=0),
+ * mixture.  Geometries (the `d` argument):
+ *   CLS_GEOM_ROD  (1)  rod of length L, directions +-1;
+ *   CLS_GEOM_BOX  (3)  3D box of side L (paper Sec. 4.3) with leakage on the
+ *                      faces normal to x and specular reflection on the four
+ *                      lateral faces (paper Sec. 2);
+ *   CLS_GEOM_SLAB (11) the paper's d = 1 slab (Sec. 4.1): continuous direction
+ *                      cosine mu, interface distance projected on x
+ *                      (Lambda/|mu|), leakage on both faces.
+ * Particles enter through x = 0 with the isotropic incident flux of benchmark
+ * suite I (cosine law mu = sqrt(xi), paper Sec. 4.1 / 4.3).  Estimators: reflection R = J(x=0),
  * transmission T = J(x=L), absorption A, and the track-length scalar flux
  * phi(x) integrated over y and z on a uniform x mesh (paper Sec. 2).
  *
@@ -31,6 +36,11 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+/* ------------------------------------------------------------- geometries */
+#define CLS_GEOM_ROD 1
+#define CLS_GEOM_BOX 3
+#define CLS_GEOM_SLAB 11
 
 /* ------------------------------------------------------------ error codes */
 #define CLS_OK 0
@@ -105,7 +115,7 @@ typedef struct {
  *                    picked at the source with p_i = Lambda_i / (Lambda_0 + Lambda_1)
  *   c0, c1           scattering probabilities c_i = Sigma_s,i / Sigma_i in [0, 1]
  *   L                rod length / box side, > 0
- *   d                1 (rod) or 3 (box)
+ *   d                CLS_GEOM_ROD, CLS_GEOM_BOX or CLS_GEOM_SLAB
  *   nbins            uniform flux bins along x, 1..4096
  * Selects the current CUDA device, allocates the device tallies (library-
  * owned, freed by cls_destroy) and zeroes them.

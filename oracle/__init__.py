@@ -50,7 +50,7 @@ class Case:
     c0: float
     c1: float
     L: float
-    d: int          # 1 = rod (directions +-1), 3 = box with reflective lateral faces
+    d: int          # 1 = rod (directions +-1), 3 = box with reflective lateral faces, 11 = slab
     nbins: int
 
     @property

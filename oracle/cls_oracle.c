@@ -22,6 +22,9 @@
  *     over y and z, plus reflection / transmission counts (paper Sec. 2, 3.3).
  *   - Rod (d = 1): directions +-1, interface distance along the rod; isotropic
  *     scattering picks +1 or -1 with probability 1/2 each.
+ *   - Slab (d = 11, the paper's d = 1, Sec. 4.1): direction cosine mu with
+ *     respect to x; incident mu = sqrt(xi); interface distance projected,
+ *     d_i = -(Lambda/|mu|) ln(1 - xi); scattering mu = 2 xi - 1; x faces only.
  *   - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
  *     random numbers: as easy as 1, 2, 3", SC'11), counter
  *     (j >> 1, h_lo, h_hi, case), key (seed_lo, seed_hi); even draw j uses
@@ -50,7 +53,7 @@ typedef struct {
     double lambda[2]; /* mean chord lengths Lambda_0, Lambda_1            */
     double c[2];      /* scattering probability c_i = Sigma_s,i / Sigma_i */
     double L;         /* rod length / box side                           */
-    int32_t d;        /* 1 = rod (directions +-1), 3 = box               */
+    int32_t d;        /* 1 = rod (directions +-1), 3 = box, 11 = slab    */
     int32_t nbins;    /* uniform x bins for the flux tally               */
 } orc_case_t;
 
@@ -231,7 +234,9 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
     double w[3] = {1.0, 0.0, 0.0};
 
     /* source: position and direction first, then the material label */
-    if (cs->d == 3) {
+    if (cs->d == 11) {
+        w[0] = sqrt(next_u(&s)); /* cosine law mu = sqrt(xi) */
+    } else if (cs->d == 3) {
         r[1] = L * next_u(&s);
         r[2] = L * next_u(&s);
         double mu = sqrt(next_u(&s));
@@ -258,6 +263,8 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
         double l_c = (cs->sigma[m] > 0.0) ? -log(1.0 - u_c) / cs->sigma[m] : INFINITY;
         double u_i = next_u(&s);
         double l_i = -cs->lambda[m] * log(1.0 - u_i);
+        if (cs->d == 11)
+            l_i = l_i / fabs(w[0]); /* projection of the chord on x */
 
         /* boundary distance: x faces, then (box) the lateral faces */
         double l_b = INFINITY;
@@ -315,6 +322,8 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
                 if (next_u(&s) < cs->c[m]) {
                     if (cs->d == 1) {
                         w[0] = (next_u(&s) < 0.5) ? 1.0 : -1.0;
+                    } else if (cs->d == 11) {
+                        w[0] = 2.0 * next_u(&s) - 1.0;
                     } else {
                         double mu = 2.0 * next_u(&s) - 1.0;
                         double ph = (2.0 * ORC_PI) * next_u(&s);
@@ -348,7 +357,7 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
 static int check_case(const orc_case_t *cs)
 {
     if (!cs) return -1;
-    if (cs->d != 1 && cs->d != 3) return -1;
+    if (cs->d != 1 && cs->d != 3 && cs->d != 11) return -1;
     if (cs->nbins < 1) return -1;
     if (!(cs->L > 0.0)) return -1;
     for (int i = 0; i < 2; i++) {

@@ -235,6 +235,8 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint
         R::sincos_2pi(draw(s, key), &sn, &cs);
         const P st = sqrt(P(1) - mu * mu);
         set_direction(s, mu, st * cs, st * sn);
+    } else if (cp.d == 11) {
+        set_direction(s, sqrt(draw(s, key)), P(0), P(0));  // slab: mu = sqrt(xi)
     } else {
         s.w[0] = P(1);
         s.w[1] = P(0);
@@ -336,7 +338,9 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
     const P om_c = draw_one_minus(s, key);
     const P l_c = (R::sigma(cp, m) > P(0)) ? R::nonneg(R::collision(cp, m, om_c)) : INF;
     const P om_i = draw_one_minus(s, key);
-    const P l_i = R::nonneg(R::interface(cp, m, om_i));
+    P l_i = R::interface(cp, m, om_i);
+    if (cp.d == 11) l_i *= fabs(s.iw[0]);  // slab: the chord projected on x, Lambda/|mu|
+    l_i = R::nonneg(l_i);
 
     // boundary distance: x faces, then the lateral faces of the box
     P l_b = INF;
@@ -419,6 +423,8 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
                 const P w = (hi >> 31) == 0u ? P(1) : P(-1);
                 s.w[0] = w;
                 s.iw[0] = w;
+            } else if (cp.d == 11) {
+                set_direction(s, P(2) * draw(s, key) - P(1), P(0), P(0));  // slab: mu = 2 xi - 1
             } else {
                 const P mu = P(2) * draw(s, key) - P(1);
                 P sn, cs;

@@ -89,7 +89,8 @@ def test_uniform_mapping_matches_oracle():
 
 # -------------------------------------------------------------- traces
 
-@pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10, workloads.suite_case("1c", nbins=10)])
+@pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10, workloads.suite_case("1c", nbins=10),
+                                    workloads.suite_case("3c", d=11, nbins=10)])
 def test_fp64_traces_replay_the_oracle(params):
     prob = cls.Problem(params)
     case = ocase(params)
@@ -123,6 +124,8 @@ def test_box_parity_ragged(n):
 
 
 @pytest.mark.parametrize("params", [
+    workloads.suite_case("1c", d=11, nbins=64),          # the paper's slab
+    (0.7, 3.0, 0.4, 2.0, 0.8, 0.3, 3.0, 11, 13),         # slab, odd bin count
     (0.0, 2.0, 0.3, 0.7, 0.5, 0.5, 2.0, 3, 1),          # Sigma_0 = 0, one bin
     (1.0, 1.0, 1e-3, 2e-3, 1.0, 0.0, 1.0, 1, 4096),     # c = 1 / 0, maximum bins, tiny chords
     (3.0, 0.5, 50.0, 80.0, 0.0, 0.0, 0.01, 3, 7),      # pure absorbers, thin box, huge chords
@@ -328,7 +331,7 @@ def test_autotune_file_cache(tmp_path):
 
 # ------------------------------------------------ the paper's printed values
 
-def _paper_rows():
+def _paper_rows(d=3):
     import json
     import os
     from fractions import Fraction
@@ -336,20 +339,22 @@ def _paper_rows():
         g = json.load(f)
     out = []
     for r in g["rows"]:
-        if r["d"] != 3:
+        if r["d"] != d:
             continue
         m = g["materials"]
         sig = [float(Fraction(v)) for v in m[r["case"][0]]["sigma"]]
         lam = [float(Fraction(v)) for v in m[r["case"][0]]["lambda"]]
         c = [float(v) for v in m[r["case"][1]]["c"]]
-        out.append((r, (sig[0], sig[1], lam[0], lam[1], c[0], c[1], 10.0, 3, 100)))
+        out.append((r, (sig[0], sig[1], lam[0], lam[1], c[0], c[1], 10.0, 3 if d == 3 else 11, 100)))
     return out
 
 
-@pytest.mark.parametrize("row,params", _paper_rows(), ids=lambda v: v["case"] if isinstance(v, dict) else "")
-def test_fp64_box_reproduces_paper_tables(row, params):
-    """Tables 3-5, d = 3: the paper's Tripoli-4 CLS results (1e9 histories) against
-    1e8 FP64 GPU histories, within 4 combined standard errors (Eq. combined_var)."""
+@pytest.mark.parametrize("row,params", _paper_rows(3) + _paper_rows(1),
+                         ids=lambda v: f"{v['case']}-d{v['d']}" if isinstance(v, dict) else "")
+def test_fp64_reproduces_paper_tables(row, params):
+    """Tables 3-5, d = 3 (box) and d = 1 (slab): the paper's Tripoli-4 CLS results
+    (1e9 histories) against 1e8 FP64 GPU histories, within 4 combined standard
+    errors (Eq. combined_var)."""
     prob = cls.Problem(params)
     prob.run(100_000_000, 2017)
     t = prob.tallies()

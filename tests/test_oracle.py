@@ -21,6 +21,7 @@ from oracle import lp_ado
 
 C1 = oracle.Case(0.5, 5.0, 2.0, 0.5, 0.5, 0.9, 10.0, 1, 100)           # rod, L = 10
 C2 = oracle.Case(0.1, 10.0, 1.0, 0.1, 0.99, 0.99, 10.0, 3, 200)        # box, L = 10
+SLAB = oracle.Case(10 / 99, 100 / 11, 99 / 100, 11 / 100, 0.9, 0.9, 10.0, 11, 50)  # paper case 1c, d = 1
 HERE = os.path.dirname(__file__)
 
 
@@ -43,7 +44,7 @@ def assert_matches_lp(res, lp, kmax=4.0, bins_kmax=4.5):
 
 # ---------------------------------------------------------------- invariants
 
-@pytest.mark.parametrize("case", [C1, C2, oracle.Case(1.0, 2.0, 0.3, 0.7, 1.0, 0.0, 2.0, 3, 7)])
+@pytest.mark.parametrize("case", [C1, C2, SLAB, oracle.Case(1.0, 2.0, 0.3, 0.7, 1.0, 0.0, 2.0, 3, 7)])
 def test_balance_and_conservation(case):
     raw = oracle.run(case, 5, 123, 3000)
     assert raw["nR"] + raw["nT"] + raw["nA"] + raw["n_capped"] == 3000
@@ -99,7 +100,7 @@ def expected_draws(case, rows):
     """Draw accounting of Algorithm A: source (3D: y, z, mu', phi'), material label,
     two distances per event, one absorb/scatter decision per collision, and the
     scattering direction (rod 1 draw, 3D 2 draws)."""
-    n = (4 if case.d == 3 else 0) + 1
+    n = {3: 4, 11: 1}.get(case.d, 0) + 1
     for ev in rows[:, 0].astype(int):
         if ev == 6:
             continue
@@ -107,11 +108,11 @@ def expected_draws(case, rows):
         if ev in (3, 4):
             n += 1
         if ev == 3:
-            n += 1 if case.d == 1 else 2
+            n += 2 if case.d == 3 else 1
     return n
 
 
-@pytest.mark.parametrize("case", [C1, C2])
+@pytest.mark.parametrize("case", [C1, C2, SLAB])
 def test_trace_is_a_valid_walk(case):
     for h in range(40):
         rows, cnt = oracle.trace(case, 3, h)
@@ -124,8 +125,11 @@ def test_trace_is_a_valid_walk(case):
         assert rows[:, 9].sum() == pytest.approx(cnt["sum_t"], rel=1e-12)
         r = rows[:, 2:5]
         assert np.all(r >= -1e-9 * case.L) and np.all(r <= case.L * (1 + 1e-9))
-        nrm = np.linalg.norm(rows[:, 5:8], axis=1)
-        np.testing.assert_allclose(nrm, 1.0, rtol=1e-12)
+        if case.d == 11:  # the slab carries only the direction cosine mu
+            assert np.all(np.abs(rows[:, 5]) <= 1.0) and np.all(rows[:, 6:8] == 0.0)
+        else:
+            nrm = np.linalg.norm(rows[:, 5:8], axis=1)
+            np.testing.assert_allclose(nrm, 1.0, rtol=1e-12)
         if case.d == 1:
             assert np.all(np.abs(rows[:, 5]) == 1.0)
         # an interface switches the label; other events keep it
@@ -172,6 +176,25 @@ def test_box_config_matches_lp_solution():
     res = oracle.finalize(raw, C2)
     lp = lp_ado.solve([C2.sigma0, C2.sigma1], [C2.lambda0, C2.lambda1], [C2.c0, C2.c1], C2.L, "box3d", C2.nbins)
     assert_matches_lp(res, lp)
+
+
+def test_slab_matches_lp_solution():
+    """The paper's d = 1 slab (Sec. 4.1): projected chords Lambda/|mu|, against the
+    LP slab solution (which the paper's d = 1 rows of Tables 3-5 pin)."""
+    raw = oracle.run_parallel(SLAB, 5, 0, 120_000)
+    res = oracle.finalize(raw, SLAB)
+    lp = lp_ado.solve([SLAB.sigma0, SLAB.sigma1], [SLAB.lambda0, SLAB.lambda1], [SLAB.c0, SLAB.c1], SLAB.L,
+                      "slab1d", SLAB.nbins)
+    assert_matches_lp(res, lp)
+
+
+def test_slab_is_not_the_box():
+    """Projected chords change the answer: the slab's R differs from the box's (paper
+    Table 3, case 1c: 0.36953 for d = 1, 0.39619 for d = 3)."""
+    box = oracle.Case(*[getattr(SLAB, f) for f in ("sigma0", "sigma1", "lambda0", "lambda1", "c0", "c1", "L")], 3, 50)
+    rs = oracle.finalize(oracle.run_parallel(SLAB, 6, 0, 60_000), SLAB)
+    rb = oracle.finalize(oracle.run_parallel(box, 6, 0, 60_000), box)
+    assert abs(rs["R"] - rb["R"]) > 5 * math.hypot(rs["sigma_R"], rb["sigma_R"])
 
 
 def test_box_pure_absorber_single_material():
