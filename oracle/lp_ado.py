@@ -26,6 +26,13 @@ Suite I incidence: psi_i(0, mu > 0) = p_i f with f = 1 / sum_{mu_n > 0} w_n mu_n
 (unit incident current, isotropic incident angular flux -- the cosine law of
 paper Sec. 4.1/4.3); psi(L, mu < 0) = 0.
 
+Suite II: a uniform isotropic volume source of one particle in total, born in
+material i with probability p_i (paper Sec. 2, 4.1, 4.3): the source term
+q_i = p_i / (L sum_m w_m) is added to every equation, no incident flux.  Its
+particular solution is the constant psi_p = -C^-1 q of the collision /
+transition matrix C; the modal part then satisfies psi_p + psi_h = 0 on the
+incoming directions of both faces.
+
 The solution is the analytical discrete-ordinates form psi(x) = sum_k a_k v_k
 exp(lambda_k (x - x_k)) with x_k = L for growing modes and 0 for decaying
 ones, so no exponential overflows; the 2N boundary conditions fix a_k.
@@ -62,11 +69,14 @@ def _integral_exp(lam, a, b, ref):
     return out
 
 
-def solve(sigma, lam, c, L, kind: str, nbins: int = 0, n_half: int = 32) -> dict:
-    """Solve the LP equations for suite I incidence.
+def solve(sigma, lam, c, L, kind: str, nbins: int = 0, n_half: int = 32, source: str = "incident") -> dict:
+    """Solve the LP equations for suite I (source="incident") or suite II
+    (source="volume") sources.
 
     Returns R, T, A, total_flux (= int phi dx), track (per material), and if
-    nbins > 0 the bin-averaged flux on the uniform mesh e_k = k L / nbins."""
+    nbins > 0 the bin-averaged flux on the uniform mesh e_k = k L / nbins.
+    For the volume source R and T are the currents leaving x = 0 and x = L and
+    Lk = (R + T) / 2 is the paper's leakage observable."""
     sigma = np.asarray(sigma, dtype=float)
     lam = np.asarray(lam, dtype=float)
     c = np.asarray(c, dtype=float)
@@ -95,6 +105,12 @@ def solve(sigma, lam, c, L, kind: str, nbins: int = 0, n_half: int = 32) -> dict
     ev = ev.real
     V = V.real
     ref = np.where(ev > 0.0, L, 0.0)
+    volume = source == "volume"
+    if volume:
+        q = np.repeat(p, n) / (L * np.sum(w))
+        psi_p = -np.linalg.solve(C, q)  # constant particular solution
+    else:
+        psi_p = np.zeros(K)
     f = 1.0 / np.sum((w * mu)[mu > 0])
     A = np.zeros((K, K))
     b = np.zeros(K)
@@ -102,20 +118,21 @@ def solve(sigma, lam, c, L, kind: str, nbins: int = 0, n_half: int = 32) -> dict
         i = r // n
         if mu2[r] > 0:
             A[r] = V[r] * np.exp(ev * (0.0 - ref))
-            b[r] = p[i] * f
+            b[r] = (0.0 if volume else p[i] * f) - psi_p[r]
         else:
             A[r] = V[r] * np.exp(ev * (L - ref))
+            b[r] = -psi_p[r]
     coef = np.linalg.solve(A, b)
-    psi0 = V @ (coef * np.exp(ev * (0.0 - ref)))
-    psiL = V @ (coef * np.exp(ev * (L - ref)))
+    psi0 = V @ (coef * np.exp(ev * (0.0 - ref))) + psi_p
+    psiL = V @ (coef * np.exp(ev * (L - ref))) + psi_p
     R = float(np.sum((w2 * np.abs(mu2) * psi0)[mu2 < 0]))
     T = float(np.sum((w2 * mu2 * psiL)[mu2 > 0]))
-    out = {"R": R, "T": T, "A": 1.0 - R - T}
+    out = {"R": R, "T": T, "A": 1.0 - R - T, "Lk": 0.5 * (R + T)}
     full = _integral_exp(ev, 0.0, L, ref) * coef
     track = []
     for i in range(2):
         sl = slice(i * n, (i + 1) * n)
-        track.append(float(w @ (V[sl] @ full)))
+        track.append(float(w @ (V[sl] @ full)) + L * float(w @ psi_p[sl]))
     out["track"] = tuple(track)
     out["total_flux"] = track[0] + track[1]
     # absorption from the track-length estimator, sum_i Sigma_a,i * track_i
@@ -126,5 +143,5 @@ def solve(sigma, lam, c, L, kind: str, nbins: int = 0, n_half: int = 32) -> dict
         flux = np.empty(nbins)
         for k in range(nbins):
             flux[k] = np.sum(sw * coef * _integral_exp(ev, edges[k], edges[k + 1], ref))
-        out["flux"] = flux / (L / nbins)
+        out["flux"] = flux / (L / nbins) + float(w2 @ psi_p)
     return out

@@ -163,3 +163,40 @@ def test_quadrature_converged():
         assert a[k] == pytest.approx(b[k], rel=1e-5)
     np.testing.assert_allclose(a["flux"], b["flux"], rtol=1e-4)
     assert b["A"] == pytest.approx(b["A_track"], rel=1e-9)
+
+
+def _load_rows2():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_cls_suite2.json")) as f:
+        g = json.load(f)
+    with open(GOLDEN) as f:
+        mats = json.load(f)["materials"]
+    rows = []
+    for r in g["rows"]:
+        case, sub = r["case"][0], r["case"][1]
+        sig = [float(Fraction(s)) for s in mats[case]["sigma"]]
+        lam = [float(Fraction(s)) for s in mats[case]["lambda"]]
+        c = [float(s) for s in mats[sub]["c"]]
+        rows.append((r, sig, lam, c))
+    return rows
+
+
+@pytest.mark.parametrize("row", _load_rows2(), ids=lambda r: f"{r[0]['case']}-d{r[0]['d']}")
+def test_paper_suite2_cls_tables(row):
+    """The LP solution with the uniform isotropic volume source equals the paper's
+    suite II CLS estimates (Tables 6-8): leakage L = (T + R)/2 and <phi>."""
+    r, sig, lam, c = row
+    kind = "box3d" if r["d"] == 3 else "slab1d"
+    out = lp_ado.solve(sig, lam, c, 10.0, kind, n_half=32, source="volume")
+    for key, ours in (("L", out["Lk"]), ("phi", out["total_flux"])):
+        val, sd = r[key]
+        tol = 4 * math.hypot(float(sd), 0.5 * _printed_unit(val)) + 1e-6 * abs(float(val))
+        assert abs(ours - float(val)) <= tol, (key, ours, val, sd)
+
+
+def test_volume_source_balance_and_symmetry():
+    """One source particle: A + R + T = 1 with A from the track-length estimator, and
+    by symmetry of the uniform source the two faces leak equally (paper Sec. 2)."""
+    out = lp_ado.solve([0.3, 2.0], [0.7, 0.4], [0.6, 0.8], 4.0, "box3d", nbins=20, source="volume")
+    assert out["A_track"] + out["R"] + out["T"] == pytest.approx(1.0, rel=1e-9)
+    assert out["R"] == pytest.approx(out["T"], rel=1e-9)
+    np.testing.assert_allclose(out["flux"], out["flux"][::-1], rtol=1e-9)
