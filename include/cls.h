@@ -11,8 +11,9 @@
  *   CLS_GEOM_SLAB (11) the paper's d = 1 slab (Sec. 4.1): continuous direction
  *                      cosine mu, interface distance projected on x
  *                      (Lambda/|mu|), leakage on both faces.
- * Particles enter through x = 0 with the isotropic incident flux of benchmark
- * suite I (cosine law mu = sqrt(xi), paper Sec. 4.1 / 4.3).  Estimators: reflection R = J(x=0),
+ * Sources (CLS_OPT_SOURCE): the isotropic incident flux on x = 0 of benchmark
+ * suite I (cosine law mu = sqrt(xi), paper Sec. 4.1 / 4.3, the default), or
+ * the uniform isotropic volume source of suite II.  Estimators: reflection R = J(x=0),
  * transmission T = J(x=L), absorption A, and the track-length scalar flux
  * phi(x) integrated over y and z on a uniform x mesh (paper Sec. 2).
  *
@@ -65,6 +66,12 @@ extern "C" {
 #define CLS_OPT_EVENTS_PER_PASS 9 /* event schedule: events per particle per pass (1..64)  */
 #define CLS_OPT_FIRST_HISTORY 10  /* set the next history id of every case (0..2^62); lets   */
                                   /* processes walk disjoint history ranges of one seed     */
+#define CLS_OPT_SOURCE 11         /* CLS_SOURCE_INCIDENT (default) or CLS_SOURCE_VOLUME, for */
+                                  /* every case; only before the first run (CLS_E_STATE)    */
+
+#define CLS_SOURCE_INCIDENT 0 /* suite I: isotropic incident flux on x = 0, cosine law (Sec. 4.1/4.3) */
+#define CLS_SOURCE_VOLUME 1   /* suite II: one particle, uniform in the volume, isotropic (Sec. 2,    */
+                              /* 4.1, 4.3); the paper's leakage is L = (R + T) / 2                      */
 
 #define CLS_PREC_FP64 0 /* all arithmetic in FP64 (draw-for-draw equal to the FP64 oracle) */
 #define CLS_PREC_FP32 1 /* position / direction / distance in FP32, tallies in FP64          */

@@ -52,6 +52,7 @@ class Case:
     L: float
     d: int          # 1 = rod (directions +-1), 3 = box with reflective lateral faces, 11 = slab
     nbins: int
+    source: int = 0  # 0 = incident flux on x = 0 (suite I), 1 = uniform isotropic volume source (suite II)
 
     @property
     def p0(self) -> float:
@@ -62,7 +63,8 @@ class Case:
 class _OrcCase(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double * 2), ("lambda_", ctypes.c_double * 2),
                 ("c", ctypes.c_double * 2), ("L", ctypes.c_double),
-                ("d", ctypes.c_int32), ("nbins", ctypes.c_int32)]
+                ("d", ctypes.c_int32), ("nbins", ctypes.c_int32), ("source", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class _OrcCounts(ctypes.Structure):
@@ -119,7 +121,7 @@ def _ocase(case: Case) -> _OrcCase:
     oc.sigma[0], oc.sigma[1] = case.sigma0, case.sigma1
     oc.lambda_[0], oc.lambda_[1] = case.lambda0, case.lambda1
     oc.c[0], oc.c[1] = case.c0, case.c1
-    oc.L, oc.d, oc.nbins = case.L, int(case.d), int(case.nbins)
+    oc.L, oc.d, oc.nbins, oc.source = case.L, int(case.d), int(case.nbins), int(case.source)
     return oc
 
 
@@ -265,6 +267,9 @@ def finalize(raw: dict, case: Case) -> dict:
     else:
         res["flux_sigma"] = np.full(case.nbins, np.nan)
     res["track"] = (raw["track"][0] / N, raw["track"][1] / N)
+    res["Lk"] = 0.5 * (res["R"] + res["T"])  # suite II leakage (paper Sec. 2)
+    res["sigma_Lk"] = math.sqrt((raw["nR"] + raw["nT"]) / N * (1 - (raw["nR"] + raw["nT"]) / N) / (N - 1)) / 2 \
+        if N > 1 else float("nan")
     for k in ("n_coll", "n_int", "n_refl", "n_events", "n_capped"):
         res[k] = raw[k]
     res["n_histories"] = N

@@ -22,6 +22,10 @@
  *     over y and z, plus reflection / transmission counts (paper Sec. 2, 3.3).
  *   - Rod (d = 1): directions +-1, interface distance along the rod; isotropic
  *     scattering picks +1 or -1 with probability 1/2 each.
+ *   - Suite II source (paper Sec. 2, 4.1, 4.3): position uniform in the
+ *     box (x; box also y, z), direction isotropic (rod: +-1 with probability
+ *     1/2; slab: mu = 2 xi - 1; box: mu = 2 xi - 1, phi = 2 pi xi', omega =
+ *     (sqrt(1-mu^2) cos phi, sqrt(1-mu^2) sin phi, mu)), then the label.
  *   - Slab (d = 11, the paper's d = 1, Sec. 4.1): direction cosine mu with
  *     respect to x; incident mu = sqrt(xi); interface distance projected,
  *     d_i = -(Lambda/|mu|) ln(1 - xi); scattering mu = 2 xi - 1; x faces only.
@@ -55,6 +59,9 @@ typedef struct {
     double L;         /* rod length / box side                           */
     int32_t d;        /* 1 = rod (directions +-1), 3 = box, 11 = slab    */
     int32_t nbins;    /* uniform x bins for the flux tally               */
+    int32_t source;   /* 0 = incident flux on x = 0 (suite I),           */
+                      /* 1 = uniform isotropic volume source (suite II)   */
+    int32_t pad;
 } orc_case_t;
 
 typedef struct {
@@ -234,7 +241,23 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
     double w[3] = {1.0, 0.0, 0.0};
 
     /* source: position and direction first, then the material label */
-    if (cs->d == 11) {
+    if (cs->source == 1) {
+        r[0] = L * next_u(&s);
+        if (cs->d == 3) {
+            r[1] = L * next_u(&s);
+            r[2] = L * next_u(&s);
+            double mu = 2.0 * next_u(&s) - 1.0;
+            double ph = (2.0 * ORC_PI) * next_u(&s);
+            double st = sqrt(1.0 - mu * mu);
+            w[0] = st * cos(ph);
+            w[1] = st * sin(ph);
+            w[2] = mu;
+        } else if (cs->d == 11) {
+            w[0] = 2.0 * next_u(&s) - 1.0;
+        } else {
+            w[0] = (next_u(&s) < 0.5) ? 1.0 : -1.0;
+        }
+    } else if (cs->d == 11) {
         w[0] = sqrt(next_u(&s)); /* cosine law mu = sqrt(xi) */
     } else if (cs->d == 3) {
         r[1] = L * next_u(&s);
@@ -359,6 +382,7 @@ static int check_case(const orc_case_t *cs)
     if (!cs) return -1;
     if (cs->d != 1 && cs->d != 3 && cs->d != 11) return -1;
     if (cs->nbins < 1) return -1;
+    if (cs->source != 0 && cs->source != 1) return -1;
     if (!(cs->L > 0.0)) return -1;
     for (int i = 0; i < 2; i++) {
         if (!(cs->sigma[i] >= 0.0) || !isfinite(cs->sigma[i])) return -1;

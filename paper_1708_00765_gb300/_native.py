@@ -30,6 +30,9 @@ CLS_OPT_BLOCKS_PER_SM = 7
 CLS_OPT_BANK = 8
 CLS_OPT_EVENTS_PER_PASS = 9
 CLS_OPT_FIRST_HISTORY = 10
+CLS_OPT_SOURCE = 11
+CLS_SOURCE_INCIDENT = 0
+CLS_SOURCE_VOLUME = 1
 
 CLS_PREC_FP64 = 0
 CLS_PREC_FP32 = 1
@@ -144,9 +147,9 @@ def _stream_handle(stream) -> int | None:
 OPTIONS = {"precision": CLS_OPT_PRECISION, "schedule": CLS_OPT_SCHEDULE, "block": CLS_OPT_BLOCK,
            "chunk": CLS_OPT_CHUNK, "nbatch": CLS_OPT_NBATCH, "max_events": CLS_OPT_MAX_EVENTS,
            "blocks_per_sm": CLS_OPT_BLOCKS_PER_SM, "bank": CLS_OPT_BANK,
-           "events_per_pass": CLS_OPT_EVENTS_PER_PASS, "first_history": CLS_OPT_FIRST_HISTORY}
+           "events_per_pass": CLS_OPT_EVENTS_PER_PASS, "first_history": CLS_OPT_FIRST_HISTORY, "source": CLS_OPT_SOURCE}
 VALUES = {"fp64": CLS_PREC_FP64, "fp32": CLS_PREC_FP32, "history": CLS_SCHED_HISTORY, "event": CLS_SCHED_EVENT,
-          "auto": CLS_SCHED_AUTO}
+          "auto": CLS_SCHED_AUTO, "incident": CLS_SOURCE_INCIDENT, "volume": CLS_SOURCE_VOLUME}
 
 
 class Problem:

@@ -226,7 +226,31 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint
     s.r[0] = P(0);
     s.r[1] = P(0);
     s.r[2] = P(0);
-    if (cp.d == 3) {
+    if (cp.source == 1) {  // suite II: uniform position, isotropic direction
+        const P L = R::L(cp);
+        s.r[0] = L * draw(s, key);
+        if (cp.d == 3) {
+            s.r[1] = L * draw(s, key);
+            s.r[2] = L * draw(s, key);
+            const P mu = P(2) * draw(s, key) - P(1);
+            P sn, cs;
+            R::sincos_2pi(draw(s, key), &sn, &cs);
+            const P st = sqrt(P(1) - mu * mu);
+            set_direction(s, st * cs, st * sn, mu);
+        } else if (cp.d == 11) {
+            set_direction(s, P(2) * draw(s, key) - P(1), P(0), P(0));
+        } else {
+            uint32_t hi, lo;
+            draw_words(s, key, hi, lo);
+            const P w = (hi >> 31) == 0u ? P(1) : P(-1);  // u < 1/2
+            s.w[0] = w;
+            s.w[1] = P(0);
+            s.w[2] = P(0);
+            s.iw[0] = w;
+            s.iw[1] = R::inf();
+            s.iw[2] = R::inf();
+        }
+    } else if (cp.d == 3) {
         const P L = R::L(cp);
         s.r[1] = L * draw(s, key);
         s.r[2] = L * draw(s, key);

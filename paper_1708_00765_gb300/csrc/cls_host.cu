@@ -717,6 +717,13 @@ int cls_set_option(cls_handle *h, int key, int64_t v) {
         if (v < 1 || v > 64) return CLS_E_INVAL;
         o.events_per_pass = (int)v;
         break;
+    case CLS_OPT_SOURCE:
+        if (v != CLS_SOURCE_INCIDENT && v != CLS_SOURCE_VOLUME) return CLS_E_INVAL;
+        if (h->ran) return CLS_E_STATE;
+        for (auto &c : h->cases) c.source = (int32_t)v;
+        CLS_CUDA(cudaSetDevice(h->device));
+        CLS_CUDA(cudaMemcpy(h->d_cases, h->cases.data(), h->cases.size() * sizeof(CaseParams), cudaMemcpyHostToDevice));
+        break;
     case CLS_OPT_FIRST_HISTORY:
         if (v < 0 || v > ((int64_t)1 << 62)) return CLS_E_INVAL;
         for (auto &nh : h->next_history) nh = (uint64_t)v;
@@ -742,6 +749,7 @@ int cls_get_option(const cls_handle *h, int key, int64_t *v) {
     case CLS_OPT_BANK: *v = o.bank; break;
     case CLS_OPT_EVENTS_PER_PASS: *v = o.events_per_pass; break;
     case CLS_OPT_FIRST_HISTORY: *v = h->next_history.empty() ? 0 : (int64_t)h->next_history[0]; break;
+    case CLS_OPT_SOURCE: *v = h->cases.empty() ? 0 : h->cases[0].source; break;
     default: return CLS_E_INVAL;
     }
     return CLS_OK;

@@ -31,7 +31,7 @@ struct CaseParams {
     int32_t d;      // 1 rod, 3 box
     int32_t nbins;
     uint32_t case_id;  // Philox counter word 3
-    uint32_t pad;
+    int32_t source;    // 0 incident flux on x = 0 (suite I), 1 uniform isotropic volume source (suite II)
     double cost;    // host estimate of events per history (ordering only)
 };
 

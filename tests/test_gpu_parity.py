@@ -28,8 +28,8 @@ COUNT_KEYS = ("nR", "nT", "nA", "n_coll", "n_int", "n_refl", "n_events", "max_ev
 GPU_KEYS = {"n_int": "n_interface", "n_refl": "n_reflect"}
 
 
-def ocase(p):
-    return oracle.Case(*p[:7], int(p[7]), int(p[8]))
+def ocase(p, source=0):
+    return oracle.Case(*p[:7], int(p[7]), int(p[8]), source=source)
 
 
 def gpu_raw(params, n, seed, first_runs=None, **opts):
@@ -361,6 +361,78 @@ def test_fp64_reproduces_paper_tables(row, params):
     prob.close()
     for key, ours, sd in (("R", t["R"], t["sigma_R"]), ("T", t["T"], t["sigma_T"]),
                           ("phi", t["total_flux"], t["sigma_total_flux"])):
+        val, psd = float(row[key][0]), float(row[key][1])
+        unit = 10.0 ** -len(row[key][0].split(".")[1])
+        assert abs(ours - val) <= 4 * math.sqrt(sd * sd + psd * psd + (0.5 * unit) ** 2), (row["case"], key, ours, val)
+
+
+
+# ------------------------------------------------------ suite II source
+
+VOLUME_CASES = [workloads.ROD_L10, workloads.BOX_L10, workloads.suite_case("2c", d=11, nbins=30)]
+
+
+@pytest.mark.parametrize("params", VOLUME_CASES)
+def test_volume_source_traces_and_parity(params):
+    """Suite II (uniform isotropic volume source): traces equal the oracle's event by
+    event, and whole runs are bit-exact in counts."""
+    prob = cls.Problem(params)
+    prob.set_option("source", "volume")
+    case = ocase(params, source=1)
+    for h in range(24):
+        g = prob.trace(9, h)
+        o, _ = oracle.trace(case, 9, h)
+        assert g.shape == o.shape and np.array_equal(g[:, [0, 1, 8]], o[:, [0, 1, 8]]), h
+        np.testing.assert_allclose(g[:, 2:8], o[:, 2:8], rtol=1e-11, atol=1e-12)
+    prob.run(10_007, 9)
+    raw_g = prob.raw_tallies()
+    prob.close()
+    assert_parity(raw_g, oracle.run(case, 9, 0, 10_007))
+
+
+def test_source_option_only_before_the_first_run():
+    prob = cls.Problem(workloads.ROD_L10)
+    prob.run(100, 1)
+    with pytest.raises(cls.ClsError) as e:
+        prob.set_option("source", "volume")
+    assert e.value.code == cls._native.CLS_E_STATE
+    prob.close()
+
+
+def _paper_rows2(d):
+    import json
+    import os
+    from fractions import Fraction
+    here = os.path.dirname(__file__)
+    with open(os.path.join(here, "golden", "paper_cls_suite2.json")) as f:
+        g = json.load(f)
+    with open(os.path.join(here, "golden", "paper_cls_suite1.json")) as f:
+        m = json.load(f)["materials"]
+    out = []
+    for r in g["rows"]:
+        if r["d"] != d:
+            continue
+        sig = [float(Fraction(v)) for v in m[r["case"][0]]["sigma"]]
+        lam = [float(Fraction(v)) for v in m[r["case"][0]]["lambda"]]
+        c = [float(v) for v in m[r["case"][1]]["c"]]
+        out.append((r, (sig[0], sig[1], lam[0], lam[1], c[0], c[1], 10.0, 3 if d == 3 else 11, 100)))
+    return out
+
+
+@pytest.mark.parametrize("row,params", _paper_rows2(3) + _paper_rows2(1),
+                         ids=lambda v: f"{v['case']}-d{v['d']}" if isinstance(v, dict) else "")
+def test_fp64_reproduces_paper_suite2_tables(row, params):
+    """Tables 6-8 (suite II), d = 3 and d = 1: leakage L = (T + R)/2 and <phi> from 1e8
+    FP64 GPU histories against the paper's 1e9-history CLS values, 4 combined sigma."""
+    prob = cls.Problem(params)
+    prob.set_option("source", "volume")
+    prob.run(100_000_000, 2018)
+    t = prob.tallies()
+    prob.close()
+    N = t["n_histories"]
+    pl = (t["nR"] + t["nT"]) / N
+    lk, sd_lk = pl / 2, math.sqrt(pl * (1 - pl) / (N - 1)) / 2
+    for key, ours, sd in (("L", lk, sd_lk), ("phi", t["total_flux"], t["sigma_total_flux"])):
         val, psd = float(row[key][0]), float(row[key][1])
         unit = 10.0 ** -len(row[key][0].split(".")[1])
         assert abs(ours - val) <= 4 * math.sqrt(sd * sd + psd * psd + (0.5 * unit) ** 2), (row["case"], key, ours, val)

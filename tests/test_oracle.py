@@ -100,7 +100,10 @@ def expected_draws(case, rows):
     """Draw accounting of Algorithm A: source (3D: y, z, mu', phi'), material label,
     two distances per event, one absorb/scatter decision per collision, and the
     scattering direction (rod 1 draw, 3D 2 draws)."""
-    n = {3: 4, 11: 1}.get(case.d, 0) + 1
+    if case.source == 1:  # suite II: position (x; box: y, z), then direction
+        n = {3: 5, 11: 2}.get(case.d, 2) + 1
+    else:
+        n = {3: 4, 11: 1}.get(case.d, 0) + 1
     for ev in rows[:, 0].astype(int):
         if ev == 6:
             continue
@@ -112,7 +115,11 @@ def expected_draws(case, rows):
     return n
 
 
-@pytest.mark.parametrize("case", [C1, C2, SLAB])
+VOL = [oracle.Case(*[getattr(c, f) for f in ("sigma0", "sigma1", "lambda0", "lambda1", "c0", "c1", "L", "d",
+                                             "nbins")], source=1) for c in (C1, C2, SLAB)]
+
+
+@pytest.mark.parametrize("case", [C1, C2, SLAB] + VOL)
 def test_trace_is_a_valid_walk(case):
     for h in range(40):
         rows, cnt = oracle.trace(case, 3, h)
@@ -186,6 +193,20 @@ def test_slab_matches_lp_solution():
     lp = lp_ado.solve([SLAB.sigma0, SLAB.sigma1], [SLAB.lambda0, SLAB.lambda1], [SLAB.c0, SLAB.c1], SLAB.L,
                       "slab1d", SLAB.nbins)
     assert_matches_lp(res, lp)
+
+
+@pytest.mark.parametrize("case,kind", [(VOL[0], "rod"), (VOL[1], "box3d"), (VOL[2], "slab1d")])
+def test_volume_source_matches_lp_solution(case, kind):
+    """Suite II (paper Sec. 2, 4.1, 4.3): uniform isotropic volume source against the
+    LP solution with a volume source (which the paper's Tables 6-8 pin)."""
+    raw = oracle.run_parallel(case, 8, 0, 80_000)
+    res = oracle.finalize(raw, case)
+    lp = lp_ado.solve([case.sigma0, case.sigma1], [case.lambda0, case.lambda1], [case.c0, case.c1], case.L, kind,
+                      case.nbins, source="volume")
+    assert_matches_lp(res, lp)
+    assert abs(res["Lk"] - lp["Lk"]) < 4 * res["sigma_Lk"]
+    # the uniform source leaks through both faces alike
+    assert abs(res["R"] - res["T"]) < 4 * math.hypot(res["sigma_R"], res["sigma_T"])
 
 
 def test_slab_is_not_the_box():
