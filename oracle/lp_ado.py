@@ -19,8 +19,15 @@ with interface rate per unit path length r_i(mu):
     lateral faces leave the x-marginal equal to an infinite slab;
   * ``"slab1d"``: |mu|/Lambda_i -- the paper's d = 1 slab, whose interface
     distance is projected on x (paper Sec. 4.1, d_i = -Lambda/|mu| ln(1 - xi));
+  * ``"extruded2d"``: rho/Lambda_i with rho = sqrt(1 - mu_z^2) -- the paper's
+    2D extruded geometry, whose interface distance is the in-plane chord
+    projected on the flight (paper Sec. 4.2, d_i = -Lambda/sqrt(1-mu^2)
+    ln(1 - xi), mu the cosine to the extrusion axis z); the rate then depends
+    on the azimuth psi of the direction around x, mu_z = sqrt(1 - mu^2) sin psi;
   * ``"rod"``: mu = +-1 with weights 1, rate 1/Lambda_i.
-Directions use a double Gauss-Legendre rule on [0,1] and [-1,0] (box3d, slab1d).
+Directions use a double Gauss-Legendre rule on [0,1] and [-1,0] (box3d, slab1d),
+times a Gauss-Legendre rule in psi on [0, pi/2] for extruded2d (the solution
+depends on psi only through sin^2 psi).
 
 Suite I incidence: psi_i(0, mu > 0) = p_i f with f = 1 / sum_{mu_n > 0} w_n mu_n
 (unit incident current, isotropic incident angular flux -- the cosine law of
@@ -43,14 +50,29 @@ from __future__ import annotations
 import numpy as np
 
 
-def directions(kind: str, n_half: int = 32):
-    """(mu, w): direction cosines and weights, sum of weights = 2."""
+def directions(kind: str, n_half: int = 32, n_psi: int = 12):
+    """(mu, w, rate): x direction cosines, weights (sum 2) and the factor that
+    multiplies 1/Lambda in each direction's interface rate."""
     if kind == "rod":
-        return np.array([1.0, -1.0]), np.array([1.0, 1.0])
+        return np.array([1.0, -1.0]), np.array([1.0, 1.0]), np.array([1.0, 1.0])
     x, w = np.polynomial.legendre.leggauss(n_half)
     mu_h = 0.5 * (x + 1.0)
     w_h = 0.5 * w
-    return np.concatenate([mu_h, -mu_h]), np.concatenate([w_h, w_h])
+    mu = np.concatenate([mu_h, -mu_h])
+    wt = np.concatenate([w_h, w_h])
+    if kind == "slab1d":
+        return mu, wt, np.abs(mu)
+    if kind == "box3d":
+        return mu, wt, np.ones_like(mu)
+    if kind == "extruded2d":
+        xp, wp = np.polynomial.legendre.leggauss(n_psi)
+        psi = 0.25 * np.pi * (xp + 1.0)
+        wpsi = wp / 2.0  # normalised to sum 1 over [0, pi/2]
+        MU, PSI = np.meshgrid(mu, psi, indexing="ij")
+        W = np.outer(wt, wpsi)
+        rho = np.sqrt(1.0 - (1.0 - MU ** 2) * np.sin(PSI) ** 2)
+        return MU.ravel(), W.ravel(), rho.ravel()
+    raise ValueError(kind)
 
 
 def _integral_exp(lam, a, b, ref):
@@ -80,7 +102,7 @@ def solve(sigma, lam, c, L, kind: str, nbins: int = 0, n_half: int = 32, source:
     sigma = np.asarray(sigma, dtype=float)
     lam = np.asarray(lam, dtype=float)
     c = np.asarray(c, dtype=float)
-    mu, w = directions(kind, n_half)
+    mu, w, rate = directions(kind, n_half)
     n = mu.size
     K = 2 * n
     p = lam / lam.sum()
@@ -89,10 +111,7 @@ def solve(sigma, lam, c, L, kind: str, nbins: int = 0, n_half: int = 32, source:
         j = 1 - i
         for a in range(n):
             row = i * n + a
-            if kind == "slab1d":
-                ri, rj = abs(mu[a]) / lam[i], abs(mu[a]) / lam[j]
-            else:
-                ri, rj = 1.0 / lam[i], 1.0 / lam[j]
+            ri, rj = rate[a] / lam[i], rate[a] / lam[j]
             C[row, row] -= sigma[i] + ri
             C[row, j * n + a] += rj
             C[row, i * n:(i + 1) * n] += 0.5 * c[i] * sigma[i] * w

@@ -148,8 +148,8 @@ def test_paper_suite1_cls_tables(row):
     """The LP solution equals the expectation of the paper's CLS estimates (Tables 3-5,
     suite I): |LP - CLS| <= 4 sqrt(sigma^2 + (half a printed unit)^2) for R, T and <phi>."""
     r, sig, lam, c = row
-    kind = "box3d" if r["d"] == 3 else "slab1d"
-    out = lp_ado.solve(sig, lam, c, 10.0, kind, n_half=32)
+    kind = {1: "slab1d", 2: "extruded2d", 3: "box3d"}[r["d"]]
+    out = lp_ado.solve(sig, lam, c, 10.0, kind, n_half=16 if r["d"] == 2 else 32)
     for key, ours in (("R", out["R"]), ("T", out["T"]), ("phi", out["total_flux"])):
         val, sd = r[key]
         tol = 4 * math.hypot(float(sd), 0.5 * _printed_unit(val)) + 1e-6 * abs(float(val))
@@ -185,8 +185,8 @@ def test_paper_suite2_cls_tables(row):
     """The LP solution with the uniform isotropic volume source equals the paper's
     suite II CLS estimates (Tables 6-8): leakage L = (T + R)/2 and <phi>."""
     r, sig, lam, c = row
-    kind = "box3d" if r["d"] == 3 else "slab1d"
-    out = lp_ado.solve(sig, lam, c, 10.0, kind, n_half=32, source="volume")
+    kind = {1: "slab1d", 2: "extruded2d", 3: "box3d"}[r["d"]]
+    out = lp_ado.solve(sig, lam, c, 10.0, kind, n_half=16 if r["d"] == 2 else 32, source="volume")
     for key, ours in (("L", out["Lk"]), ("phi", out["total_flux"])):
         val, sd = r[key]
         tol = 4 * math.hypot(float(sd), 0.5 * _printed_unit(val)) + 1e-6 * abs(float(val))
@@ -200,3 +200,19 @@ def test_volume_source_balance_and_symmetry():
     assert out["A_track"] + out["R"] + out["T"] == pytest.approx(1.0, rel=1e-9)
     assert out["R"] == pytest.approx(out["T"], rel=1e-9)
     np.testing.assert_allclose(out["flux"], out["flux"][::-1], rtol=1e-9)
+
+
+def test_extruded_quadrature_converged():
+    a = lp_ado.solve([0.1, 10.0], [1.0, 0.1], [0.9, 0.9], 10.0, "extruded2d", nbins=20, n_half=12)
+    b = lp_ado.solve([0.1, 10.0], [1.0, 0.1], [0.9, 0.9], 10.0, "extruded2d", nbins=20, n_half=20)
+    for k in ("R", "T", "total_flux"):
+        assert a[k] == pytest.approx(b[k], rel=2e-5)
+    assert b["A"] == pytest.approx(b["A_track"], rel=1e-8)
+
+
+def test_extruded_reduces_to_box_without_switching():
+    """Lambda -> infinity: no interfaces, so the projection of the chords no longer
+    matters and the extruded geometry equals the box."""
+    a = lp_ado.solve([0.3, 1.1], [1e9, 3e9], [0.7, 0.4], 5.0, "extruded2d", n_half=12)
+    b = lp_ado.solve([0.3, 1.1], [1e9, 3e9], [0.7, 0.4], 5.0, "box3d", n_half=12)
+    assert a["R"] == pytest.approx(b["R"], rel=1e-6) and a["T"] == pytest.approx(b["T"], rel=1e-6)
