@@ -5,6 +5,10 @@
  * single-speed transport with isotropic scattering through a binary Markov
  * mixture.  Geometries (the `d` argument):
  *   CLS_GEOM_ROD  (1)  rod of length L, directions +-1;
+ *   CLS_GEOM_EXTRUDED (2) the paper's 2D extruded box (Sec. 4.2): x faces leak,
+ *                      y faces reflect, invariant along z; the interface
+ *                      distance is the in-plane chord along the flight,
+ *                      Lambda/sqrt(1 - mu_z^2);
  *   CLS_GEOM_BOX  (3)  3D box of side L (paper Sec. 4.3) with leakage on the
  *                      faces normal to x and specular reflection on the four
  *                      lateral faces (paper Sec. 2);
@@ -40,6 +44,7 @@ extern "C" {
 
 /* ------------------------------------------------------------- geometries */
 #define CLS_GEOM_ROD 1
+#define CLS_GEOM_EXTRUDED 2
 #define CLS_GEOM_BOX 3
 #define CLS_GEOM_SLAB 11
 
@@ -122,7 +127,7 @@ typedef struct {
  *                    picked at the source with p_i = Lambda_i / (Lambda_0 + Lambda_1)
  *   c0, c1           scattering probabilities c_i = Sigma_s,i / Sigma_i in [0, 1]
  *   L                rod length / box side, > 0
- *   d                CLS_GEOM_ROD, CLS_GEOM_BOX or CLS_GEOM_SLAB
+ *   d                CLS_GEOM_ROD, CLS_GEOM_EXTRUDED, CLS_GEOM_BOX or CLS_GEOM_SLAB
  *   nbins            uniform flux bins along x, 1..4096
  * Selects the current CUDA device, allocates the device tallies (library-
  * owned, freed by cls_destroy) and zeroes them.

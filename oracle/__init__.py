@@ -50,7 +50,7 @@ class Case:
     c0: float
     c1: float
     L: float
-    d: int          # 1 = rod (directions +-1), 3 = box with reflective lateral faces, 11 = slab
+    d: int          # 1 = rod (directions +-1), 2 = extruded 2D, 3 = box with reflective lateral faces, 11 = slab
     nbins: int
     source: int = 0  # 0 = incident flux on x = 0 (suite I), 1 = uniform isotropic volume source (suite II)
 

@@ -26,6 +26,12 @@
  *     box (x; box also y, z), direction isotropic (rod: +-1 with probability
  *     1/2; slab: mu = 2 xi - 1; box: mu = 2 xi - 1, phi = 2 pi xi', omega =
  *     (sqrt(1-mu^2) cos phi, sqrt(1-mu^2) sin phi, mu)), then the label.
+ *   - Extruded 2D (d = 2, paper Sec. 4.2): the box's x and y faces only (the
+ *     geometry is invariant along z); the 3D direction omega of the box, with
+ *     mu = omega_z the cosine to the extrusion axis; interface distance
+ *     d_i = -Lambda/sqrt(1 - mu^2) ln(1 - xi), the in-plane chord projected on
+ *     the flight.  Sources draw no z (suite I: y, mu', phi'; suite II: x, y,
+ *     mu, phi).
  *   - Slab (d = 11, the paper's d = 1, Sec. 4.1): direction cosine mu with
  *     respect to x; incident mu = sqrt(xi); interface distance projected,
  *     d_i = -(Lambda/|mu|) ln(1 - xi); scattering mu = 2 xi - 1; x faces only.
@@ -57,7 +63,7 @@ typedef struct {
     double lambda[2]; /* mean chord lengths Lambda_0, Lambda_1            */
     double c[2];      /* scattering probability c_i = Sigma_s,i / Sigma_i */
     double L;         /* rod length / box side                           */
-    int32_t d;        /* 1 = rod (directions +-1), 3 = box, 11 = slab    */
+    int32_t d;        /* 1 rod (directions +-1), 2 extruded 2D, 3 box, 11 slab */
     int32_t nbins;    /* uniform x bins for the flux tally               */
     int32_t source;   /* 0 = incident flux on x = 0 (suite I),           */
                       /* 1 = uniform isotropic volume source (suite II)   */
@@ -243,9 +249,10 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
     /* source: position and direction first, then the material label */
     if (cs->source == 1) {
         r[0] = L * next_u(&s);
-        if (cs->d == 3) {
+        if (cs->d == 3 || cs->d == 2) {
             r[1] = L * next_u(&s);
-            r[2] = L * next_u(&s);
+            if (cs->d == 3)
+                r[2] = L * next_u(&s);
             double mu = 2.0 * next_u(&s) - 1.0;
             double ph = (2.0 * ORC_PI) * next_u(&s);
             double st = sqrt(1.0 - mu * mu);
@@ -259,9 +266,10 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
         }
     } else if (cs->d == 11) {
         w[0] = sqrt(next_u(&s)); /* cosine law mu = sqrt(xi) */
-    } else if (cs->d == 3) {
+    } else if (cs->d == 3 || cs->d == 2) {
         r[1] = L * next_u(&s);
-        r[2] = L * next_u(&s);
+        if (cs->d == 3)
+            r[2] = L * next_u(&s);
         double mu = sqrt(next_u(&s));
         double ph = (2.0 * ORC_PI) * next_u(&s);
         double st = sqrt(1.0 - mu * mu);
@@ -288,6 +296,8 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
         double l_i = -cs->lambda[m] * log(1.0 - u_i);
         if (cs->d == 11)
             l_i = l_i / fabs(w[0]); /* projection of the chord on x */
+        else if (cs->d == 2)
+            l_i = l_i / sqrt(1.0 - w[2] * w[2]); /* in-plane chord along the flight */
 
         /* boundary distance: x faces, then (box) the lateral faces */
         double l_b = INFINITY;
@@ -296,8 +306,9 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
         else if (w[0] < 0.0) { l_b = (0.0 - r[0]) / w[0]; face = 0; }
         if (l_b < 0.0) l_b = 0.0;
         double l_lat[3] = {INFINITY, INFINITY, INFINITY};
-        if (cs->d == 3) {
-            for (int a = 1; a < 3; a++) {
+        if (cs->d == 3 || cs->d == 2) {
+            int na = (cs->d == 3) ? 3 : 2; /* extruded: y faces only */
+            for (int a = 1; a < na; a++) {
                 if (w[a] > 0.0) l_lat[a] = (L - r[a]) / w[a];
                 else if (w[a] < 0.0) l_lat[a] = (0.0 - r[a]) / w[a];
                 if (l_lat[a] < 0.0) l_lat[a] = 0.0;
@@ -313,7 +324,8 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
                 tally_flight(tal, x0, xf, w[0], l_b, m);
                 r[0] = xf;
                 r[1] += l_b * w[1];
-                r[2] += l_b * w[2];
+                if (cs->d == 3)
+                    r[2] += l_b * w[2];
                 if (face == 0) { cnt->nR++; outcome = 0; trace_event(tr, EV_LEAK_X0, &s, r, w, m, l_b); }
                 else { cnt->nT++; outcome = 1; trace_event(tr, EV_LEAK_XL, &s, r, w, m, l_b); }
             } else {
@@ -324,7 +336,7 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
                     if (l_lat[a] == l_b) {
                         r[a] = (w[a] > 0.0) ? L : 0.0; /* snap onto the face */
                         w[a] = -w[a];                  /* specular reflection */
-                    } else {
+                    } else if (a == 1 || cs->d == 3) {
                         r[a] += l_b * w[a];
                     }
                 }
@@ -338,7 +350,8 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
             tally_flight(tal, x0, x1, w[0], l, m);
             r[0] = x1;
             r[1] += l * w[1];
-            r[2] += l * w[2];
+            if (cs->d == 3)
+                r[2] += l * w[2];
             if (l_c <= l_i) {
                 /* collision: scatter with probability c_m, else absorb */
                 cnt->n_coll++;
@@ -380,7 +393,7 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
 static int check_case(const orc_case_t *cs)
 {
     if (!cs) return -1;
-    if (cs->d != 1 && cs->d != 3 && cs->d != 11) return -1;
+    if (cs->d != 1 && cs->d != 2 && cs->d != 3 && cs->d != 11) return -1;
     if (cs->nbins < 1) return -1;
     if (cs->source != 0 && cs->source != 1) return -1;
     if (!(cs->L > 0.0)) return -1;

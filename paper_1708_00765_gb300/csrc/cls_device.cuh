@@ -229,9 +229,9 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint
     if (cp.source == 1) {  // suite II: uniform position, isotropic direction
         const P L = R::L(cp);
         s.r[0] = L * draw(s, key);
-        if (cp.d == 3) {
+        if (cp.d == 3 || cp.d == 2) {
             s.r[1] = L * draw(s, key);
-            s.r[2] = L * draw(s, key);
+            if (cp.d == 3) s.r[2] = L * draw(s, key);
             const P mu = P(2) * draw(s, key) - P(1);
             P sn, cs;
             R::sincos_2pi(draw(s, key), &sn, &cs);
@@ -250,10 +250,10 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint
             s.iw[1] = R::inf();
             s.iw[2] = R::inf();
         }
-    } else if (cp.d == 3) {
+    } else if (cp.d == 3 || cp.d == 2) {
         const P L = R::L(cp);
         s.r[1] = L * draw(s, key);
-        s.r[2] = L * draw(s, key);
+        if (cp.d == 3) s.r[2] = L * draw(s, key);
         const P mu = sqrt(draw(s, key));  // cosine law mu' = sqrt(xi)
         P sn, cs;
         R::sincos_2pi(draw(s, key), &sn, &cs);
@@ -364,6 +364,7 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
     const P om_i = draw_one_minus(s, key);
     P l_i = R::interface(cp, m, om_i);
     if (cp.d == 11) l_i *= fabs(s.iw[0]);  // slab: the chord projected on x, Lambda/|mu|
+    else if (cp.d == 2) l_i /= sqrt(P(1) - s.w[2] * s.w[2]);  // extruded: in-plane chord along the flight
     l_i = R::nonneg(l_i);
 
     // boundary distance: x faces, then the lateral faces of the box
@@ -378,18 +379,21 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
     }
     l_b = R::nonneg(l_b);
     P l_y = INF, l_z = INF;
-    if (cp.d == 3) {
+    const bool box = cp.d == 3;
+    if (box || cp.d == 2) {  // lateral faces: y (and z in the box; the extruded geometry has none)
         if (R::pos(s.w[1])) l_y = R::nonneg((L - s.r[1]) * s.iw[1]);
         else if (R::neg(s.w[1])) l_y = R::nonneg((P(0) - s.r[1]) * s.iw[1]);
         if (R::lt(l_y, l_b)) {
             l_b = l_y;
             face = 2;
         }
-        if (R::pos(s.w[2])) l_z = R::nonneg((L - s.r[2]) * s.iw[2]);
-        else if (R::neg(s.w[2])) l_z = R::nonneg((P(0) - s.r[2]) * s.iw[2]);
-        if (R::lt(l_z, l_b)) {
-            l_b = l_z;
-            face = 2;
+        if (box) {
+            if (R::pos(s.w[2])) l_z = R::nonneg((L - s.r[2]) * s.iw[2]);
+            else if (R::neg(s.w[2])) l_z = R::nonneg((P(0) - s.r[2]) * s.iw[2]);
+            if (R::lt(l_z, l_b)) {
+                l_b = l_z;
+                face = 2;
+            }
         }
     }
 
@@ -398,10 +402,8 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
             const P xf = (face == 0) ? P(0) : L;
             plan_flight(f, s, cp, s.r[0], xf, l_b, m);
             s.r[0] = xf;
-            if (cp.d == 3) {
-                s.r[1] += l_b * s.w[1];
-                s.r[2] += l_b * s.w[2];
-            }
+            if (box || cp.d == 2) s.r[1] += l_b * s.w[1];
+            if (box) s.r[2] += l_b * s.w[2];
             const int ev = (face == 0) ? EV_LEAK_X0 : EV_LEAK_XL;
             trace_row<P, TRACE>(tr, ev, s, (double)l_b);
             return ev;
@@ -420,7 +422,7 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
             s.r[2] = R::pos(s.w[2]) ? L : P(0);
             s.w[2] = -s.w[2];
             s.iw[2] = -s.iw[2];
-        } else {
+        } else if (box) {
             s.r[2] += l_b * s.w[2];
         }
         ++s.n_refl;
@@ -433,10 +435,8 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
     const P x1 = s.r[0] + l * s.w[0];
     plan_flight(f, s, cp, s.r[0], x1, l, m);
     s.r[0] = x1;
-    if (cp.d == 3) {
-        s.r[1] += l * s.w[1];
-        s.r[2] += l * s.w[2];
-    }
+    if (box || cp.d == 2) s.r[1] += l * s.w[1];
+    if (box) s.r[2] += l * s.w[2];
     if (coll) {
         ++s.n_coll;
         if (draw_below(s, key, R::thr_c53(cp, m), R::thr_c24(cp, m))) {

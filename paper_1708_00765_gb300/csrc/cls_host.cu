@@ -106,7 +106,7 @@ int validate(const double *p) {
     if (!(finite(l0) && l0 > 0 && finite(l1) && l1 > 0)) return CLS_E_INVAL;
     if (!(c0 >= 0 && c0 <= 1 && c1 >= 0 && c1 <= 1)) return CLS_E_INVAL;
     if (!(finite(L) && L > 0)) return CLS_E_INVAL;
-    if (!(d == 1.0 || d == 3.0 || d == 11.0)) return CLS_E_INVAL;
+    if (!(d == 1.0 || d == 2.0 || d == 3.0 || d == 11.0)) return CLS_E_INVAL;
     if (!(nb >= 1 && nb <= kMaxBins && nb == std::floor(nb))) return CLS_E_INVAL;
     return CLS_OK;
 }

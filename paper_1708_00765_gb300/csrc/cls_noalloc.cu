@@ -69,7 +69,7 @@ bool valid_case(const double *p) {
     const double s0 = p[0], s1 = p[1], l0 = p[2], l1 = p[3], c0 = p[4], c1 = p[5], L = p[6], d = p[7], nb = p[8];
     auto fin = [](double v) { return v == v && v - v == 0.0; };
     return fin(s0) && s0 >= 0 && fin(s1) && s1 >= 0 && fin(l0) && l0 > 0 && fin(l1) && l1 > 0 && c0 >= 0 &&
-           c0 <= 1 && c1 >= 0 && c1 <= 1 && fin(L) && L > 0 && (d == 1.0 || d == 3.0 || d == 11.0) && nb >= 1 && nb <= 4096 &&
+           c0 <= 1 && c1 >= 0 && c1 <= 1 && fin(L) && L > 0 && (d == 1.0 || d == 2.0 || d == 3.0 || d == 11.0) && nb >= 1 && nb <= 4096 &&
            nb == (double)(int)nb;
 }
 

@@ -28,12 +28,12 @@ SUITE_MATERIALS = {
 SUITE_SCATTERING = {"a": (0.0, 1.0), "b": (1.0, 0.0), "c": (0.9, 0.9)}
 
 
-GEOM_ROD, GEOM_BOX, GEOM_SLAB = 1, 3, 11
+GEOM_ROD, GEOM_EXTRUDED, GEOM_BOX, GEOM_SLAB = 1, 2, 3, 11
 
 
 def suite_case(name: str, d: int = 3, L: float = 10.0, nbins: int = 100):
     """Benchmark configuration like '1a' (paper Tables 1-2) as a case tuple;
-    d = 3 for the box, 11 for the paper's d = 1 slab."""
+    d = 3 for the box, 2 for the extruded 2D box, 11 for the paper's d = 1 slab."""
     (s0, s1), (l0, l1) = SUITE_MATERIALS[name[0]]
     c0, c1 = SUITE_SCATTERING[name[1]]
     return (s0, s1, l0, l1, c0, c1, L, d, nbins)

@@ -90,7 +90,8 @@ def test_uniform_mapping_matches_oracle():
 # -------------------------------------------------------------- traces
 
 @pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10, workloads.suite_case("1c", nbins=10),
-                                    workloads.suite_case("3c", d=11, nbins=10)])
+                                    workloads.suite_case("3c", d=11, nbins=10),
+                                    workloads.suite_case("2c", d=2, nbins=10)])
 def test_fp64_traces_replay_the_oracle(params):
     prob = cls.Problem(params)
     case = ocase(params)
@@ -125,6 +126,7 @@ def test_box_parity_ragged(n):
 
 @pytest.mark.parametrize("params", [
     workloads.suite_case("1c", d=11, nbins=64),          # the paper's slab
+    workloads.suite_case("2a", d=2, nbins=40),           # the paper's extruded 2D box
     (0.7, 3.0, 0.4, 2.0, 0.8, 0.3, 3.0, 11, 13),         # slab, odd bin count
     (0.0, 2.0, 0.3, 0.7, 0.5, 0.5, 2.0, 3, 1),          # Sigma_0 = 0, one bin
     (1.0, 1.0, 1e-3, 2e-3, 1.0, 0.0, 1.0, 1, 4096),     # c = 1 / 0, maximum bins, tiny chords
@@ -345,14 +347,14 @@ def _paper_rows(d=3):
         sig = [float(Fraction(v)) for v in m[r["case"][0]]["sigma"]]
         lam = [float(Fraction(v)) for v in m[r["case"][0]]["lambda"]]
         c = [float(v) for v in m[r["case"][1]]["c"]]
-        out.append((r, (sig[0], sig[1], lam[0], lam[1], c[0], c[1], 10.0, 3 if d == 3 else 11, 100)))
+        out.append((r, (sig[0], sig[1], lam[0], lam[1], c[0], c[1], 10.0, {1: 11, 2: 2, 3: 3}[d], 100)))
     return out
 
 
-@pytest.mark.parametrize("row,params", _paper_rows(3) + _paper_rows(1),
+@pytest.mark.parametrize("row,params", _paper_rows(3) + _paper_rows(1) + _paper_rows(2),
                          ids=lambda v: f"{v['case']}-d{v['d']}" if isinstance(v, dict) else "")
 def test_fp64_reproduces_paper_tables(row, params):
-    """Tables 3-5, d = 3 (box) and d = 1 (slab): the paper's Tripoli-4 CLS results
+    """Tables 3-5, d = 3 (box), d = 2 (extruded) and d = 1 (slab): the paper's Tripoli-4 CLS results
     (1e9 histories) against 1e8 FP64 GPU histories, within 4 combined standard
     errors (Eq. combined_var)."""
     prob = cls.Problem(params)
@@ -369,7 +371,8 @@ def test_fp64_reproduces_paper_tables(row, params):
 
 # ------------------------------------------------------ suite II source
 
-VOLUME_CASES = [workloads.ROD_L10, workloads.BOX_L10, workloads.suite_case("2c", d=11, nbins=30)]
+VOLUME_CASES = [workloads.ROD_L10, workloads.BOX_L10, workloads.suite_case("2c", d=11, nbins=30),
+                workloads.suite_case("1b", d=2, nbins=30)]
 
 
 @pytest.mark.parametrize("params", VOLUME_CASES)
@@ -415,14 +418,14 @@ def _paper_rows2(d):
         sig = [float(Fraction(v)) for v in m[r["case"][0]]["sigma"]]
         lam = [float(Fraction(v)) for v in m[r["case"][0]]["lambda"]]
         c = [float(v) for v in m[r["case"][1]]["c"]]
-        out.append((r, (sig[0], sig[1], lam[0], lam[1], c[0], c[1], 10.0, 3 if d == 3 else 11, 100)))
+        out.append((r, (sig[0], sig[1], lam[0], lam[1], c[0], c[1], 10.0, {1: 11, 2: 2, 3: 3}[d], 100)))
     return out
 
 
-@pytest.mark.parametrize("row,params", _paper_rows2(3) + _paper_rows2(1),
+@pytest.mark.parametrize("row,params", _paper_rows2(3) + _paper_rows2(1) + _paper_rows2(2),
                          ids=lambda v: f"{v['case']}-d{v['d']}" if isinstance(v, dict) else "")
 def test_fp64_reproduces_paper_suite2_tables(row, params):
-    """Tables 6-8 (suite II), d = 3 and d = 1: leakage L = (T + R)/2 and <phi> from 1e8
+    """Tables 6-8 (suite II), d = 3, 2 and 1: leakage L = (T + R)/2 and <phi> from 1e8
     FP64 GPU histories against the paper's 1e9-history CLS values, 4 combined sigma."""
     prob = cls.Problem(params)
     prob.set_option("source", "volume")

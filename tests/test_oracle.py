@@ -22,6 +22,7 @@ from oracle import lp_ado
 C1 = oracle.Case(0.5, 5.0, 2.0, 0.5, 0.5, 0.9, 10.0, 1, 100)           # rod, L = 10
 C2 = oracle.Case(0.1, 10.0, 1.0, 0.1, 0.99, 0.99, 10.0, 3, 200)        # box, L = 10
 SLAB = oracle.Case(10 / 99, 100 / 11, 99 / 100, 11 / 100, 0.9, 0.9, 10.0, 11, 50)  # paper case 1c, d = 1
+EXT = oracle.Case(10 / 99, 100 / 11, 99 / 10, 11 / 10, 0.9, 0.9, 10.0, 2, 40)      # paper case 2c, d = 2
 HERE = os.path.dirname(__file__)
 
 
@@ -87,7 +88,7 @@ def test_invalid_cases_rejected():
     for bad in (oracle.Case(0.5, 5.0, 0.0, 0.5, 0.5, 0.9, 10.0, 1, 100),
                 oracle.Case(0.5, 5.0, 2.0, 0.5, 1.5, 0.9, 10.0, 1, 100),
                 oracle.Case(-1, 5.0, 2.0, 0.5, 0.5, 0.9, 10.0, 1, 100),
-                oracle.Case(0.5, 5.0, 2.0, 0.5, 0.5, 0.9, 10.0, 2, 100),
+                oracle.Case(0.5, 5.0, 2.0, 0.5, 0.5, 0.9, 10.0, 4, 100),
                 oracle.Case(0.5, 5.0, 2.0, 0.5, 0.5, 0.9, 0.0, 1, 100),
                 oracle.Case(0.5, 5.0, 2.0, 0.5, 0.5, 0.9, 10.0, 1, 0)):
         with pytest.raises(ValueError):
@@ -100,10 +101,10 @@ def expected_draws(case, rows):
     """Draw accounting of Algorithm A: source (3D: y, z, mu', phi'), material label,
     two distances per event, one absorb/scatter decision per collision, and the
     scattering direction (rod 1 draw, 3D 2 draws)."""
-    if case.source == 1:  # suite II: position (x; box: y, z), then direction
-        n = {3: 5, 11: 2}.get(case.d, 2) + 1
+    if case.source == 1:  # suite II: position (x; box: y, z; extruded: y), then direction
+        n = {3: 5, 2: 4, 11: 2}.get(case.d, 2) + 1
     else:
-        n = {3: 4, 11: 1}.get(case.d, 0) + 1
+        n = {3: 4, 2: 3, 11: 1}.get(case.d, 0) + 1
     for ev in rows[:, 0].astype(int):
         if ev == 6:
             continue
@@ -111,7 +112,7 @@ def expected_draws(case, rows):
         if ev in (3, 4):
             n += 1
         if ev == 3:
-            n += 2 if case.d == 3 else 1
+            n += 2 if case.d in (2, 3) else 1
     return n
 
 
@@ -119,7 +120,7 @@ VOL = [oracle.Case(*[getattr(c, f) for f in ("sigma0", "sigma1", "lambda0", "lam
                                              "nbins")], source=1) for c in (C1, C2, SLAB)]
 
 
-@pytest.mark.parametrize("case", [C1, C2, SLAB] + VOL)
+@pytest.mark.parametrize("case", [C1, C2, SLAB, EXT] + VOL + [oracle.Case(*list(EXT.__dict__.values())[:9], source=1)])
 def test_trace_is_a_valid_walk(case):
     for h in range(40):
         rows, cnt = oracle.trace(case, 3, h)
@@ -132,6 +133,8 @@ def test_trace_is_a_valid_walk(case):
         assert rows[:, 9].sum() == pytest.approx(cnt["sum_t"], rel=1e-12)
         r = rows[:, 2:5]
         assert np.all(r >= -1e-9 * case.L) and np.all(r <= case.L * (1 + 1e-9))
+        if case.d == 2:  # invariant along z: z is never tracked
+            assert np.all(rows[:, 4] == 0.0)
         if case.d == 11:  # the slab carries only the direction cosine mu
             assert np.all(np.abs(rows[:, 5]) <= 1.0) and np.all(rows[:, 6:8] == 0.0)
         else:
@@ -207,6 +210,17 @@ def test_volume_source_matches_lp_solution(case, kind):
     assert abs(res["Lk"] - lp["Lk"]) < 4 * res["sigma_Lk"]
     # the uniform source leaks through both faces alike
     assert abs(res["R"] - res["T"]) < 4 * math.hypot(res["sigma_R"], res["sigma_T"])
+
+
+@pytest.mark.parametrize("source", [0, 1])
+def test_extruded_matches_lp_solution(source):
+    """The paper's extruded 2D geometry (Sec. 4.2) against the LP solution with the
+    projected in-plane chord (pinned by the paper's d = 2 rows)."""
+    case = oracle.Case(*list(EXT.__dict__.values())[:9], source=source)
+    res = oracle.finalize(oracle.run_parallel(case, 12, 0, 80_000), case)
+    lp = lp_ado.solve([case.sigma0, case.sigma1], [case.lambda0, case.lambda1], [case.c0, case.c1], case.L,
+                      "extruded2d", case.nbins, n_half=12, source="volume" if source else "incident")
+    assert_matches_lp(res, lp)
 
 
 def test_slab_is_not_the_box():
