@@ -41,7 +41,7 @@ FP32_WARP_INST_PER_EVENT = 42.8
 # DRAM bytes per full-size FP64 launch (1e8 histories) from a one-pass ncu
 # capture of the current kernel (profiles/history_kernel_box_L10.md); set to
 # None whenever the kernel changes until it is captured again.
-FP64_DRAM_BYTES_PER_LAUNCH = 918272
+FP64_DRAM_BYTES_PER_LAUNCH = None
 SM_COUNT = 152           # GB300
 DFMA_PER_SM_CLK = 2      # ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / 152 SMs
 ISSUE_PER_SM_CLK = 4     # one warp instruction per scheduler per clock, 4 schedulers
@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--histories", type=int, default=None, help="override histories per step (tests only)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-tracking arm")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 arm (profiling only)")
+    ap.add_argument("--no-projected", action="store_true",
+                    help="skip the arms that walk the box by its x-marginal (geometry 13)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="box", choices=["box", "diffusive", "batch"],
                     help="box: L=10 box (default, the headline line); diffusive: L=100 box, c=0.999, "
@@ -348,10 +350,12 @@ def main():
 
     results = {}
     arms = ([] if args.no_fp64 else ["fp64"]) + ([] if args.no_fp32 else ["fp32"])
+    if not args.no_projected and not (args.no_fp64 or args.no_fp32):
+        arms += ["fp64_x", "fp32_x"]
     clocks = None
     for arm in arms:
-        prob = cls.Problem(params)
-        prob.set_option("precision", arm)
+        prob = cls.Problem(workloads.BOX_L10_X if arm.endswith("_x") else params)
+        prob.set_option("precision", arm[:4])
         # rank r walks its own history ids: warm-up runs come first, the timed runs follow
         base = rank * (args.warmup + args.steps) * n
         if base:
@@ -456,6 +460,12 @@ def main():
             line["fp32"] = r32
             if r32["fom_total_flux"] and r64["fom_total_flux"]:
                 line["fom_ratio_fp32_over_fp64"] = r32["fom_total_flux"] / r64["fom_total_flux"]
+        for arm in ("fp64_x", "fp32_x"):
+            if arm in results:
+                rx = dict(results[arm])
+                rx["note"] = "same box walked by its x-marginal (geometry 13): same law, fewer draws"
+                line[arm] = rx
+                line["fom_ratio_" + arm + "_over_fp64"] = rx["fom_total_flux"] / r64["fom_total_flux"]
         if not args.no_cpu_baseline and world == 1:
             rate, ns, dt, used = oracle_rate(params, 10.0, os.cpu_count() or 1, first=10**12)
             line["cpu_baseline"] = {"value": rate, "unit": "histories/s", "cores": used, "kind": "oracle",

@@ -14,7 +14,12 @@
  *                      lateral faces (paper Sec. 2);
  *   CLS_GEOM_SLAB (11) the paper's d = 1 slab (Sec. 4.1): continuous direction
  *                      cosine mu, interface distance projected on x
- *                      (Lambda/|mu|), leakage on both faces.
+ *                      (Lambda/|mu|), leakage on both faces;
+ *   CLS_GEOM_BOX_X (13) the box's x-marginal: since specular lateral faces keep
+ *                      omega_x, the box's tallies have the law of a walk in
+ *                      mu = omega_x alone (scatter mu = 2 xi - 1, chords along
+ *                      the flight, no lateral events).  Same law as
+ *                      CLS_GEOM_BOX, fewer draws, not draw-for-draw equal.
  * Sources (CLS_OPT_SOURCE): the isotropic incident flux on x = 0 of benchmark
  * suite I (cosine law mu = sqrt(xi), paper Sec. 4.1 / 4.3, the default), or
  * the uniform isotropic volume source of suite II.  Estimators: reflection R = J(x=0),
@@ -47,6 +52,7 @@ extern "C" {
 #define CLS_GEOM_EXTRUDED 2
 #define CLS_GEOM_BOX 3
 #define CLS_GEOM_SLAB 11
+#define CLS_GEOM_BOX_X 13
 
 /* ------------------------------------------------------------ error codes */
 #define CLS_OK 0
@@ -127,7 +133,8 @@ typedef struct {
  *                    picked at the source with p_i = Lambda_i / (Lambda_0 + Lambda_1)
  *   c0, c1           scattering probabilities c_i = Sigma_s,i / Sigma_i in [0, 1]
  *   L                rod length / box side, > 0
- *   d                CLS_GEOM_ROD, CLS_GEOM_EXTRUDED, CLS_GEOM_BOX or CLS_GEOM_SLAB
+ *   d                CLS_GEOM_ROD, CLS_GEOM_EXTRUDED, CLS_GEOM_BOX, CLS_GEOM_SLAB or
+ *                    CLS_GEOM_BOX_X
  *   nbins            uniform flux bins along x, 1..4096
  * Selects the current CUDA device, allocates the device tallies (library-
  * owned, freed by cls_destroy) and zeroes them.

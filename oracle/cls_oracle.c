@@ -32,6 +32,11 @@
  *     d_i = -Lambda/sqrt(1 - mu^2) ln(1 - xi), the in-plane chord projected on
  *     the flight.  Sources draw no z (suite I: y, mu', phi'; suite II: x, y,
  *     mu, phi).
+ *   - Box projected on x (d = 13): the box's x-marginal.  Specular lateral
+ *     faces keep omega_x, and CLS chords are drawn along the flight, so the
+ *     tallies have the law of a walk in mu = omega_x alone: incident
+ *     mu = sqrt(xi), volume source mu = 2 xi - 1, scattering mu = 2 xi - 1 (the
+ *     x cosine of an isotropic direction), chords not projected, x faces only.
  *   - Slab (d = 11, the paper's d = 1, Sec. 4.1): direction cosine mu with
  *     respect to x; incident mu = sqrt(xi); interface distance projected,
  *     d_i = -(Lambda/|mu|) ln(1 - xi); scattering mu = 2 xi - 1; x faces only.
@@ -63,7 +68,7 @@ typedef struct {
     double lambda[2]; /* mean chord lengths Lambda_0, Lambda_1            */
     double c[2];      /* scattering probability c_i = Sigma_s,i / Sigma_i */
     double L;         /* rod length / box side                           */
-    int32_t d;        /* 1 rod (directions +-1), 2 extruded 2D, 3 box, 11 slab */
+    int32_t d;        /* 1 rod, 2 extruded 2D, 3 box, 11 slab, 13 box (x only) */
     int32_t nbins;    /* uniform x bins for the flux tally               */
     int32_t source;   /* 0 = incident flux on x = 0 (suite I),           */
                       /* 1 = uniform isotropic volume source (suite II)   */
@@ -259,12 +264,12 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
             w[0] = st * cos(ph);
             w[1] = st * sin(ph);
             w[2] = mu;
-        } else if (cs->d == 11) {
+        } else if (cs->d == 11 || cs->d == 13) {
             w[0] = 2.0 * next_u(&s) - 1.0;
         } else {
             w[0] = (next_u(&s) < 0.5) ? 1.0 : -1.0;
         }
-    } else if (cs->d == 11) {
+    } else if (cs->d == 11 || cs->d == 13) {
         w[0] = sqrt(next_u(&s)); /* cosine law mu = sqrt(xi) */
     } else if (cs->d == 3 || cs->d == 2) {
         r[1] = L * next_u(&s);
@@ -358,7 +363,7 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
                 if (next_u(&s) < cs->c[m]) {
                     if (cs->d == 1) {
                         w[0] = (next_u(&s) < 0.5) ? 1.0 : -1.0;
-                    } else if (cs->d == 11) {
+                    } else if (cs->d == 11 || cs->d == 13) {
                         w[0] = 2.0 * next_u(&s) - 1.0;
                     } else {
                         double mu = 2.0 * next_u(&s) - 1.0;
@@ -393,7 +398,7 @@ static int run_history(const orc_case_t *cs, uint32_t case_id, uint64_t seed, ui
 static int check_case(const orc_case_t *cs)
 {
     if (!cs) return -1;
-    if (cs->d != 1 && cs->d != 2 && cs->d != 3 && cs->d != 11) return -1;
+    if (cs->d != 1 && cs->d != 2 && cs->d != 3 && cs->d != 11 && cs->d != 13) return -1;
     if (cs->nbins < 1) return -1;
     if (cs->source != 0 && cs->source != 1) return -1;
     if (!(cs->L > 0.0)) return -1;

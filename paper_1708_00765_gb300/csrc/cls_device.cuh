@@ -202,6 +202,14 @@ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
     return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
+// Geometry of a case: G is a compile-time geometry code (1, 2, 3, 11, 13) for
+// launches whose cases share one geometry, 0 to read it from the case.  A
+// fixed G folds every geometry branch of the walk away.
+template <int G>
+__device__ __forceinline__ int geometry(const CaseParams &cp) {
+    return G != 0 ? G : cp.d;
+}
+
 template <typename P>
 __device__ __forceinline__ void set_direction(History<P> &s, P wx, P wy, P wz) {
     using R = Real<P>;
@@ -214,9 +222,10 @@ __device__ __forceinline__ void set_direction(History<P> &s, P wx, P wy, P wz) {
 }
 
 // Source: position and direction first, then the material label.
-template <typename P>
+template <typename P, int G = 0>
 __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint2 key, uint64_t h) {
     using R = Real<P>;
+    const int gd = geometry<G>(cp);
     s.h_lo = (uint32_t)h;
     s.h_hi = (uint32_t)(h >> 32);
     s.cid = cp.case_id;
@@ -229,15 +238,15 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint
     if (cp.source == 1) {  // suite II: uniform position, isotropic direction
         const P L = R::L(cp);
         s.r[0] = L * draw(s, key);
-        if (cp.d == 3 || cp.d == 2) {
+        if (gd == 3 || gd == 2) {
             s.r[1] = L * draw(s, key);
-            if (cp.d == 3) s.r[2] = L * draw(s, key);
+            if (gd == 3) s.r[2] = L * draw(s, key);
             const P mu = P(2) * draw(s, key) - P(1);
             P sn, cs;
             R::sincos_2pi(draw(s, key), &sn, &cs);
             const P st = sqrt(P(1) - mu * mu);
             set_direction(s, st * cs, st * sn, mu);
-        } else if (cp.d == 11) {
+        } else if (gd == 11 || gd == 13) {
             set_direction(s, P(2) * draw(s, key) - P(1), P(0), P(0));
         } else {
             uint32_t hi, lo;
@@ -250,17 +259,17 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint
             s.iw[1] = R::inf();
             s.iw[2] = R::inf();
         }
-    } else if (cp.d == 3 || cp.d == 2) {
+    } else if (gd == 3 || gd == 2) {
         const P L = R::L(cp);
         s.r[1] = L * draw(s, key);
-        if (cp.d == 3) s.r[2] = L * draw(s, key);
+        if (gd == 3) s.r[2] = L * draw(s, key);
         const P mu = sqrt(draw(s, key));  // cosine law mu' = sqrt(xi)
         P sn, cs;
         R::sincos_2pi(draw(s, key), &sn, &cs);
         const P st = sqrt(P(1) - mu * mu);
         set_direction(s, mu, st * cs, st * sn);
-    } else if (cp.d == 11) {
-        set_direction(s, sqrt(draw(s, key)), P(0), P(0));  // slab: mu = sqrt(xi)
+    } else if (gd == 11 || gd == 13) {
+        set_direction(s, sqrt(draw(s, key)), P(0), P(0));  // slab, projected box: mu = sqrt(xi)
     } else {
         s.w[0] = P(1);
         s.w[1] = P(0);
@@ -343,10 +352,11 @@ __device__ __forceinline__ void plan_flight(Flight<P> &f, History<P> &s, const C
 // One event of Algorithm A.  Fills the flight to score and returns -1 while
 // the history continues, else the terminating event (EV_LEAK_X0, EV_LEAK_XL,
 // EV_ABSORB, EV_CAPPED).
-template <typename P, bool TRACE>
+template <typename P, bool TRACE, int G = 0>
 __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 key, uint32_t max_events,
                                     Flight<P> &f, TraceSink *tr) {
     using R = Real<P>;
+    const int gd = geometry<G>(cp);
     f.k0 = 0;
     f.k1 = -1;
     if (s.events == max_events) {
@@ -363,8 +373,8 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
     const P l_c = (R::sigma(cp, m) > P(0)) ? R::nonneg(R::collision(cp, m, om_c)) : INF;
     const P om_i = draw_one_minus(s, key);
     P l_i = R::interface(cp, m, om_i);
-    if (cp.d == 11) l_i *= fabs(s.iw[0]);  // slab: the chord projected on x, Lambda/|mu|
-    else if (cp.d == 2) l_i /= sqrt(P(1) - s.w[2] * s.w[2]);  // extruded: in-plane chord along the flight
+    if (gd == 11) l_i *= fabs(s.iw[0]);  // slab: the chord projected on x, Lambda/|mu|
+    else if (gd == 2) l_i /= sqrt(P(1) - s.w[2] * s.w[2]);  // extruded: in-plane chord along the flight
     l_i = R::nonneg(l_i);
 
     // boundary distance: x faces, then the lateral faces of the box
@@ -379,8 +389,8 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
     }
     l_b = R::nonneg(l_b);
     P l_y = INF, l_z = INF;
-    const bool box = cp.d == 3;
-    if (box || cp.d == 2) {  // lateral faces: y (and z in the box; the extruded geometry has none)
+    const bool box = gd == 3;
+    if (box || gd == 2) {  // lateral faces: y (and z in the box; the extruded geometry has none)
         if (R::pos(s.w[1])) l_y = R::nonneg((L - s.r[1]) * s.iw[1]);
         else if (R::neg(s.w[1])) l_y = R::nonneg((P(0) - s.r[1]) * s.iw[1]);
         if (R::lt(l_y, l_b)) {
@@ -402,7 +412,7 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
             const P xf = (face == 0) ? P(0) : L;
             plan_flight(f, s, cp, s.r[0], xf, l_b, m);
             s.r[0] = xf;
-            if (box || cp.d == 2) s.r[1] += l_b * s.w[1];
+            if (box || gd == 2) s.r[1] += l_b * s.w[1];
             if (box) s.r[2] += l_b * s.w[2];
             const int ev = (face == 0) ? EV_LEAK_X0 : EV_LEAK_XL;
             trace_row<P, TRACE>(tr, ev, s, (double)l_b);
@@ -435,20 +445,20 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 k
     const P x1 = s.r[0] + l * s.w[0];
     plan_flight(f, s, cp, s.r[0], x1, l, m);
     s.r[0] = x1;
-    if (box || cp.d == 2) s.r[1] += l * s.w[1];
+    if (box || gd == 2) s.r[1] += l * s.w[1];
     if (box) s.r[2] += l * s.w[2];
     if (coll) {
         ++s.n_coll;
         if (draw_below(s, key, R::thr_c53(cp, m), R::thr_c24(cp, m))) {
-            if (cp.d == 1) {
+            if (gd == 1) {
                 // u < 1/2 exactly when the top bit of the draw is clear
                 uint32_t hi, lo;
                 draw_words(s, key, hi, lo);
                 const P w = (hi >> 31) == 0u ? P(1) : P(-1);
                 s.w[0] = w;
                 s.iw[0] = w;
-            } else if (cp.d == 11) {
-                set_direction(s, P(2) * draw(s, key) - P(1), P(0), P(0));  // slab: mu = 2 xi - 1
+            } else if (gd == 11 || gd == 13) {
+                set_direction(s, P(2) * draw(s, key) - P(1), P(0), P(0));  // mu = 2 xi - 1
             } else {
                 const P mu = P(2) * draw(s, key) - P(1);
                 P sn, cs;
@@ -605,7 +615,7 @@ struct MinBlocks<float> {
     static constexpr int value = 4;
 };
 
-template <typename P>
+template <typename P, int G>
 __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -691,7 +701,7 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
             if (((need >> lane) & 1u) && rank < take) {
                 lcase = a.runs[feed_run].case_index;
                 lreg = feed_reg;
-                source<P>(s, a.cases[lcase], key, cursor + rank);
+                source<P, G>(s, a.cases[lcase], key, cursor + rank);
                 alive = true;
             }
             if (feed_reg == 0) fed0 += (int)take;
@@ -703,7 +713,7 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
         f.k0 = 0;
         f.k1 = -1;
         int out = -1;
-        if (alive) out = step<P, false>(s, a.cases[lcase], key, a.max_events, f, nullptr);
+        if (alive) out = step<P, false, G>(s, a.cases[lcase], key, a.max_events, f, nullptr);
         warp_deposit<P>(regions, rb, lreg, f, lane);
         if (out >= 0) {
             finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, out);

@@ -216,7 +216,7 @@ __device__ __forceinline__ int block_flag_scan(bool flag, EventBlock *eb, int *t
     return before + in_warp;
 }
 
-template <typename P>
+template <typename P, int G>
 __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int rb = a.region_bytes;
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
                 const CaseParams &cp = a.cases[a.runs[run].case_index];
                 for (int i = tid; i < take; i += blockDim.x) {
                     History<P> s;
-                    source<P>(s, cp, key, first + (unsigned long long)i);
+                    source<P, G>(s, cp, key, first + (unsigned long long)i);
                     bank_store<P>(buf, S, (uint32_t)(start + i), s, run, reg);
                 }
             }
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
                 int out = -1;
                 f.k0 = 0;
                 f.k1 = -1;
-                if (alive) out = step<P, false>(s, a.cases[ci], key, a.max_events, f, nullptr);
+                if (alive) out = step<P, false, G>(s, a.cases[ci], key, a.max_events, f, nullptr);
                 warp_deposit<P>(regions, rb, reg, f, lane);
                 if (out >= 0) {
                     finish_event_history<P>(regions + reg * rb, nbs, s, out);
@@ -402,21 +402,40 @@ __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
         if (eb->key_run[r] >= 0) block_flush<P>(regions + r * rb, a, a.runs[eb->key_run[r]].case_index, eb->key_batch[r]);
 }
 
-template <typename P>
-cudaError_t launch_event_impl(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
+template <typename P, int G>
+cudaError_t launch_event_g(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(event_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(event_kernel<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    event_kernel<P><<<grid, block, smem, st>>>(a);
+    event_kernel<P, G><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename P>
-cudaError_t occupancy_event_impl(int block, size_t smem, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, event_kernel<P>, block, smem);
+cudaError_t launch_event_impl(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t st, int geom) {
+    switch (geom) {
+    case 1: return launch_event_g<P, 1>(a, grid, block, smem, st);
+    case 2: return launch_event_g<P, 2>(a, grid, block, smem, st);
+    case 3: return launch_event_g<P, 3>(a, grid, block, smem, st);
+    case 11: return launch_event_g<P, 11>(a, grid, block, smem, st);
+    case 13: return launch_event_g<P, 13>(a, grid, block, smem, st);
+    default: return launch_event_g<P, 0>(a, grid, block, smem, st);
+    }
+}
+
+template <typename P>
+cudaError_t occupancy_event_impl(int block, size_t smem, int *blocks_per_sm, int geom) {
+    switch (geom) {
+    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, event_kernel<P, 1>, block, smem);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, event_kernel<P, 2>, block, smem);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, event_kernel<P, 3>, block, smem);
+    case 11: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, event_kernel<P, 11>, block, smem);
+    case 13: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, event_kernel<P, 13>, block, smem);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, event_kernel<P, 0>, block, smem);
+    }
 }
 
 }  // namespace cls

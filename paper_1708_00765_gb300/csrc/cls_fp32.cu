@@ -4,20 +4,32 @@
 
 namespace cls {
 
-static bool g_history_attr_set = false;
-
-cudaError_t launch_history_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-    if (!g_history_attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(history_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+template <int G>
+cudaError_t launch_history_g(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(history_kernel<float, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
-        g_history_attr_set = true;
+        attr_set = true;
     }
-    history_kernel<float><<<grid, block, smem, s>>>(a);
+    history_kernel<float, G><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_event_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-    return launch_event_impl<float>(a, grid, block, smem, s);
+// One instantiation per geometry (compile-time branches) plus the mixed one.
+cudaError_t launch_history_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s, int geom) {
+    switch (geom) {
+    case 1: return launch_history_g<1>(a, grid, block, smem, s);
+    case 2: return launch_history_g<2>(a, grid, block, smem, s);
+    case 3: return launch_history_g<3>(a, grid, block, smem, s);
+    case 11: return launch_history_g<11>(a, grid, block, smem, s);
+    case 13: return launch_history_g<13>(a, grid, block, smem, s);
+    default: return launch_history_g<0>(a, grid, block, smem, s);
+    }
+}
+
+cudaError_t launch_event_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s, int geom) {
+    return launch_event_impl<float>(a, grid, block, smem, s, geom);
 }
 
 cudaError_t launch_trace_fp32(const TraceArgs &a, cudaStream_t s) {
@@ -25,12 +37,19 @@ cudaError_t launch_trace_fp32(const TraceArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<float>, block, smem);
+cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm, int geom) {
+    switch (geom) {
+    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<float, 1>, block, smem);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<float, 2>, block, smem);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<float, 3>, block, smem);
+    case 11: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<float, 11>, block, smem);
+    case 13: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<float, 13>, block, smem);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<float, 0>, block, smem);
+    }
 }
 
-cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm) {
-    return occupancy_event_impl<float>(block, smem, blocks_per_sm);
+cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm, int geom) {
+    return occupancy_event_impl<float>(block, smem, blocks_per_sm, geom);
 }
 
 }  // namespace cls

@@ -6,20 +6,32 @@
 
 namespace cls {
 
-static bool g_history_attr_set = false;
-
-cudaError_t launch_history_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-    if (!g_history_attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(history_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+template <int G>
+cudaError_t launch_history_g(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(history_kernel<double, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
-        g_history_attr_set = true;
+        attr_set = true;
     }
-    history_kernel<double><<<grid, block, smem, s>>>(a);
+    history_kernel<double, G><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_event_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-    return launch_event_impl<double>(a, grid, block, smem, s);
+// One instantiation per geometry (compile-time branches) plus the mixed one.
+cudaError_t launch_history_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s, int geom) {
+    switch (geom) {
+    case 1: return launch_history_g<1>(a, grid, block, smem, s);
+    case 2: return launch_history_g<2>(a, grid, block, smem, s);
+    case 3: return launch_history_g<3>(a, grid, block, smem, s);
+    case 11: return launch_history_g<11>(a, grid, block, smem, s);
+    case 13: return launch_history_g<13>(a, grid, block, smem, s);
+    default: return launch_history_g<0>(a, grid, block, smem, s);
+    }
+}
+
+cudaError_t launch_event_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s, int geom) {
+    return launch_event_impl<double>(a, grid, block, smem, s, geom);
 }
 
 cudaError_t launch_trace_fp64(const TraceArgs &a, cudaStream_t s) {
@@ -27,8 +39,15 @@ cudaError_t launch_trace_fp64(const TraceArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double>, block, smem);
+cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm, int geom) {
+    switch (geom) {
+    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 1>, block, smem);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 2>, block, smem);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 3>, block, smem);
+    case 11: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 11>, block, smem);
+    case 13: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 13>, block, smem);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 0>, block, smem);
+    }
 }
 
 size_t event_block_bytes() { return (sizeof(EventBlock) + 15) & ~(size_t)15; }
@@ -37,8 +56,8 @@ int event_bank_fields(int precision) {
     return precision == 0 ? BankLayout<double>::kFields : BankLayout<float>::kFields;
 }
 
-cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm) {
-    return occupancy_event_impl<double>(block, smem, blocks_per_sm);
+cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm, int geom) {
+    return occupancy_event_impl<double>(block, smem, blocks_per_sm, geom);
 }
 
 }  // namespace cls

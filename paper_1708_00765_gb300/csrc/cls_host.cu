@@ -51,6 +51,7 @@ struct cls_handle {
     int sm_count = 0;
     bool batch = false;
     std::vector<double> params;  // ncases x 9, as created
+    int geom = 0;                // geometry shared by every case, 0 if mixed
     Options opt;
     int used_blocks_per_sm = 0;
     std::vector<CaseParams> cases;
@@ -106,7 +107,7 @@ int validate(const double *p) {
     if (!(finite(l0) && l0 > 0 && finite(l1) && l1 > 0)) return CLS_E_INVAL;
     if (!(c0 >= 0 && c0 <= 1 && c1 >= 0 && c1 <= 1)) return CLS_E_INVAL;
     if (!(finite(L) && L > 0)) return CLS_E_INVAL;
-    if (!(d == 1.0 || d == 2.0 || d == 3.0 || d == 11.0)) return CLS_E_INVAL;
+    if (!(d == 1.0 || d == 2.0 || d == 3.0 || d == 11.0 || d == 13.0)) return CLS_E_INVAL;
     if (!(nb >= 1 && nb <= kMaxBins && nb == std::floor(nb))) return CLS_E_INVAL;
     return CLS_OK;
 }
@@ -230,6 +231,9 @@ int create_common(const double *params, int ncases, bool batch, cls_handle **out
         h->nbins_max = std::max(h->nbins_max, h->cases.back().nbins);
     }
     h->nbins_stride = (h->nbins_max + 1) & ~1;
+    h->geom = h->cases[0].d;
+    for (const CaseParams &c : h->cases)
+        if (c.d != h->geom) h->geom = 0;
     h->order.resize(ncases);
     std::iota(h->order.begin(), h->order.end(), 0);
     std::stable_sort(h->order.begin(), h->order.end(),
@@ -339,9 +343,10 @@ int tracker_shape(cls_handle *h, int region_bytes, Shape *out) {
     }
     int bps = h->opt.blocks_per_sm;
     if (bps <= 0) {
-        cudaError_t e = event ? (fp64 ? occupancy_event_fp64(block, smem, &bps) : occupancy_event_fp32(block, smem, &bps))
-                              : (fp64 ? occupancy_history_fp64(block, smem, &bps)
-                                      : occupancy_history_fp32(block, smem, &bps));
+        const int g = h->geom;
+        cudaError_t e = event ? (fp64 ? occupancy_event_fp64(block, smem, &bps, g) : occupancy_event_fp32(block, smem, &bps, g))
+                              : (fp64 ? occupancy_history_fp64(block, smem, &bps, g)
+                                      : occupancy_history_fp32(block, smem, &bps, g));
         if (e != cudaSuccess) return CLS_E_CUDA;
         if (bps < 1) return CLS_E_INVAL;  // the block does not fit on an SM
     }
@@ -378,10 +383,11 @@ int launch_tracker(cls_handle *h, LaunchArgs a, const Shape &sh, cudaStream_t s)
         a.bank = h->d_bank;
         a.bank_slots = sh.bank_slots;
         a.events_per_pass = (uint32_t)h->opt.events_per_pass;
-        e = fp64 ? launch_event_fp64(a, sh.grid, sh.block, sh.smem, s) : launch_event_fp32(a, sh.grid, sh.block, sh.smem, s);
+        e = fp64 ? launch_event_fp64(a, sh.grid, sh.block, sh.smem, s, h->geom)
+                 : launch_event_fp32(a, sh.grid, sh.block, sh.smem, s, h->geom);
     } else {
-        e = fp64 ? launch_history_fp64(a, sh.grid, sh.block, sh.smem, s)
-                 : launch_history_fp32(a, sh.grid, sh.block, sh.smem, s);
+        e = fp64 ? launch_history_fp64(a, sh.grid, sh.block, sh.smem, s, h->geom)
+                 : launch_history_fp32(a, sh.grid, sh.block, sh.smem, s, h->geom);
     }
     return cuda_fail(e);
 }

@@ -112,16 +112,17 @@ inline unsigned long long unit_threshold(double v, int bits) {
 }
 
 // Launchers, one set per precision translation unit.
-cudaError_t launch_history_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_history_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_event_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_event_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s);
+// `geom`: the geometry code every case of the launch shares, or 0 (mixed)
+cudaError_t launch_history_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s, int geom);
+cudaError_t launch_history_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s, int geom);
+cudaError_t launch_event_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s, int geom);
+cudaError_t launch_event_fp32(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s, int geom);
 cudaError_t launch_trace_fp64(const TraceArgs &a, cudaStream_t s);
 cudaError_t launch_trace_fp32(const TraceArgs &a, cudaStream_t s);
-cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm);
-cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm);
-cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm);
-cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm);
+cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm, int geom);
+cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm, int geom);
+cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm, int geom);
+cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm, int geom);
 size_t event_block_bytes();           // block-shared bookkeeping of the event tracker
 int event_bank_fields(int precision); // 16-byte SoA fields per particle (0 = FP64)
 

@@ -54,7 +54,7 @@ int scratch_for_current_device(NoallocScratch **out, int *sm_count) {
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return CLS_E_CUDA;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CLS_E_CUDA;
-        if (cudaFuncSetAttribute(history_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(history_kernel<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024) != cudaSuccess)
             return CLS_E_CUDA;
         g_sm_count[dev] = sms;
@@ -69,7 +69,7 @@ bool valid_case(const double *p) {
     const double s0 = p[0], s1 = p[1], l0 = p[2], l1 = p[3], c0 = p[4], c1 = p[5], L = p[6], d = p[7], nb = p[8];
     auto fin = [](double v) { return v == v && v - v == 0.0; };
     return fin(s0) && s0 >= 0 && fin(s1) && s1 >= 0 && fin(l0) && l0 > 0 && fin(l1) && l1 > 0 && c0 >= 0 &&
-           c0 <= 1 && c1 >= 0 && c1 <= 1 && fin(L) && L > 0 && (d == 1.0 || d == 2.0 || d == 3.0 || d == 11.0) && nb >= 1 && nb <= 4096 &&
+           c0 <= 1 && c1 >= 0 && c1 <= 1 && fin(L) && L > 0 && (d == 1.0 || d == 2.0 || d == 3.0 || d == 11.0 || d == 13.0) && nb >= 1 && nb <= 4096 &&
            nb == (double)(int)nb;
 }
 
@@ -171,9 +171,9 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
     const int block = 32 * warps;
     const size_t smem = (size_t)warps * per_warp;
     int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, history_kernel<double>, block, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, history_kernel<double, 0>, block, smem) != cudaSuccess)
         return CLS_E_CUDA;
     if (bps < 1) return CLS_E_INVAL;
-    history_kernel<double><<<sm_count * bps, block, smem, s>>>(a);
+    history_kernel<double, 0><<<sm_count * bps, block, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? CLS_OK : CLS_E_CUDA;
 }

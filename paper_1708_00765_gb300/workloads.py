@@ -13,6 +13,8 @@ ROD_L10_HISTORIES = 100_000
 
 # Box of side 10, Sigma = (0.1, 10), Lambda = (1, 0.1), c = 0.99 (long histories), 200 bins; 1e8 histories.
 BOX_L10 = (0.1, 10.0, 1.0, 0.1, 0.99, 0.99, 10.0, 3, 200)
+# The same box walked by its x-marginal (geometry 13): same law of the tallies.
+BOX_L10_X = (0.1, 10.0, 1.0, 0.1, 0.99, 0.99, 10.0, 13, 200)
 BOX_L10_HISTORIES = 100_000_000
 
 # Diffusive box: L = 100, Sigma = (1, 10), Lambda = (0.5, 0.2), c = 0.999, 500 bins; 1e8 histories.
@@ -28,7 +30,7 @@ SUITE_MATERIALS = {
 SUITE_SCATTERING = {"a": (0.0, 1.0), "b": (1.0, 0.0), "c": (0.9, 0.9)}
 
 
-GEOM_ROD, GEOM_EXTRUDED, GEOM_BOX, GEOM_SLAB = 1, 2, 3, 11
+GEOM_ROD, GEOM_EXTRUDED, GEOM_BOX, GEOM_SLAB, GEOM_BOX_X = 1, 2, 3, 11, 13
 
 
 def suite_case(name: str, d: int = 3, L: float = 10.0, nbins: int = 100):
