@@ -59,9 +59,10 @@ def parse():
     ap.add_argument("--no-projected", action="store_true",
                     help="skip the arms that walk the box by its x-marginal (geometry 13)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="box", choices=["box", "diffusive", "batch"],
+    ap.add_argument("--workload", default="box", choices=["box", "diffusive", "batch", "suite"],
                     help="box: L=10 box (default, the headline line); diffusive: L=100 box, c=0.999, "
-                         "history vs event schedule; batch: 256-case sweep, FP64 plain vs FP32 batched")
+                         "history vs event schedule; batch: 256-case sweep, FP64 plain vs FP32 batched; "
+                         "suite: the paper's 54 benchmark configurations (Tables 3-8), FP64")
     return ap.parse_args()
 
 
@@ -323,6 +324,86 @@ def batch_workload(args, rank, world, pg):
         }), flush=True)
 
 
+def suite_workload(args, rank, world, pg):
+    """The paper's benchmark suite (Tables 1-2 materials; d = 1 slab, 2 extruded,
+    3 box; suites I and II): each configuration walked in FP64 on the GPU, timed with
+    CUDA events, next to the paper's published CPU rate 1e9 / t_tot (another machine:
+    context only) and the printed CLS values."""
+    import torch
+    from fractions import Fraction
+    import paper_1708_00765_gb300 as cls
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = args.histories or 100_000_000
+    stream = torch.cuda.current_stream()
+    here = os.path.join(ROOT, "tests", "golden")
+    with open(os.path.join(here, "paper_cls_suite1.json")) as f:
+        g1 = json.load(f)
+    with open(os.path.join(here, "paper_cls_suite2.json")) as f:
+        g2 = json.load(f)
+    mats = g1["materials"]
+    rows = [(1, r) for r in g1["rows"]] + [(2, r) for r in g2["rows"]]
+    out = []
+    tot_t = 0.0
+    tot_h = 0
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    with sampler:
+        for suite, r in rows:
+            sig = [float(Fraction(v)) for v in mats[r["case"][0]]["sigma"]]
+            lam = [float(Fraction(v)) for v in mats[r["case"][0]]["lambda"]]
+            c = [float(v) for v in mats[r["case"][1]]["c"]]
+            geom = {1: 11, 2: 2, 3: 3}[r["d"]]
+            prob = cls.Problem((sig[0], sig[1], lam[0], lam[1], c[0], c[1], 10.0, geom, 100))
+            if suite == 2:
+                prob.set_option("source", "volume")
+            prob.run(min(n, 100_000), 99, stream=stream)  # warm-up
+            prob.reset()
+            start = torch.cuda.Event(enable_timing=True)
+            stop = torch.cuda.Event(enable_timing=True)
+            prob.set_option("first_history", rank * n)
+            start.record(stream)
+            prob.run(n, 2019, stream=stream)
+            stop.record(stream)
+            stop.synchronize()
+            dt = max_over_ranks(pg, start.elapsed_time(stop) * 1e-3)
+            t = prob.tallies()
+            prob.close()
+            N = t["n_histories"]
+            z = {}
+            if suite == 1:
+                obs = {"R": (t["R"], t["sigma_R"]), "T": (t["T"], t["sigma_T"]),
+                       "phi": (t["total_flux"], t["sigma_total_flux"])}
+            else:
+                pl = (t["nR"] + t["nT"]) / N
+                obs = {"L": (pl / 2, math.sqrt(pl * (1 - pl) / (N - 1)) / 2),
+                       "phi": (t["total_flux"], t["sigma_total_flux"])}
+            for k, (v, sd) in obs.items():
+                pv, psd = float(r[k][0]), float(r[k][1])
+                z[k] = round((v - pv) / math.sqrt(sd * sd + psd * psd), 2)
+            paper_rate = 1e9 / float(r["t_tot_s"])
+            rate = world * n / dt
+            out.append({"suite": "I" if suite == 1 else "II", "case": r["case"], "d": r["d"], "cite": r["cite"],
+                        "histories_per_s": rate, "events_per_history": t["n_events"] / N,
+                        "paper_cpu_histories_per_s": paper_rate, "speedup_vs_paper_cpu": rate / paper_rate,
+                        "z_vs_paper": z})
+            tot_t += dt
+            tot_h += world * n
+    if rank == 0:
+        zs = [abs(v) for o in out for v in o["z_vs_paper"].values()]
+        sp = sorted(o["speedup_vs_paper_cpu"] for o in out)
+        print(json.dumps({
+            "metric": METRIC, "value": tot_h / tot_t, "unit": "histories/s", "n_gpus": world, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * tot_t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper benchmark suite: 3 cases x 3 sub-cases x d in {1,2,3} x suites I, II "
+                                   "(Tables 1-8), L = 10, 100 bins, FP64 history tracker",
+                       "histories_per_configuration": n, "configurations": len(out)},
+            "clocks": sampler.summary(),
+            "speedup_vs_paper_cpu": {"median": sp[len(sp) // 2], "min": sp[0], "max": sp[-1],
+                                     "note": "paper: 1e9 / t_tot on a Xeon E5-2680 v2 cluster, cores not stated"},
+            "z_vs_paper": {"max_abs": max(zs), "rms": math.sqrt(sum(v * v for v in zs) / len(zs))},
+            "configurations": out}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local, pg = dist_setup()
@@ -332,7 +413,8 @@ def main():
     if args.workload != "box":
         import paper_1708_00765_gb300 as cls
         cls.load(build_if_missing=True)
-        (diffusive_workload if args.workload == "diffusive" else batch_workload)(args, rank, world, pg)
+        {"diffusive": diffusive_workload, "batch": batch_workload, "suite": suite_workload}[args.workload](
+            args, rank, world, pg)
         barrier(pg)
         return
     import torch

@@ -15,7 +15,8 @@ __global__ void philox_pair_kernel(const uint32_t *in, int n, uint32_t *ours, ui
     if (i >= n) return;
     const uint4 c = make_uint4(in[6 * i + 0], in[6 * i + 1], in[6 * i + 2], in[6 * i + 3]);
     const uint2 k = make_uint2(in[6 * i + 4], in[6 * i + 5]);
-    const uint4 a = cls::philox4x32_10(c, k);
+    const cls::RoundKeys rk = cls::make_round_keys(((uint64_t)k.y << 32) | k.x);
+    const uint4 a = cls::philox4x32_10(c, rk);
     const uint4 b = curand_Philox4x32_10(c, k);
     ours[4 * i + 0] = a.x;
     ours[4 * i + 1] = a.y;
@@ -31,7 +32,7 @@ __global__ void uniform_kernel(uint64_t seed, uint32_t case_id, const uint64_t *
                                double *o64, float *o32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint2 key = cls::seed_key(seed);
+    const cls::RoundKeys key = cls::make_round_keys(seed);
     cls::History<double> s64;
     cls::History<float> s32;
     s64.h_lo = s32.h_lo = (uint32_t)h[i];

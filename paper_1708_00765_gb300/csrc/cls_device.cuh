@@ -26,20 +26,17 @@ namespace cls {
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
-// 32x32->64 multiplies mixed with the other two words and the round key;
-// the key advances by the Weyl increments between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+// 32x32->64 multiplies mixed with the other two words and the round key; the
+// key advances by the Weyl increments between rounds.  The round keys come
+// precomputed (RoundKeys, cls_internal.h): all threads of a launch share them.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys &rk) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k.x += 0x9E3779B9u;
-            k.y += 0xBB67AE85u;
-        }
         const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
         const uint32_t lo0 = 0xD2511F53u * c.x;
         const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
         const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        c = make_uint4(hi1 ^ c.y ^ rk.k[2 * r], lo1, hi0 ^ c.w ^ rk.k[2 * r + 1], lo0);
     }
     return c;
 }
@@ -161,7 +158,7 @@ struct Flight {
 // Output words (hi, lo) of draw j = s.j of the history; advances j.  Even
 // draws compute a Philox block and keep its words 2, 3 for the odd draw.
 template <typename P>
-__device__ __forceinline__ void draw_words(History<P> &s, uint2 key, uint32_t &hi, uint32_t &lo) {
+__device__ __forceinline__ void draw_words(History<P> &s, const RoundKeys &key, uint32_t &hi, uint32_t &lo) {
     if ((s.j & 1u) == 0u) {
         const uint4 o = philox4x32_10(make_uint4(s.j >> 1, s.h_lo, s.h_hi, s.cid), key);
         hi = o.x;
@@ -176,7 +173,7 @@ __device__ __forceinline__ void draw_words(History<P> &s, uint2 key, uint32_t &h
 }
 
 template <typename P>
-__device__ __forceinline__ P draw(History<P> &s, uint2 key) {
+__device__ __forceinline__ P draw(History<P> &s, const RoundKeys &key) {
     uint32_t hi, lo;
     draw_words(s, key, hi, lo);
     return Real<P>::uniform(hi, lo);
@@ -184,7 +181,7 @@ __device__ __forceinline__ P draw(History<P> &s, uint2 key) {
 
 // 1 - u of the next draw, exactly
 template <typename P>
-__device__ __forceinline__ P draw_one_minus(History<P> &s, uint2 key) {
+__device__ __forceinline__ P draw_one_minus(History<P> &s, const RoundKeys &key) {
     uint32_t hi, lo;
     draw_words(s, key, hi, lo);
     return Real<P>::one_minus(hi, lo);
@@ -192,15 +189,12 @@ __device__ __forceinline__ P draw_one_minus(History<P> &s, uint2 key) {
 
 // whether the next draw is below the value whose thresholds are given
 template <typename P>
-__device__ __forceinline__ bool draw_below(History<P> &s, uint2 key, unsigned long long thr53, uint32_t thr24) {
+__device__ __forceinline__ bool draw_below(History<P> &s, const RoundKeys &key, unsigned long long thr53, uint32_t thr24) {
     uint32_t hi, lo;
     draw_words(s, key, hi, lo);
     return Real<P>::below(hi, lo, thr53, thr24);
 }
 
-__device__ __forceinline__ uint2 seed_key(uint64_t seed) {
-    return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-}
 
 // Geometry of a case: G is a compile-time geometry code (1, 2, 3, 11, 13) for
 // launches whose cases share one geometry, 0 to read it from the case.  A
@@ -223,7 +217,7 @@ __device__ __forceinline__ void set_direction(History<P> &s, P wx, P wy, P wz) {
 
 // Source: position and direction first, then the material label.
 template <typename P, int G = 0>
-__device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, uint2 key, uint64_t h) {
+__device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, const RoundKeys &key, uint64_t h) {
     using R = Real<P>;
     const int gd = geometry<G>(cp);
     s.h_lo = (uint32_t)h;
@@ -353,7 +347,7 @@ __device__ __forceinline__ void plan_flight(Flight<P> &f, History<P> &s, const C
 // the history continues, else the terminating event (EV_LEAK_X0, EV_LEAK_XL,
 // EV_ABSORB, EV_CAPPED).
 template <typename P, bool TRACE, int G = 0>
-__device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, uint2 key, uint32_t max_events,
+__device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const RoundKeys &key, uint32_t max_events,
                                     Flight<P> &f, TraceSink *tr) {
     using R = Real<P>;
     const int gd = geometry<G>(cp);
@@ -639,7 +633,7 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
     Flight<P> f;
     bool alive = false;
     int lreg = 0, lcase = 0;
-    const uint2 key = seed_key(a.seed);
+    const RoundKeys &key = a.rk;
     const unsigned lt_mask = (1u << lane) - 1u;
 
     while (true) {
@@ -742,7 +736,7 @@ template <typename P>
 __global__ void trace_kernel(const TraceArgs a) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const CaseParams &cp = a.cases[a.case_index];
-    const uint2 key = seed_key(a.seed);
+    const RoundKeys key = make_round_keys(a.seed);
     History<P> s;
     Flight<P> f;
     source<P>(s, cp, key, a.history);

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
     const uint32_t S = a.bank_slots;  // slots per block and buffer
     const size_t buf_bytes = (size_t)S * 16 * BankLayout<P>::kFields;
     unsigned char *bank = reinterpret_cast<unsigned char *>(a.bank) + (size_t)blockIdx.x * 2 * buf_bytes;
-    const uint2 key = seed_key(a.seed);
+    const RoundKeys &key = a.rk;
     const int nbs = a.t.nbins_stride;
 
     for (int i = tid; i < 2 * rb / 8; i += blockDim.x) reinterpret_cast<unsigned long long *>(regions)[i] = 0ull;

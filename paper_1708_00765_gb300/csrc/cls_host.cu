@@ -300,6 +300,7 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, LaunchArgs *a) {
     a->chunk_counter = h->d_chunk_counter;
     a->t = Tallies{h->d_flux, h->d_stats, h->d_counters, h->nbatch, h->nbins_stride};
     a->seed = seed;
+    a->rk = make_round_keys(seed);
     a->max_events = h->opt.max_events;
     a->region_bytes = region_bytes_for(h);
     a->flush_every = (h->opt.precision == CLS_PREC_FP32) ? kFp32FlushHistories : 0;

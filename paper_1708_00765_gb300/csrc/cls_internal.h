@@ -66,7 +66,28 @@ struct Tallies {
     int nbins_stride;
 };
 
+// The ten round keys of Philox4x32-10 for one seed: (k0, k1) of round r are
+// (seed_lo + r * 0x9E3779B9, seed_hi + r * 0xBB67AE85) mod 2^32.  Every thread
+// of a launch shares them, so they travel in the kernel arguments (constant
+// bank) instead of being recomputed in every Philox block.
+struct RoundKeys {
+    uint32_t k[20];
+};
+
+__host__ __device__ inline RoundKeys make_round_keys(uint64_t seed) {
+    RoundKeys rk;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk.k[2 * r] = k0;
+        rk.k[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return rk;
+}
+
 struct LaunchArgs {
+    RoundKeys rk;  // from the seed
     const CaseParams *cases;
     const RunCase *runs;  // in chunk order (largest estimated cost first)
     int nruns;

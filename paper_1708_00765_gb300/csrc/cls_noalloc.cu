@@ -160,6 +160,7 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
     a.chunk_counter = &scratch->chunk_counter;
     a.t = Tallies{d_flux, d_stats, d_counters, nbatch, nbins_stride};
     a.seed = seed;
+    a.rk = make_round_keys(seed);
     a.max_events = 100000000u;
     a.region_bytes = region_bytes((int)sizeof(double), nbins_stride);
     a.flush_every = 0;
