@@ -73,7 +73,8 @@ extern "C" {
 #define CLS_OPT_NBATCH 5        /* statistics batches per run, 2..1024 (default 64)         */
 #define CLS_OPT_MAX_EVENTS 6    /* per-history event cap, 1..2^28 (default 1e8)             */
 #define CLS_OPT_BLOCKS_PER_SM 7 /* persistent grid = SMs x this; 0 = occupancy maximum     */
-#define CLS_OPT_BANK 8          /* event schedule: particle bank slots (0 = automatic)      */
+#define CLS_OPT_BANK 8          /* event schedule: bank particles per warp, 0..4096, rounded  */
+                                /* up to a multiple of 32 (0 = 128)                         */
 #define CLS_OPT_EVENTS_PER_PASS 9 /* event schedule: events per particle per pass (1..64)  */
 #define CLS_OPT_FIRST_HISTORY 10  /* set the next history id of every case (0..2^62); lets   */
                                   /* processes walk disjoint history ranges of one seed     */

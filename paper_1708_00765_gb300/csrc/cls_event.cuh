@@ -1,18 +1,18 @@
 // cls_event.cuh -- event-based CLS tracker over a structure-of-arrays particle bank.
 //
-// Each persistent block owns a slice of a particle bank in global memory, held
-// as structure-of-arrays of 16-byte vectors (one coalesced 128-bit load or
-// store per field per particle) and double-buffered.  A pass of the block:
-//   1. refill: empty slots take new histories from the global work counter;
-//      their sources are sampled by full warps;
-//   2. flights: every live particle is loaded, advanced by up to
+// Each warp of the persistent grid owns a slice of a particle bank in global
+// memory: `bank_slots` particles, held as structure-of-arrays of 16-byte
+// vectors (one coalesced 128-bit load or store per field per particle) and
+// double-buffered.  A pass of the warp:
+//   1. refill: empty slots take new histories from the global work counter, 32
+//      at a time, so sources are sampled by full warps;
+//   2. flights: the live particles are loaded 32 at a time, advanced by up to
 //      `events_per_pass` events of Algorithm A (same `step` as the history
 //      tracker, warp-cooperative tallies), and the survivors are compacted into
-//      the other buffer (warp ballot + block prefix sum), so dead lanes are
-//      squeezed out before the next pass.
-// Tallies go to two block-shared regions keyed by (case, batch); a region is
-// flushed when it must change key (no live particle refers to it any more),
-// periodically in FP32 mode, and when the block retires.
+//      the other buffer (ballot + prefix popcount), squeezing dead lanes out.
+// No block-wide synchronisation: warps progress independently.  Tallies go to
+// two warp-private regions keyed by (case, batch), as in the history tracker;
+// per-region live counts tell when a region may change key.
 #pragma once
 
 #include "cls_device.cuh"
@@ -127,62 +127,16 @@ __device__ __forceinline__ void bank_load<double>(const unsigned char *buf, uint
     run = (int)m1.w;
 }
 
-// Block-shared bookkeeping of the event tracker.
-struct EventBlock {
-    unsigned long long cursor, end, pending;
-    int key_run[2];
-    uint32_t key_batch[2];
-    int live[2];  // live particles whose tallies go to region r
-    int fed[2];   // histories fed into region r since its last flush
-    int feed_reg, feed_run;
-    int exhausted, have_pending;
-    int nfill;    // slots filled in the current buffer
-    // action broadcast by thread 0 during refill (for a flush: act_run is the
-    // case index and act_first the batch of the region's old key)
-    int act, act_reg, act_take, act_start, act_run;
-    unsigned long long act_first;
-    int warp_tot[32];
-};
 
-enum { ACT_DONE = 0, ACT_FILL = 1, ACT_FLUSH = 2 };
-
-// Block-wide flush of a region into the global tallies of (case, batch).
-template <typename P>
-__device__ __forceinline__ void block_flush(unsigned char *region, const LaunchArgs &a, int case_index, uint32_t batch) {
-    using B = typename Real<P>::Bin;
-    const int nbs = a.t.nbins_stride;
-    const int nb = a.cases[case_index].nbins;
-    B *bins = reinterpret_cast<B *>(region);
-    double *g = a.t.flux + ((size_t)case_index * a.t.nbatch + batch) * (size_t)nbs;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        const B v = bins[k];
-        if (v != B(0)) {
-            atomicAdd(&g[k], (double)v);
-            bins[k] = B(0);
-        }
-    }
-    double *st = region_stats<P>(region, nbs);
-    const int t = threadIdx.x;
-    if (t < S_NUM) {
-        const double v = st[t];
-        if (v != 0.0) {
-            atomicAdd(&a.t.stats[(size_t)case_index * S_NUM + t], v);
-            st[t] = 0.0;
-        }
-    } else if (t < S_NUM + C_NUM) {
-        const int c = t - S_NUM;
-        unsigned long long *ct = reinterpret_cast<unsigned long long *>(st + S_NUM);
-        const unsigned long long v = ct[c];
-        if (v != 0ull) {
-            unsigned long long *gc = &a.t.counters[(size_t)case_index * C_NUM + c];
-            if (c == C_MAXEV) atomicMax(gc, v);
-            else atomicAdd(gc, v);
-            ct[c] = 0ull;
-        }
-    }
+// Sum over the warp.
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(CLS_FULL_MASK, v, o);
+    return v;
 }
 
-// History end: per-history FP64 statistics, outcome and event maximum.
+// History end in the event tracker: per-history FP64 statistics, outcome and
+// event maximum (event and collision counts are added per pass).
 template <typename P>
 __device__ __forceinline__ void finish_event_history(unsigned char *region, int nbs, const History<P> &s, int outcome) {
     double *st = region_stats<P>(region, nbs);
@@ -199,207 +153,174 @@ __device__ __forceinline__ void finish_event_history(unsigned char *region, int 
     atomicMax(&ct[C_MAXEV], (unsigned long long)s.events);
 }
 
-// Exclusive block prefix sum of a 0/1 flag (warp ballots, then warp totals).
-__device__ __forceinline__ int block_flag_scan(bool flag, EventBlock *eb, int *total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const unsigned b = __ballot_sync(CLS_FULL_MASK, flag);
-    const int in_warp = __popc(b & ((1u << lane) - 1u));
-    if (lane == 0) eb->warp_tot[warp] = __popc(b);
-    __syncthreads();
-    int before = 0, tot = 0;
-    for (int w = 0; w < nw; ++w) {
-        const int v = eb->warp_tot[w];
-        before += (w < warp) ? v : 0;
-        tot += v;
-    }
-    *total = tot;
-    return before + in_warp;
-}
-
 template <typename P, int G>
 __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const int rb = a.region_bytes;
-    unsigned char *regions = smem;
-    EventBlock *eb = reinterpret_cast<EventBlock *>(smem + 2 * rb);
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const uint32_t S = a.bank_slots;  // slots per block and buffer
-    const size_t buf_bytes = (size_t)S * 16 * BankLayout<P>::kFields;
-    unsigned char *bank = reinterpret_cast<unsigned char *>(a.bank) + (size_t)blockIdx.x * 2 * buf_bytes;
+    unsigned char *regions = smem + (size_t)warp * 2 * rb;
+    for (int i = lane; i < 2 * rb / 8; i += 32) reinterpret_cast<unsigned long long *>(regions)[i] = 0ull;
+    __syncwarp();
+    const uint32_t W = a.bank_slots;  // particles per warp and buffer (multiple of 32)
+    const size_t buf_bytes = (size_t)W * 16 * BankLayout<P>::kFields;
+    const size_t gwarp = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    unsigned char *bank = reinterpret_cast<unsigned char *>(a.bank) + gwarp * 2 * buf_bytes;
     const RoundKeys &key = a.rk;
     const int nbs = a.t.nbins_stride;
+    const unsigned lt_mask = (1u << lane) - 1u;
 
-    for (int i = tid; i < 2 * rb / 8; i += blockDim.x) reinterpret_cast<unsigned long long *>(regions)[i] = 0ull;
-    if (tid == 0) {
-        eb->cursor = eb->end = 0;
-        eb->key_run[0] = eb->key_run[1] = -1;
-        eb->key_batch[0] = eb->key_batch[1] = 0;
-        eb->live[0] = eb->live[1] = 0;
-        eb->fed[0] = eb->fed[1] = 0;
-        eb->feed_reg = 0;
-        eb->feed_run = 0;
-        eb->exhausted = 0;
-        eb->have_pending = 0;
-        eb->nfill = 0;
-    }
-    __syncthreads();
-
+    // warp-uniform feeding state (as in the history tracker) and live counts
+    int key_run[2] = {-1, -1};
+    uint32_t key_batch[2] = {0, 0};
+    int fed[2] = {0, 0};
+    int live[2] = {0, 0};
+    uint64_t cursor = 0, end = 0;
+    int feed_reg = 0, feed_run = 0;
+    bool exhausted = false, have_pending = false;
+    unsigned long long pending = 0;
+    uint32_t nlive = 0;
     int cur = 0;
+
     while (true) {
         unsigned char *buf = bank + cur * buf_bytes;
         unsigned char *nxt = bank + (cur ^ 1) * buf_bytes;
-        // ---------------------------------------------------------- refill
-        // Thread 0 picks one action per round; the whole block carries it out.
-        while (true) {
-            if (tid == 0) {
-                int act = ACT_DONE;
-                while (true) {
-                    const int free_slots = (int)S - eb->nfill;
-                    if (free_slots <= 0) break;
-                    if (eb->cursor < eb->end) {
-                        const unsigned long long avail = eb->end - eb->cursor;
-                        const int take = (avail < (unsigned long long)free_slots) ? (int)avail : free_slots;
-                        act = ACT_FILL;
-                        eb->act_take = take;
-                        eb->act_start = eb->nfill;
-                        eb->act_first = eb->cursor;
-                        eb->act_reg = eb->feed_reg;
-                        eb->act_run = eb->feed_run;
-                        eb->cursor += take;
-                        eb->nfill += take;
-                        eb->live[eb->feed_reg] += take;
-                        eb->fed[eb->feed_reg] += take;
+        // ------------------------------------------------------------ refill
+        while (nlive < W && !exhausted) {
+            if (cursor == end) {
+                unsigned long long ch;
+                if (have_pending) {
+                    ch = pending;
+                    have_pending = false;
+                } else {
+                    if (lane == 0) ch = atomicAdd(a.chunk_counter, 1ull);
+                    ch = __shfl_sync(CLS_FULL_MASK, ch, 0);
+                }
+                if (ch >= a.total_chunks) {
+                    exhausted = true;
+                    break;
+                }
+                const int run = find_run(a, ch);
+                const RunCase &rc = a.runs[run];
+                const uint64_t local0 = (ch - rc.chunk_begin) * (uint64_t)a.chunk;
+                const uint64_t cnt = min((uint64_t)a.chunk, rc.n - local0);
+                const uint32_t batch = (uint32_t)(local0 / rc.batch_len);
+                int r = -1;
+                if (key_run[0] == run && key_batch[0] == batch) r = 0;
+                else if (key_run[1] == run && key_batch[1] == batch) r = 1;
+                if (r < 0) {
+                    const int other = feed_reg ^ 1;
+                    if (live[other] == 0) r = other;
+                    else if (live[feed_reg] == 0) r = feed_reg;
+                    if (r < 0) {  // both regions still referenced: drain first
+                        pending = ch;
+                        have_pending = true;
                         break;
                     }
-                    if (eb->exhausted) break;
-                    unsigned long long ch;
-                    if (eb->have_pending) {
-                        ch = eb->pending;
-                        eb->have_pending = 0;
-                    } else {
-                        ch = atomicAdd(a.chunk_counter, 1ull);
-                    }
-                    if (ch >= a.total_chunks) {
-                        eb->exhausted = 1;
-                        break;
-                    }
-                    const int run = find_run(a, ch);
-                    const RunCase &rc = a.runs[run];
-                    const uint64_t local0 = (ch - rc.chunk_begin) * (uint64_t)a.chunk;
-                    const uint64_t cnt = min((uint64_t)a.chunk, rc.n - local0);
-                    const uint32_t batch = (uint32_t)(local0 / rc.batch_len);
-                    int r = -1;
-                    if (eb->key_run[0] == run && eb->key_batch[0] == batch) r = 0;
-                    else if (eb->key_run[1] == run && eb->key_batch[1] == batch) r = 1;
-                    if (r < 0) {
-                        const int other = eb->feed_reg ^ 1;
-                        int rr = -1;
-                        if (eb->live[other] == 0) rr = other;
-                        else if (eb->live[eb->feed_reg] == 0) rr = eb->feed_reg;
-                        if (rr < 0) {  // both regions still referenced: drain first
-                            eb->pending = ch;
-                            eb->have_pending = 1;
-                            break;
-                        }
-                        if (eb->key_run[rr] >= 0) {  // flush the old key, then retry this chunk
-                            act = ACT_FLUSH;
-                            eb->act_reg = rr;
-                            eb->act_run = a.runs[eb->key_run[rr]].case_index;
-                            eb->act_first = eb->key_batch[rr];
-                            eb->key_run[rr] = -1;
-                            eb->pending = ch;
-                            eb->have_pending = 1;
-                            break;
-                        }
-                        eb->key_run[rr] = run;
-                        eb->key_batch[rr] = batch;
-                        eb->fed[rr] = 0;
-                        r = rr;
-                    }
-                    eb->feed_reg = r;
-                    eb->feed_run = run;
-                    eb->cursor = rc.first + local0;
-                    eb->end = eb->cursor + cnt;
+                    if (key_run[r] >= 0)
+                        flush_region<P>(regions + r * rb, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
+                    key_run[r] = run;
+                    key_batch[r] = batch;
+                    fed[r] = 0;
                 }
-                eb->act = act;
+                feed_reg = r;
+                feed_run = run;
+                cursor = rc.first + local0;
+                end = cursor + cnt;
             }
-            __syncthreads();
-            const int act = eb->act;
-            if (act == ACT_DONE) break;
-            if (act == ACT_FLUSH) {
-                block_flush<P>(regions + eb->act_reg * rb, a, eb->act_run, (uint32_t)eb->act_first);
-            } else {
-                const int take = eb->act_take, start = eb->act_start, reg = eb->act_reg, run = eb->act_run;
-                const unsigned long long first = eb->act_first;
-                const CaseParams &cp = a.cases[a.runs[run].case_index];
-                for (int i = tid; i < take; i += blockDim.x) {
-                    History<P> s;
-                    source<P, G>(s, cp, key, first + (unsigned long long)i);
-                    bank_store<P>(buf, S, (uint32_t)(start + i), s, run, reg);
-                }
+            const uint64_t avail = end - cursor;
+            const uint32_t room = W - nlive;
+            const uint32_t take = (uint32_t)min((uint64_t)min(room, 32u), avail);
+            if ((uint32_t)lane < take) {
+                const CaseParams &cp = a.cases[a.runs[feed_run].case_index];
+                History<P> s;
+                source<P, G>(s, cp, key, cursor + lane);
+                bank_store<P>(buf, W, nlive + lane, s, feed_run, feed_reg);
             }
-            __syncthreads();
+            cursor += take;
+            nlive += take;
+            live[feed_reg] += (int)take;
+            fed[feed_reg] += (int)take;
         }
-        const int nlive = eb->nfill;
         if (nlive == 0) break;
+        __syncwarp();
 
-        // --------------------------------------------------------- flights
-        int out_base = 0;
-        for (int r0 = 0; r0 < nlive; r0 += blockDim.x) {
-            const int slot = r0 + tid;
+        // ----------------------------------------------------------- flights
+        // collisions, interface crossings, reflections, events of this pass, per region
+        unsigned long long c0 = 0, i0 = 0, f0 = 0, e0 = 0, c1 = 0, i1 = 0, f1 = 0, e1 = 0;
+        uint32_t out = 0;
+        for (uint32_t r0 = 0; r0 < nlive; r0 += 32) {
+            const uint32_t slot = r0 + lane;
             History<P> s;
             Flight<P> f;
             int run = 0, reg = 0;
             bool alive = slot < nlive;
-            if (alive) bank_load<P>(buf, S, (uint32_t)slot, s, run, reg);
-            const uint32_t ev0 = alive ? s.events : 0u;
-            s.n_coll = s.n_int = s.n_refl = 0;
+            if (alive) bank_load<P>(buf, W, slot, s, run, reg);
             const int ci = alive ? a.runs[run].case_index : 0;
             s.cid = a.cases[ci].case_id;  // Philox counter word 3 (not stored in the bank)
+            const uint32_t ev0 = alive ? s.events : 0u;
+            s.n_coll = s.n_int = s.n_refl = 0;
+            bool died = false;
             for (uint32_t e = 0; e < a.events_per_pass; ++e) {
                 if (!__any_sync(CLS_FULL_MASK, alive)) break;
-                int out = -1;
+                int o = -1;
                 f.k0 = 0;
                 f.k1 = -1;
-                if (alive) out = step<P, false, G>(s, a.cases[ci], key, a.max_events, f, nullptr);
+                if (alive) o = step<P, false, G>(s, a.cases[ci], key, a.max_events, f, nullptr);
                 warp_deposit<P>(regions, rb, reg, f, lane);
-                if (out >= 0) {
-                    finish_event_history<P>(regions + reg * rb, nbs, s, out);
-                    atomicSub(&eb->live[reg], 1);
+                if (o >= 0) {
+                    finish_event_history<P>(regions + reg * rb, nbs, s, o);
                     alive = false;
+                    died = true;
                 }
             }
             if (slot < nlive) {
-                double *st = region_stats<P>(regions + reg * rb, nbs);
-                unsigned long long *ct = reinterpret_cast<unsigned long long *>(st + S_NUM);
-                if (s.n_coll) atomicAdd(&ct[C_COLL], (unsigned long long)s.n_coll);
-                if (s.n_int) atomicAdd(&ct[C_INT], (unsigned long long)s.n_int);
-                if (s.n_refl) atomicAdd(&ct[C_REFL], (unsigned long long)s.n_refl);
-                atomicAdd(&ct[C_EVENTS], (unsigned long long)(s.events - ev0));
+                if (reg == 0) {
+                    c0 += s.n_coll;
+                    i0 += s.n_int;
+                    f0 += s.n_refl;
+                    e0 += s.events - ev0;
+                } else {
+                    c1 += s.n_coll;
+                    i1 += s.n_int;
+                    f1 += s.n_refl;
+                    e1 += s.events - ev0;
+                }
             }
-            int total = 0;
-            const int idx = block_flag_scan(alive, eb, &total);
-            if (alive) bank_store<P>(nxt, S, (uint32_t)(out_base + idx), s, run, reg);
-            out_base += total;
-            __syncthreads();
+            live[0] -= __popc(__ballot_sync(CLS_FULL_MASK, died && reg == 0));
+            live[1] -= __popc(__ballot_sync(CLS_FULL_MASK, died && reg == 1));
+            const unsigned b = __ballot_sync(CLS_FULL_MASK, alive);
+            if (alive) bank_store<P>(nxt, W, out + __popc(b & lt_mask), s, run, reg);
+            out += __popc(b);
         }
-        if (tid == 0) eb->nfill = out_base;
+        // warp-aggregated event counters: one shared-memory atomic per counter
+        for (int r = 0; r < 2; ++r) {
+            unsigned long long *ct = reinterpret_cast<unsigned long long *>(region_stats<P>(regions + r * rb, nbs) + S_NUM);
+            const unsigned long long v0 = warp_sum(r ? c1 : c0), v1 = warp_sum(r ? i1 : i0);
+            const unsigned long long v2 = warp_sum(r ? f1 : f0), v3 = warp_sum(r ? e1 : e0);
+            if (lane == 0) {
+                if (v0) atomicAdd(&ct[C_COLL], v0);
+                if (v1) atomicAdd(&ct[C_INT], v1);
+                if (v2) atomicAdd(&ct[C_REFL], v2);
+                if (v3) atomicAdd(&ct[C_EVENTS], v3);
+            }
+        }
+        __syncwarp();
+        nlive = out;
         cur ^= 1;
         // FP32 regions: bound the partial sums
         if (a.flush_every) {
             for (int r = 0; r < 2; ++r) {
-                if (eb->fed[r] >= a.flush_every && eb->key_run[r] >= 0) {
-                    block_flush<P>(regions + r * rb, a, a.runs[eb->key_run[r]].case_index, eb->key_batch[r]);
-                    __syncthreads();
-                    if (tid == 0) eb->fed[r] = 0;
+                if (fed[r] >= a.flush_every && key_run[r] >= 0) {
+                    flush_region<P>(regions + r * rb, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
+                    fed[r] = 0;
                 }
             }
         }
-        __syncthreads();
     }
+    __syncwarp();
     for (int r = 0; r < 2; ++r)
-        if (eb->key_run[r] >= 0) block_flush<P>(regions + r * rb, a, a.runs[eb->key_run[r]].case_index, eb->key_batch[r]);
+        if (key_run[r] >= 0) flush_region<P>(regions + r * rb, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
 }
 
 template <typename P, int G>

@@ -50,8 +50,6 @@ cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm, i
     }
 }
 
-size_t event_block_bytes() { return (sizeof(EventBlock) + 15) & ~(size_t)15; }
-
 int event_bank_fields(int precision) {
     return precision == 0 ? BankLayout<double>::kFields : BankLayout<float>::kFields;
 }

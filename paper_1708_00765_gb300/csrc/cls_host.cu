@@ -327,21 +327,12 @@ struct Shape {
 int tracker_shape(cls_handle *h, int region_bytes, Shape *out) {
     const bool event = h->opt.schedule == CLS_SCHED_EVENT;
     const bool fp64 = h->opt.precision == CLS_PREC_FP64;
-    int block;
-    size_t smem;
-    if (event) {
-        // two block-shared regions plus the block's bookkeeping
-        block = h->opt.block;
-        smem = 2 * (size_t)region_bytes + event_block_bytes();
-        if (smem > kMaxSmemPerBlock) return CLS_E_INVAL;
-    } else {
-        // each warp owns two tally regions; wide meshes get fewer warps per block
-        const size_t per_warp = 2 * (size_t)region_bytes;
-        const int fit_warps = (int)std::min<size_t>(kMaxSmemPerBlock / per_warp, 8);
-        if (fit_warps < 1) return CLS_E_INVAL;
-        block = 32 * std::min(h->opt.block / 32, fit_warps);
-        smem = (size_t)(block / 32) * per_warp;
-    }
+    // each warp owns two tally regions; wide meshes get fewer warps per block
+    const size_t per_warp = 2 * (size_t)region_bytes;
+    const int fit_warps = (int)std::min<size_t>(kMaxSmemPerBlock / per_warp, 8);
+    if (fit_warps < 1) return CLS_E_INVAL;
+    const int block = 32 * std::min(h->opt.block / 32, fit_warps);
+    const size_t smem = (size_t)(block / 32) * per_warp;
     int bps = h->opt.blocks_per_sm;
     if (bps <= 0) {
         const int g = h->geom;
@@ -355,15 +346,16 @@ int tracker_shape(cls_handle *h, int region_bytes, Shape *out) {
     out->grid = h->sm_count * bps;
     out->block = block;
     out->smem = smem;
-    out->bank_slots = event ? (uint32_t)(h->opt.bank > 0 ? h->opt.bank : 16 * block) : 0u;
+    out->bank_slots = event ? (uint32_t)(h->opt.bank > 0 ? ((h->opt.bank + 31) & ~31) : 128) : 0u;
     return CLS_OK;
 }
 
-// Event schedule: make sure the particle bank (grid x 2 buffers x slots x
-// fields x 16 B) is allocated.  Done before any graph capture.
+// Event schedule: make sure the particle bank (grid warps x 2 buffers x
+// slots x fields x 16 B) is allocated.  Done before any graph capture.
 int ensure_bank(cls_handle *h, const Shape &sh) {
     if (h->opt.schedule != CLS_SCHED_EVENT) return CLS_OK;
-    const size_t need = (size_t)sh.grid * 2 * sh.bank_slots * (size_t)event_bank_fields(h->opt.precision) * 16;
+    const size_t need = (size_t)sh.grid * (sh.block / 32) * 2 * sh.bank_slots *
+                        (size_t)event_bank_fields(h->opt.precision) * 16;
     if (need <= h->bank_bytes) return CLS_OK;
     CLS_CUDA(cudaDeviceSynchronize());
     cudaFree(h->d_bank);
@@ -717,7 +709,7 @@ int cls_set_option(cls_handle *h, int key, int64_t v) {
         o.blocks_per_sm = (int)v;
         break;
     case CLS_OPT_BANK:
-        if (v < 0 || v > (int64_t)1 << 26) return CLS_E_INVAL;
+        if (v < 0 || v > 4096) return CLS_E_INVAL;
         o.bank = (int)v;
         break;
     case CLS_OPT_EVENTS_PER_PASS:

@@ -100,8 +100,8 @@ struct LaunchArgs {
     int region_bytes;     // bytes per warp tally region (see region_bytes())
     int flush_every;      // flush a region after this many histories were fed into it (0: never)
     // event schedule only
-    void *bank;
-    uint32_t bank_slots;
+    void *bank;            // grid warps x 2 buffers x bank_slots particles (SoA)
+    uint32_t bank_slots;   // particles per warp and buffer, a multiple of 32
     uint32_t events_per_pass;
 };
 
@@ -144,7 +144,6 @@ cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm, i
 cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm, int geom);
 cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm, int geom);
 cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm, int geom);
-size_t event_block_bytes();           // block-shared bookkeeping of the event tracker
 int event_bank_fields(int precision); // 16-byte SoA fields per particle (0 = FP64)
 
 }  // namespace cls
