@@ -138,7 +138,8 @@ typedef struct {
  *                    CLS_GEOM_BOX_X
  *   nbins            uniform flux bins along x, 1..4096
  * Selects the current CUDA device, allocates the device tallies (library-
- * owned, freed by cls_destroy) and zeroes them.
+ * owned, freed by cls_destroy) and zeroes them.  Flux tallies (cases x
+ * statistics batches x bins) above 2^32 doubles are refused (CLS_E_NOMEM).
  * Errors: CLS_E_INVAL, CLS_E_NOMEM, CLS_E_NODEVICE, CLS_E_CUDA. */
 int cls_create(double sigma0, double sigma1, double lambda0, double lambda1, double c0, double c1,
                double L, int d, int nbins, cls_handle **out);

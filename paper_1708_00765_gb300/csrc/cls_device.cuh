@@ -504,15 +504,24 @@ __device__ __forceinline__ void finish_history(unsigned char *region, int nbs, c
 // bins of all lanes' flights are then spread evenly over the 32 lanes (warp
 // prefix sum of the interior counts, and a 5-step shuffle search for the lane
 // that owns each interior bin), so long flights do not serialise the warp.
+// A lane with lreg == 2 scores straight into the FP64 global bins at
+// gflux + goff, those of its (case, batch) (see the region eviction in the
+// trackers).
 template <typename P>
-__device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes, int lreg, const Flight<P> &f,
-                                             int lane) {
+__device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes, int lreg, double *gflux,
+                                             uint32_t goff, const Flight<P> &f, int lane) {
     using B = typename Real<P>::Bin;
     const bool has = f.k1 >= f.k0;
     if (has) {
-        B *bins = reinterpret_cast<B *>(regions + lreg * rbytes);
-        atomicAdd(&bins[f.k0], (B)f.a0);
-        if (f.k1 > f.k0) atomicAdd(&bins[f.k1], (B)f.a1);
+        if (lreg < 2) {
+            B *bins = reinterpret_cast<B *>(regions + lreg * rbytes);
+            atomicAdd(&bins[f.k0], (B)f.a0);
+            if (f.k1 > f.k0) atomicAdd(&bins[f.k1], (B)f.a1);
+        } else {
+            double *gbins = gflux + goff;
+            atomicAdd(&gbins[f.k0], (double)f.a0);
+            if (f.k1 > f.k0) atomicAdd(&gbins[f.k1], (double)f.a1);
+        }
     }
     const int ni = has ? max(f.k1 - f.k0 - 1, 0) : 0;
     int incl = ni;
@@ -523,6 +532,7 @@ __device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes,
     }
     const int total = __shfl_sync(CLS_FULL_MASK, incl, 31);
     if (total == 0) return;
+    const bool any_global = __any_sync(CLS_FULL_MASK, lreg == 2 && ni > 0);
     const int base_bin = f.k0 + 1 - (incl - ni);  // interior task t of this lane goes to base_bin + t
     for (int base = 0; base < total; base += 32) {
         const int t = base + lane;
@@ -535,11 +545,42 @@ __device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes,
         const int ob = __shfl_sync(CLS_FULL_MASK, base_bin, o);
         const P oc = __shfl_sync(CLS_FULL_MASK, f.c, o);
         const int oreg = __shfl_sync(CLS_FULL_MASK, lreg, o);
+        uint32_t ogoff = 0;
+        if (any_global) ogoff = __shfl_sync(CLS_FULL_MASK, goff, o);
         if (t < total) {
-            B *bins = reinterpret_cast<B *>(regions + oreg * rbytes);
-            atomicAdd(&bins[ob + t], (B)oc);
+            if (oreg < 2) {
+                B *bins = reinterpret_cast<B *>(regions + oreg * rbytes);
+                atomicAdd(&bins[ob + t], (B)oc);
+            } else {
+                atomicAdd(&gflux[ogoff + ob + t], (double)oc);
+            }
         }
     }
+}
+
+// History end for a lane that scores into global memory: the same statistics
+// and counters as finish_history, added to the case's global tally block.
+template <typename P>
+__device__ __forceinline__ void finish_history_global(const LaunchArgs &a, int case_index, const History<P> &s,
+                                                      int outcome, bool with_event_counts) {
+    double *st = a.t.stats + (size_t)case_index * S_NUM;
+    unsigned long long *ct = a.t.counters + (size_t)case_index * C_NUM;
+    const double t0 = (double)s.track0;
+    const double t1 = (double)s.track1;
+    const double t = t0 + t1;
+    atomicAdd(&st[S_T], t);
+    atomicAdd(&st[S_T2], t * t);
+    if (t0 != 0.0) atomicAdd(&st[S_TRACK0], t0);
+    if (t1 != 0.0) atomicAdd(&st[S_TRACK1], t1);
+    const int c = (outcome == EV_LEAK_X0) ? C_R : (outcome == EV_LEAK_XL) ? C_T : (outcome == EV_ABSORB) ? C_A : C_CAPPED;
+    atomicAdd(&ct[c], 1ull);
+    if (with_event_counts) {
+        if (s.n_coll) atomicAdd(&ct[C_COLL], (unsigned long long)s.n_coll);
+        if (s.n_int) atomicAdd(&ct[C_INT], (unsigned long long)s.n_int);
+        if (s.n_refl) atomicAdd(&ct[C_REFL], (unsigned long long)s.n_refl);
+        atomicAdd(&ct[C_EVENTS], (unsigned long long)s.events);
+    }
+    atomicMax(&ct[C_MAXEV], (unsigned long long)s.events);
 }
 
 // Flush a warp region into the global tally block of (case, batch): one global
@@ -598,6 +639,10 @@ __device__ __forceinline__ int find_run(const LaunchArgs &a, uint64_t ch) {
 // across history and chunk boundaries.  Each warp owns two shared-memory tally
 // regions keyed by (case, batch); a region is flushed to global memory when
 // its key changes, after flush_every histories, or when the warp retires.
+// When a new key arrives while both regions still serve live histories, the
+// older region is flushed and re-keyed, and its remaining histories score
+// straight into the FP64 global tallies: the warp never waits for a straggler
+// of a heavy-tailed history-length distribution.
 // Blocks per SM the register allocation must allow: FP64 is bound by the FP64
 // pipe, FP32 by issue and latency, which more resident warps help hide.
 template <typename P>
@@ -625,14 +670,16 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
     int fed0 = 0, fed1 = 0;
     uint64_t cursor = 0, end = 0;  // history ids of the chunk being fed
     int feed_reg = 0, feed_run = 0;
-    bool exhausted = false, have_pending = false;
-    unsigned long long pending = 0;
+    uint32_t feed_batch = 0;
+    bool exhausted = false;
 
-    // lane state
+    // lane state: lreg is the lane's tally region, or 2 once that region was
+    // handed to a newer key (the lane then scores into global memory)
     History<P> s;
     Flight<P> f;
     bool alive = false;
     int lreg = 0, lcase = 0;
+    uint32_t lbatch = 0;
     const RoundKeys &key = a.rk;
     const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -641,13 +688,8 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
         while (need != 0u && !exhausted) {
             if (cursor == end) {
                 unsigned long long ch;
-                if (have_pending) {
-                    ch = pending;
-                    have_pending = false;
-                } else {
-                    if (lane == 0) ch = atomicAdd(a.chunk_counter, 1ull);
-                    ch = __shfl_sync(CLS_FULL_MASK, ch, 0);
-                }
+                if (lane == 0) ch = atomicAdd(a.chunk_counter, 1ull);
+                ch = __shfl_sync(CLS_FULL_MASK, ch, 0);
                 if (ch >= a.total_chunks) {
                     exhausted = true;
                     break;
@@ -666,18 +708,19 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
                     const int other = feed_reg ^ 1;
                     if (!(other ? live1 : live0)) r = other;
                     else if (!(feed_reg ? live1 : live0)) r = feed_reg;
-                    if (r < 0) {  // both regions in use by other keys: drain first
-                        pending = ch;
-                        have_pending = true;
-                        break;
+                    else r = other;  // both referenced: evict the older region
+                    const int old_run = r ? key_run1 : key_run0;
+                    const uint32_t old_batch = r ? key_batch1 : key_batch0;
+                    if (old_run >= 0) {
+                        flush_region<P>(regions + r * rb, a, a.runs[old_run].case_index, old_batch, lane);
+                        // lanes still walking a history of the old key go on in global memory
+                        if (alive && lreg == r) lreg = 2;
                     }
                     if (r == 0) {
-                        if (key_run0 >= 0) flush_region<P>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
                         key_run0 = run;
                         key_batch0 = batch;
                         fed0 = 0;
                     } else {
-                        if (key_run1 >= 0) flush_region<P>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
                         key_run1 = run;
                         key_batch1 = batch;
                         fed1 = 0;
@@ -685,6 +728,7 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
                 }
                 feed_reg = r;
                 feed_run = run;
+                feed_batch = batch;
                 cursor = rc.first + local0;
                 end = cursor + cnt;
             }
@@ -695,6 +739,7 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
             if (((need >> lane) & 1u) && rank < take) {
                 lcase = a.runs[feed_run].case_index;
                 lreg = feed_reg;
+                lbatch = feed_batch;
                 source<P, G>(s, a.cases[lcase], key, cursor + rank);
                 alive = true;
             }
@@ -708,9 +753,11 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
         f.k1 = -1;
         int out = -1;
         if (alive) out = step<P, false, G>(s, a.cases[lcase], key, a.max_events, f, nullptr);
-        warp_deposit<P>(regions, rb, lreg, f, lane);
+        const uint32_t goff = (lreg == 2) ? ((uint32_t)lcase * (uint32_t)a.t.nbatch + lbatch) * (uint32_t)a.t.nbins_stride : 0u;
+        warp_deposit<P>(regions, rb, lreg, a.t.flux, goff, f, lane);
         if (out >= 0) {
-            finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, out);
+            if (lreg < 2) finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, out);
+            else finish_history_global<P>(a, lcase, s, out, true);
             alive = false;
         }
         if (a.flush_every) {

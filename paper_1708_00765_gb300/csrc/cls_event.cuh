@@ -12,7 +12,11 @@
 //      the other buffer (ballot + prefix popcount), squeezing dead lanes out.
 // No block-wide synchronisation: warps progress independently.  Tallies go to
 // two warp-private regions keyed by (case, batch), as in the history tracker;
-// per-region live counts tell when a region may change key.
+// per-region live counts tell when a region is free.  When a new key arrives
+// and both regions are in use, a region with only a few particles left is
+// flushed and given a new generation, after which those particles score into
+// the FP64 global tallies; otherwise the warp keeps walking its bank and
+// retries the chunk after the next pass.
 #pragma once
 
 #include "cls_device.cuh"
@@ -23,7 +27,8 @@ namespace cls {
 //   FP32: [0] (x, y, z, track0) [1] (wx, wy, wz, track1) [2] meta0 [3] meta1
 //   FP64: [0] (x, y) [1] (z, track0) [2] (wx, wy) [3] (wz, track1) [4] (iwx, iwy)
 //         [5] (iwz, -) [6] meta0 [7] meta1
-//   meta0 = (h_lo, h_hi, j, c2); meta1 = (c3, m | region << 1, events, run)
+//   meta0 = (h_lo, h_hi, j, c2); meta1 = (c3, m | region << 1 | generation << 3, events, run)
+//   (region 0 or 1: a warp tally region of that generation; 2: global tallies)
 template <typename P>
 struct BankLayout;
 template <>
@@ -73,7 +78,7 @@ __device__ __forceinline__ void bank_load<float>(const unsigned char *buf, uint3
     s.c2 = c.w;
     s.c3 = d.x;
     s.m = (int)(d.y & 1u);
-    reg = (int)((d.y >> 1) & 1u);
+    reg = (int)(d.y >> 1);
     s.events = d.z;
     run = (int)d.w;
 }
@@ -122,7 +127,7 @@ __device__ __forceinline__ void bank_load<double>(const unsigned char *buf, uint
     s.c2 = m0.w;
     s.c3 = m1.x;
     s.m = (int)(m1.y & 1u);
-    reg = (int)((m1.y >> 1) & 1u);
+    reg = (int)(m1.y >> 1);
     s.events = m1.z;
     run = (int)m1.w;
 }
@@ -170,15 +175,21 @@ __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
     const int nbs = a.t.nbins_stride;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    // warp-uniform feeding state (as in the history tracker) and live counts
+    // warp-uniform feeding state (as in the history tracker), live counts and
+    // region generations: a banked particle names its region and that region's
+    // generation; a region handed to a newer key gets a new generation, and
+    // particles of an older one score into global memory
     int key_run[2] = {-1, -1};
     uint32_t key_batch[2] = {0, 0};
     int fed[2] = {0, 0};
     int live[2] = {0, 0};
+    uint32_t gen[2] = {0, 0};
     uint64_t cursor = 0, end = 0;
     int feed_reg = 0, feed_run = 0;
     bool exhausted = false, have_pending = false;
     unsigned long long pending = 0;
+    // a region still serving more particles than this is drained rather than evicted
+    const int evict_max = (int)(W >> 4);
     uint32_t nlive = 0;
     int cur = 0;
 
@@ -212,13 +223,17 @@ __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
                     const int other = feed_reg ^ 1;
                     if (live[other] == 0) r = other;
                     else if (live[feed_reg] == 0) r = feed_reg;
-                    if (r < 0) {  // both regions still referenced: drain first
+                    else if (live[other] <= evict_max) r = other;  // a few stragglers: evict
+                    if (r < 0) {  // both regions busy: keep walking the bank, retry next pass
                         pending = ch;
                         have_pending = true;
                         break;
                     }
-                    if (key_run[r] >= 0)
+                    if (key_run[r] >= 0) {
                         flush_region<P>(regions + r * rb, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
+                        gen[r] += 1;  // its banked particles now score into global memory
+                        live[r] = 0;
+                    }
                     key_run[r] = run;
                     key_batch[r] = batch;
                     fed[r] = 0;
@@ -235,7 +250,7 @@ __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
                 const CaseParams &cp = a.cases[a.runs[feed_run].case_index];
                 History<P> s;
                 source<P, G>(s, cp, key, cursor + lane);
-                bank_store<P>(buf, W, nlive + lane, s, feed_run, feed_reg);
+                bank_store<P>(buf, W, nlive + lane, s, feed_run, feed_reg | (int)(gen[feed_reg] << 2));
             }
             cursor += take;
             nlive += take;
@@ -253,11 +268,21 @@ __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
             const uint32_t slot = r0 + lane;
             History<P> s;
             Flight<P> f;
-            int run = 0, reg = 0;
+            int run = 0, packed = 0;
             bool alive = slot < nlive;
-            if (alive) bank_load<P>(buf, W, slot, s, run, reg);
+            if (alive) bank_load<P>(buf, W, slot, s, run, packed);
             const int ci = alive ? a.runs[run].case_index : 0;
             s.cid = a.cases[ci].case_id;  // Philox counter word 3 (not stored in the bank)
+            // the particle's region, or 2 if that region has since changed key
+            int reg = packed & 3;
+            if (reg < 2 && (uint32_t)(packed >> 2) != gen[reg]) reg = 2;
+            uint32_t goff = 0;
+            if (alive && reg == 2) {
+                const RunCase &rc = a.runs[run];
+                const uint64_t h = ((uint64_t)s.h_hi << 32) | s.h_lo;
+                const uint32_t batch = (uint32_t)((h - rc.first) / rc.batch_len);
+                goff = ((uint32_t)ci * (uint32_t)a.t.nbatch + batch) * (uint32_t)nbs;
+            }
             const uint32_t ev0 = alive ? s.events : 0u;
             s.n_coll = s.n_int = s.n_refl = 0;
             bool died = false;
@@ -267,9 +292,10 @@ __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
                 f.k0 = 0;
                 f.k1 = -1;
                 if (alive) o = step<P, false, G>(s, a.cases[ci], key, a.max_events, f, nullptr);
-                warp_deposit<P>(regions, rb, reg, f, lane);
+                warp_deposit<P>(regions, rb, reg, a.t.flux, goff, f, lane);
                 if (o >= 0) {
-                    finish_event_history<P>(regions + reg * rb, nbs, s, o);
+                    if (reg < 2) finish_event_history<P>(regions + reg * rb, nbs, s, o);
+                    else finish_history_global<P>(a, ci, s, o, false);
                     alive = false;
                     died = true;
                 }
@@ -280,17 +306,24 @@ __global__ void __launch_bounds__(256) event_kernel(const LaunchArgs a) {
                     i0 += s.n_int;
                     f0 += s.n_refl;
                     e0 += s.events - ev0;
-                } else {
+                } else if (reg == 1) {
                     c1 += s.n_coll;
                     i1 += s.n_int;
                     f1 += s.n_refl;
                     e1 += s.events - ev0;
+                } else {
+                    unsigned long long *gc = a.t.counters + (size_t)ci * C_NUM;
+                    if (s.n_coll) atomicAdd(&gc[C_COLL], (unsigned long long)s.n_coll);
+                    if (s.n_int) atomicAdd(&gc[C_INT], (unsigned long long)s.n_int);
+                    if (s.n_refl) atomicAdd(&gc[C_REFL], (unsigned long long)s.n_refl);
+                    atomicAdd(&gc[C_EVENTS], (unsigned long long)(s.events - ev0));
                 }
             }
             live[0] -= __popc(__ballot_sync(CLS_FULL_MASK, died && reg == 0));
             live[1] -= __popc(__ballot_sync(CLS_FULL_MASK, died && reg == 1));
+            const int store_tag = (reg < 2) ? (reg | (int)(gen[reg] << 2)) : 2;
             const unsigned b = __ballot_sync(CLS_FULL_MASK, alive);
-            if (alive) bank_store<P>(nxt, W, out + __popc(b & lt_mask), s, run, reg);
+            if (alive) bank_store<P>(nxt, W, out + __popc(b & lt_mask), s, run, store_tag);
             out += __popc(b);
         }
         // warp-aggregated event counters: one shared-memory atomic per counter

@@ -172,6 +172,7 @@ void free_tallies(cls_handle *h) {
 int alloc_tallies(cls_handle *h) {
     const size_t nc = h->cases.size();
     const size_t nflux = nc * (size_t)h->nbatch * (size_t)h->nbins_stride;
+    if (nflux >= (1ull << 32)) return CLS_E_NOMEM;  // flux tallies are addressed with 32-bit offsets
     if (cudaMalloc(&h->d_flux, nflux * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->d_stats, nc * S_NUM * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->d_counters, nc * C_NUM * sizeof(unsigned long long)) != cudaSuccess) {

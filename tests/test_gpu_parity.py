@@ -455,3 +455,17 @@ def test_projected_box_matches_the_box_in_law():
     z = (tb["flux"] - tx["flux"]) / np.hypot(tb["flux_sigma"], tx["flux_sigma"])
     assert np.max(np.abs(z)) < 5 and np.mean(z * z) < 3.0
     assert tx["n_reflect"] == 0 and tb["n_reflect"] > 0
+
+
+@pytest.mark.parametrize("schedule", ["history", "event"])
+@pytest.mark.parametrize("precision", ["fp64"])
+def test_region_eviction_keeps_parity(schedule, precision):
+    """1024 statistics batches and 32-history chunks: nearly every claim brings a new
+    (case, batch) key, so warps keep evicting regions that still serve long histories,
+    which then score into global memory.  Counts stay bit-exact and every batch's flux
+    matches the oracle's."""
+    p = workloads.BOX_L10
+    n = 40_000
+    raw_g, _ = gpu_raw(p, n, 23, schedule=schedule, precision=precision, nbatch=1024, chunk=32)
+    raw_o = oracle.run(ocase(p), 23, 0, n, nbatch=1024)
+    assert_parity(raw_g, raw_o)
