@@ -37,11 +37,11 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # and warp instructions per event of history_kernel<float>.  Re-measured
 # whenever the kernel changes.
 FP64_FLOP_PER_EVENT = 148.8
-FP32_WARP_INST_PER_EVENT = 42.8
+FP32_WARP_INST_PER_EVENT = 40.4
 # DRAM bytes per full-size FP64 launch (1e8 histories) from a one-pass ncu
 # capture of the current kernel (profiles/history_kernel_box_L10.md); set to
 # None whenever the kernel changes until it is captured again.
-FP64_DRAM_BYTES_PER_LAUNCH = None
+FP64_DRAM_BYTES_PER_LAUNCH = 774144
 SM_COUNT = 152           # GB300
 DFMA_PER_SM_CLK = 2      # ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / 152 SMs
 ISSUE_PER_SM_CLK = 4     # one warp instruction per scheduler per clock, 4 schedulers
