@@ -254,6 +254,14 @@ int cls_debug_philox(const uint32_t *in, int n, uint32_t *ours, uint32_t *theirs
 int cls_debug_uniform(uint64_t seed, uint32_t case_id, const uint64_t *h, const uint64_t *j, int n,
                       double *out64, float *out32);
 
+/* The FP64 walk's elementary functions of a draw: for u = k[i] 2^-53
+ * (0 <= k[i] < 2^53), ln1m[i] = ln(1 - u) (the distances l_c = -ln(1-u)/Sigma
+ * and l_i = -Lambda ln(1-u) of paper Sec. 4) and sin2pi[i], cos2pi[i] =
+ * sin, cos of 2 pi u (the azimuth of isotropic directions, paper Sec. 4.3).
+ * Host arrays of n entries; any output may be NULL; synchronous.
+ * Errors: CLS_E_INVAL (k[i] >= 2^53, n < 1), CLS_E_CUDA, CLS_E_NOMEM. */
+int cls_debug_math(const uint64_t *k, int n, double *ln1m, double *sin2pi, double *cos2pi);
+
 /* ------------------------------------------------- allocation-free run */
 
 /* Largest number of cases one cls_run_noalloc call takes. */

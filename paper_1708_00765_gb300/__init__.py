@@ -7,9 +7,9 @@ has not been built.
 """
 from . import build
 from ._native import (CLS_E_EVENT_LIMIT, CLS_OK, CLS_PREC_FP32, CLS_PREC_FP64, CLS_SCHED_EVENT,
-                      CLS_SCHED_HISTORY, EXPORTED, ClsError, Problem, debug_philox, debug_uniform, load,
+                      CLS_SCHED_HISTORY, EXPORTED, ClsError, Problem, debug_math, debug_philox, debug_uniform, load,
                       strerror)
 
-__all__ = ["build", "load", "Problem", "ClsError", "strerror", "debug_philox", "debug_uniform", "EXPORTED",
+__all__ = ["build", "load", "Problem", "ClsError", "strerror", "debug_philox", "debug_uniform", "debug_math", "EXPORTED",
            "CLS_OK", "CLS_E_EVENT_LIMIT", "CLS_PREC_FP32", "CLS_PREC_FP64", "CLS_SCHED_EVENT",
            "CLS_SCHED_HISTORY"]

@@ -43,7 +43,7 @@ CLS_SCHED_EVENT = 2
 # every symbol include/cls.h declares
 EXPORTED = ("cls_create", "cls_set_option", "cls_get_option", "cls_run", "cls_tallies", "cls_raw_tallies",
             "cls_reset", "cls_destroy", "cls_strerror", "cls_trace", "cls_batch_create", "cls_batch_run",
-            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_run_noalloc", "cls_autotune", "cls_finalize_raw")
+            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_debug_math", "cls_run_noalloc", "cls_autotune", "cls_finalize_raw")
 
 CLS_NOALLOC_MAX_CASES = 64
 
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "cls_num_cases": ([H], i),
         "cls_debug_philox": ([P(u32), i, P(u32), P(u32)], i),
         "cls_debug_uniform": ([u64, u32, P(u64), P(u64), i, P(d), P(ctypes.c_float)], i),
+        "cls_debug_math": ([P(u64), i, P(d), P(d), P(d)], i),
         "cls_run_noalloc": ([P(d), i, u64, u64, u64, i, i, H, H, H, H], i),
         "cls_autotune": ([H, u64, u64, H], i),
         "cls_finalize_raw": ([P(cls_raw_t), P(d), P(u64), d, P(cls_tallies_t)], i),
@@ -274,6 +275,15 @@ def debug_uniform(seed: int, case_id: int, h, j):
     _check(load().cls_debug_uniform(seed, case_id, _ptr(h, ctypes.c_uint64), _ptr(j, ctypes.c_uint64), n,
                                     _ptr(o64), _ptr(o32, ctypes.c_float)), "cls_debug_uniform")
     return o64, o32
+
+
+def debug_math(k):
+    """cls_debug_math: the FP64 walk's ln(1 - u), sin(2 pi u), cos(2 pi u) for u = k 2^-53."""
+    k = np.ascontiguousarray(k, dtype=np.uint64)
+    n = k.size
+    ln1m, sn, cs = np.zeros(n), np.zeros(n), np.zeros(n)
+    _check(load().cls_debug_math(_ptr(k, ctypes.c_uint64), n, _ptr(ln1m), _ptr(sn), _ptr(cs)), "cls_debug_math")
+    return ln1m, sn, cs
 
 
 def run_noalloc(params, first: int, n: int, seed: int, nbatch: int, nbins_stride: int, d_flux: int, d_stats: int,

@@ -51,6 +51,17 @@ __global__ void uniform_kernel(uint64_t seed, uint32_t case_id, const uint64_t *
     o32[i] = u32;
 }
 
+__global__ void math_kernel(const uint64_t *k, int n, double *out) {
+    cls::load_math_tables<double>(threadIdx.x, blockDim.x);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double sn, cs;
+    cls::sincos_2pi_k(k[i], &sn, &cs);
+    out[3 * (size_t)i + 0] = cls::log_one_minus(k[i]);
+    out[3 * (size_t)i + 1] = sn;
+    out[3 * (size_t)i + 2] = cs;
+}
 }  // namespace
 
 extern "C" int cls_debug_philox(const uint32_t *in, int n, uint32_t *ours, uint32_t *theirs) {
@@ -91,4 +102,28 @@ extern "C" int cls_debug_uniform(uint64_t seed, uint32_t case_id, const uint64_t
     if (e == cudaSuccess && out32) e = cudaMemcpy(out32, d32, n * sizeof(float), cudaMemcpyDeviceToHost);
     cudaFree(dh);
     return e == cudaSuccess ? CLS_OK : CLS_E_CUDA;
+}
+
+extern "C" int cls_debug_math(const uint64_t *k, int n, double *ln1m, double *sin2pi, double *cos2pi) {
+    if (!k || n < 1) return CLS_E_INVAL;
+    for (int i = 0; i < n; ++i)
+        if (k[i] >= (1ull << 53)) return CLS_E_INVAL;
+    uint64_t *dk = nullptr;
+    if (cudaMalloc(&dk, (size_t)n * (sizeof(uint64_t) + 3 * sizeof(double))) != cudaSuccess) return CLS_E_NOMEM;
+    double *dout = reinterpret_cast<double *>(dk + n);
+    cudaError_t e = cudaMemcpy(dk, k, n * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        math_kernel<<<(n + 255) / 256, 256>>>(dk, n, dout);
+        e = cudaGetLastError();
+    }
+    std::vector<double> host(3 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(host.data(), dout, host.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(dk);
+    if (e != cudaSuccess) return CLS_E_CUDA;
+    for (int i = 0; i < n; ++i) {
+        if (ln1m) ln1m[i] = host[3 * (size_t)i];
+        if (sin2pi) sin2pi[i] = host[3 * (size_t)i + 1];
+        if (cos2pi) cos2pi[i] = host[3 * (size_t)i + 2];
+    }
+    return CLS_OK;
 }

@@ -19,10 +19,81 @@
 #include <cuda_runtime.h>
 
 #include "cls_internal.h"
+#include "cls_math_tables.h"
 
 namespace cls {
 
 #define CLS_FULL_MASK 0xffffffffu
+
+// ------------------------------------------------- FP64 logarithm, sine/cosine
+// The FP64 walk takes its logarithms and its sine/cosine pairs straight from
+// the 53-bit integer k of a draw (u = k 2^-53), through tables that every FP64
+// kernel copies into shared memory when it starts (load_math_tables).  Both
+// keep the FP64 pipe, the walk's bottleneck, to about a dozen operations each.
+struct __align__(16) LogEntry {
+    double F, t_hi, t_lo, pad;
+};
+__shared__ LogEntry cls_log_tab[CLS_LOG_TABLE_N];
+__shared__ double2 cls_sincos_tab[CLS_SINCOS_TABLE_N];
+
+template <typename P>
+__device__ __forceinline__ void load_math_tables(int tid, int nthreads) {
+    if constexpr (sizeof(P) == 8) {
+        for (int i = tid; i < CLS_LOG_TABLE_N; i += nthreads)
+            cls_log_tab[i] = LogEntry{cls_log_table_init[i][0], cls_log_table_init[i][1], cls_log_table_init[i][2], 0.0};
+        for (int i = tid; i < CLS_SINCOS_TABLE_N; i += nthreads)
+            cls_sincos_tab[i] = make_double2(cls_sincos_table_init[i][0], cls_sincos_table_init[i][1]);
+    }
+}
+
+// the integer E as a double, exactly (|E| < 2^51), by the 1.5 2^52 shift
+__device__ __forceinline__ double small_int_to_double(long long e) {
+    return __longlong_as_double(0x4338000000000000ll + e) - 0x1.8p52;
+}
+
+// ln(1 - u) for u = k 2^-53, 0 <= k < 2^53: the table-driven method of
+// Tang (ACM TOMS 16, 1990).  1 - u = n 2^-53 = m 2^e with m in [1, 2); the
+// top 8 fraction bits i of m select F_i ~ 1/c_i, so that r = m F_i - 1 has
+// |r| <= 2^-9 and ln(1 - u) = E ln 2 + T_i + ln(1 + r), with ln(1 + r) from
+// its Taylor series to r^6 (truncation below 2^-56 relative).  Arguments with
+// u < 2^-9 use r = -u exactly (table entry 256), and u = 0 gives 0.  The head
+// E ln2_hi + T_hi is exact; the result is within about one ulp.
+__device__ __forceinline__ double log_one_minus(unsigned long long k) {
+    const unsigned long long n = (1ull << 53) - k - (k == 0ull ? 1ull : 0ull);
+    const int s = __clzll((long long)n) - 11;                     // n << s: leading bit at bit 52
+    const unsigned long long mb = (n << s) + (1022ull << 52);     // bits of m in [1, 2)
+    const int idx = (k >> 44) == 0ull ? 256 : (int)((mb >> 44) & 255ull);
+    const int E = (idx >= 128 ? 1 : 0) - 1 - s;                   // e = -1 - s, plus the folded ln 2
+    const double m = __longlong_as_double((long long)mb);
+    const double2 Ft = *reinterpret_cast<const double2 *>(&cls_log_tab[idx].F);
+    const double t_lo = cls_log_tab[idx].t_lo;
+    const double r = fma(m, Ft.x, -1.0);
+    const double Ed = small_int_to_double(E);
+    const double r2 = r * r;
+    double q = fma(r, -1.0 / 6.0, 1.0 / 5.0);  // q = -1/2 + r/3 - r^2/4 + r^3/5 - r^4/6
+    q = fma(q, r, -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    const double head = fma(Ed, CLS_LN2_HI, Ft.y);  // exact
+    const double tail = fma(Ed, CLS_LN2_LO, t_lo);
+    const double res = head + (r + fma(r2, q, tail));
+    return k == 0ull ? 0.0 : res;
+}
+
+// (sin, cos) of 2 pi u for u = k 2^-53: angle addition from the nearest
+// tabulated angle 2 pi j/256, |delta| <= pi/256, with the Taylor series of
+// sin delta to delta^7 and of cos delta - 1 to delta^6.
+__device__ __forceinline__ void sincos_2pi_k(unsigned long long k, double *sn, double *cs) {
+    const unsigned long long j = (k + (1ull << 44)) >> 45;       // nearest multiple of 2^45, 0..256
+    const long long t = (long long)k - (long long)(j << 45);     // in [-2^44, 2^44)
+    const double2 sc = cls_sincos_tab[j & 255ull];
+    const double d = small_int_to_double(t) * 0x1.921fb54442d18p-51;  // 2 pi t 2^-53
+    const double d2 = d * d;
+    const double cm1 = d2 * fma(d2, fma(d2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
+    const double sd = fma(d * d2, fma(d2, fma(d2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), d);
+    *sn = sc.x + fma(sc.y, sd, sc.x * cm1);
+    *cs = sc.y + fma(sc.y, cm1, -(sc.x * sd));
+}
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -84,16 +155,28 @@ struct Real<double> {
     static __device__ __forceinline__ double L(const CaseParams &c) { return c.L; }
     static __device__ __forceinline__ double dx(const CaseParams &c) { return c.dx; }
     static __device__ __forceinline__ double inv_dx(const CaseParams &c) { return c.inv_dx; }
-    // l_c = -ln(1 - u) / Sigma_m, as -ln(1 - u) * (1 / Sigma_m)
-    static __device__ __forceinline__ double collision(const CaseParams &c, int m, double one_minus_u) {
-        return -log(one_minus_u) * c.inv_sigma[m];
+    static __device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+    // min(floor(t), cap) for finite t >= 0, from the bit pattern
+    static __device__ __forceinline__ int floor_index(double t, int cap) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+        const int e = (int)(b >> 52) - 1023;
+        const int sh = min(max(52 - e, 0), 63);
+        const unsigned long long v = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh;
+        return (int)min(v, (unsigned long long)cap);
     }
-    static __device__ __forceinline__ double interface(const CaseParams &c, int m, double one_minus_u) {
-        return -c.lambda[m] * log(one_minus_u);
+    static __device__ __forceinline__ double of_int(int k) { return small_int_to_double(k); }
+    // l_c = -ln(1 - u) / Sigma_m, as -ln(1 - u) * (1 / Sigma_m), from the draw's words
+    static __device__ __forceinline__ double collision(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
+        return -log_one_minus(k53(hi, lo)) * c.inv_sigma[m];
+    }
+    static __device__ __forceinline__ double interface(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
+        return -c.lambda[m] * log_one_minus(k53(hi, lo));
     }
     static __device__ __forceinline__ double recip(double a) { return 1.0 / a; }
-    // (sin, cos) of 2 pi u
-    static __device__ __forceinline__ void sincos_2pi(double u, double *s, double *co) { sincospi(2.0 * u, s, co); }
+    // (sin, cos) of 2 pi u from the draw's words
+    static __device__ __forceinline__ void sincos_2pi(uint32_t hi, uint32_t lo, double *s, double *co) {
+        sincos_2pi_k(k53(hi, lo), s, co);
+    }
 };
 
 // FP32 tracking: position, direction and distances in float; shared-memory
@@ -123,14 +206,19 @@ struct Real<float> {
     static __device__ __forceinline__ float L(const CaseParams &c) { return c.L_f; }
     static __device__ __forceinline__ float dx(const CaseParams &c) { return c.dx_f; }
     static __device__ __forceinline__ float inv_dx(const CaseParams &c) { return c.inv_dx_f; }
-    static __device__ __forceinline__ float collision(const CaseParams &c, int m, float one_minus_u) {
-        return -__logf(one_minus_u) * c.inv_sigma_f[m];
+    static __device__ __forceinline__ bool is_zero(float x) { return x == 0.0f; }
+    static __device__ __forceinline__ int floor_index(float t, int cap) { return min((int)t, cap); }
+    static __device__ __forceinline__ float of_int(int k) { return (float)k; }
+    static __device__ __forceinline__ float collision(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
+        return -__logf(one_minus(hi, lo)) * c.inv_sigma_f[m];
     }
-    static __device__ __forceinline__ float interface(const CaseParams &c, int m, float one_minus_u) {
-        return -c.lambda_f[m] * __logf(one_minus_u);
+    static __device__ __forceinline__ float interface(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
+        return -c.lambda_f[m] * __logf(one_minus(hi, lo));
     }
     static __device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
-    static __device__ __forceinline__ void sincos_2pi(float u, float *s, float *co) { sincospif(2.0f * u, s, co); }
+    static __device__ __forceinline__ void sincos_2pi(uint32_t hi, uint32_t lo, float *s, float *co) {
+        sincospif(2.0f * uniform(hi, lo), s, co);
+    }
 };
 
 // ----------------------------------------------------------- history state
@@ -144,8 +232,15 @@ struct History {
     uint32_t c2, c3;  // words 2, 3 of the last Philox block (odd draws)
     uint32_t h_lo, h_hi, cid;
     uint32_t events, n_coll, n_int, n_refl;
+    uint32_t pend;    // direction still to draw (DIR_*), 3D and extruded geometries
     P track0, track1; // per-history track length in material 0 / 1
 };
+
+// A new direction of the 3D or extruded walk is drawn by resolve_direction,
+// which the history tracker runs once per step for every lane that needs one:
+// the lanes born this step and those that scattered in the last one share one
+// pass through the sqrt, sine/cosine and reciprocal arithmetic.
+enum : uint32_t { DIR_NONE = 0, DIR_SCATTER = 1, DIR_SOURCE_COSINE = 2, DIR_SOURCE_ISOTROPIC = 3 };
 
 // One flight's contribution to the mesh: a0 into bin k0, a1 into bin k1
 // (k1 > k0) and c into each interior bin k0 < k < k1.  Empty when k1 < k0.
@@ -187,6 +282,14 @@ __device__ __forceinline__ P draw_one_minus(History<P> &s, const RoundKeys &key)
     return Real<P>::one_minus(hi, lo);
 }
 
+// (sin, cos) of 2 pi u for the next draw u
+template <typename P>
+__device__ __forceinline__ void draw_sincos_2pi(History<P> &s, const RoundKeys &key, P *sn, P *cs) {
+    uint32_t hi, lo;
+    draw_words(s, key, hi, lo);
+    Real<P>::sincos_2pi(hi, lo, sn, cs);
+}
+
 // whether the next draw is below the value whose thresholds are given
 template <typename P>
 __device__ __forceinline__ bool draw_below(History<P> &s, const RoundKeys &key, unsigned long long thr53, uint32_t thr24) {
@@ -210,13 +313,35 @@ __device__ __forceinline__ void set_direction(History<P> &s, P wx, P wy, P wz) {
     s.w[0] = wx;
     s.w[1] = wy;
     s.w[2] = wz;
-    s.iw[0] = (wx != P(0)) ? R::recip(wx) : R::inf();
-    s.iw[1] = (wy != P(0)) ? R::recip(wy) : R::inf();
-    s.iw[2] = (wz != P(0)) ? R::recip(wz) : R::inf();
+    s.iw[0] = R::is_zero(wx) ? R::inf() : R::recip(wx);
+    s.iw[1] = R::is_zero(wy) ? R::inf() : R::recip(wy);
+    s.iw[2] = R::is_zero(wz) ? R::inf() : R::recip(wz);
 }
 
-// Source: position and direction first, then the material label.
-template <typename P, int G = 0>
+// Draw the pending direction of a 3D or extruded walk: mu, then the azimuth
+// phi, then (at the source) the material label, in the order of the serial
+// walk.  Cosine-law incidence (paper Sec. 4.3): mu = sqrt(xi) about +x,
+// omega = (mu, st cos phi, st sin phi); isotropic (scattering, volume source):
+// mu = 2 xi - 1, omega = (st cos phi, st sin phi, mu); st = sqrt(1 - mu^2).
+template <typename P>
+__device__ __forceinline__ void resolve_direction(History<P> &s, const CaseParams &cp, const RoundKeys &key) {
+    if (s.pend == DIR_NONE) return;
+    const bool cosine = s.pend == DIR_SOURCE_COSINE;
+    const P u = draw(s, key);
+    const P mu = cosine ? sqrt(u) : P(2) * u - P(1);
+    P sn, cs;
+    draw_sincos_2pi(s, key, &sn, &cs);
+    const P st = sqrt(P(1) - mu * mu);
+    const P a = st * cs, b = st * sn;
+    set_direction(s, cosine ? mu : a, cosine ? a : b, cosine ? b : mu);
+    if (s.pend != DIR_SCATTER) s.m = draw_below(s, key, cp.thr_p053, cp.thr_p024) ? 0 : 1;
+    s.pend = DIR_NONE;
+}
+
+// Source: position and direction first, then the material label.  With
+// DEFER, a 3D or extruded source leaves its direction and label pending for
+// the caller's resolve_direction.
+template <typename P, int G = 0, bool DEFER = false>
 __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, const RoundKeys &key, uint64_t h) {
     using R = Real<P>;
     const int gd = geometry<G>(cp);
@@ -225,22 +350,23 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, cons
     s.cid = cp.case_id;
     s.j = 0;
     s.events = s.n_coll = s.n_int = s.n_refl = 0;
+    s.pend = DIR_NONE;
     s.track0 = s.track1 = P(0);
     s.r[0] = P(0);
     s.r[1] = P(0);
     s.r[2] = P(0);
-    if (cp.source == 1) {  // suite II: uniform position, isotropic direction
-        const P L = R::L(cp);
+    const P L = R::L(cp);
+    if (gd == 3 || gd == 2) {
+        if (cp.source == 1) s.r[0] = L * draw(s, key);  // suite II: uniform position, isotropic direction
+        s.r[1] = L * draw(s, key);
+        if (gd == 3) s.r[2] = L * draw(s, key);
+        s.pend = (cp.source == 1) ? DIR_SOURCE_ISOTROPIC : DIR_SOURCE_COSINE;
+        if (!DEFER) resolve_direction(s, cp, key);
+        return;
+    }
+    if (cp.source == 1) {
         s.r[0] = L * draw(s, key);
-        if (gd == 3 || gd == 2) {
-            s.r[1] = L * draw(s, key);
-            if (gd == 3) s.r[2] = L * draw(s, key);
-            const P mu = P(2) * draw(s, key) - P(1);
-            P sn, cs;
-            R::sincos_2pi(draw(s, key), &sn, &cs);
-            const P st = sqrt(P(1) - mu * mu);
-            set_direction(s, st * cs, st * sn, mu);
-        } else if (gd == 11 || gd == 13) {
+        if (gd == 11 || gd == 13) {
             set_direction(s, P(2) * draw(s, key) - P(1), P(0), P(0));
         } else {
             uint32_t hi, lo;
@@ -253,15 +379,6 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, cons
             s.iw[1] = R::inf();
             s.iw[2] = R::inf();
         }
-    } else if (gd == 3 || gd == 2) {
-        const P L = R::L(cp);
-        s.r[1] = L * draw(s, key);
-        if (gd == 3) s.r[2] = L * draw(s, key);
-        const P mu = sqrt(draw(s, key));  // cosine law mu' = sqrt(xi)
-        P sn, cs;
-        R::sincos_2pi(draw(s, key), &sn, &cs);
-        const P st = sqrt(P(1) - mu * mu);
-        set_direction(s, mu, st * cs, st * sn);
     } else if (gd == 11 || gd == 13) {
         set_direction(s, sqrt(draw(s, key)), P(0), P(0));  // slab, projected box: mu = sqrt(xi)
     } else {
@@ -315,38 +432,52 @@ __device__ __forceinline__ void plan_flight(Flight<P> &f, History<P> &s, const C
     else s.track1 += l;
     f.k0 = 0;
     f.k1 = -1;
-    if (!(l > P(0))) return;
+    if (!R::pos(l)) return;
     const int nb = cp.nbins;
     const P inv_dx = R::inv_dx(cp);
-    const P wx = s.w[0];
-    if (wx == P(0)) {
-        const int k = min(max((int)floor(x0 * inv_dx), 0), nb - 1);
+    // the x-extent clipped to [0, L]; every value below is >= 0, so min and
+    // max are the integer comparisons of R::lt
+    const P a = R::nonneg(x0), b = R::nonneg(x1);
+    if (R::is_zero(s.w[0])) {
+        const int k = R::floor_index(a * inv_dx, nb - 1);
         f.k0 = f.k1 = k;
         f.a0 = l;
         return;
     }
     const P L = R::L(cp);
-    const P lo = fmax(fmin(x0, x1), P(0));
-    const P hi = fmin(fmax(x0, x1), L);
-    const P iaw = fabs(s.iw[0]);
-    const int k0 = min(max((int)floor(lo * inv_dx), 0), nb - 1);
-    const int k1 = min(max((int)floor(hi * inv_dx), 0), nb - 1);
+    const P lo = R::lt(a, b) ? a : b;
+    P hi = R::lt(a, b) ? b : a;
+    hi = R::lt(L, hi) ? L : hi;
+    const int k0 = R::floor_index(lo * inv_dx, nb - 1);
+    const int k1 = R::floor_index(hi * inv_dx, nb - 1);
     f.k0 = k0;
     f.k1 = k1;
     if (k0 == k1) {  // the flight lies inside one bin: its length itself
         f.a0 = l;
         return;
     }
+    const P iaw = fabs(s.iw[0]);
     const P dx = R::dx(cp);
-    f.a0 = fmax((P)(k0 + 1) * dx - lo, P(0)) * iaw;
-    f.a1 = fmax(hi - (P)k1 * dx, P(0)) * iaw;
+    f.a0 = R::nonneg(R::of_int(k0 + 1) * dx - lo) * iaw;
+    f.a1 = R::nonneg(hi - R::of_int(k1) * dx) * iaw;
     f.c = dx * iaw;
+}
+
+// Distance along the flight to the face ahead on one axis: (L - r)/omega
+// moving up, (0 - r)/omega moving down, clamped at 0; infinite when omega is
+// +-0.  One multiply on every lane, no branch.
+template <typename P>
+__device__ __forceinline__ P face_distance(P r, P w, P iw, P L) {
+    using R = Real<P>;
+    const P target = R::pos(w) ? L : P(0);
+    const P d = R::nonneg((target - r) * iw);
+    return R::is_zero(w) ? R::inf() : d;
 }
 
 // One event of Algorithm A.  Fills the flight to score and returns -1 while
 // the history continues, else the terminating event (EV_LEAK_X0, EV_LEAK_XL,
 // EV_ABSORB, EV_CAPPED).
-template <typename P, bool TRACE, int G = 0>
+template <typename P, bool TRACE, int G = 0, bool DEFER = false>
 __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const RoundKeys &key, uint32_t max_events,
                                     Flight<P> &f, TraceSink *tr) {
     using R = Real<P>;
@@ -363,37 +494,30 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
     const P L = R::L(cp);
 
     // collision, then interface distance
-    const P om_c = draw_one_minus(s, key);
-    const P l_c = (R::sigma(cp, m) > P(0)) ? R::nonneg(R::collision(cp, m, om_c)) : INF;
-    const P om_i = draw_one_minus(s, key);
-    P l_i = R::interface(cp, m, om_i);
+    uint32_t hi, lo;
+    draw_words(s, key, hi, lo);
+    const P l_c = R::pos(R::sigma(cp, m)) ? R::nonneg(R::collision(cp, m, hi, lo)) : INF;
+    draw_words(s, key, hi, lo);
+    P l_i = R::interface(cp, m, hi, lo);
     if (gd == 11) l_i *= fabs(s.iw[0]);  // slab: the chord projected on x, Lambda/|mu|
     else if (gd == 2) l_i /= sqrt(P(1) - s.w[2] * s.w[2]);  // extruded: in-plane chord along the flight
     l_i = R::nonneg(l_i);
 
     // boundary distance: x faces, then the lateral faces of the box
-    P l_b = INF;
-    int face = -1;  // 0: x = 0, 1: x = L, 2: lateral
-    if (R::pos(s.w[0])) {
-        l_b = (L - s.r[0]) * s.iw[0];
-        face = 1;
-    } else if (R::neg(s.w[0])) {
-        l_b = (P(0) - s.r[0]) * s.iw[0];
-        face = 0;
-    }
-    l_b = R::nonneg(l_b);
+    // (the face ahead minus the position) / omega, on every lane; infinite for omega = 0
+    int face = R::pos(s.w[0]) ? 1 : 0;  // 0: x = 0, 1: x = L, 2: lateral
+    P l_b = face_distance(s.r[0], s.w[0], s.iw[0], L);
     P l_y = INF, l_z = INF;
     const bool box = gd == 3;
-    if (box || gd == 2) {  // lateral faces: y (and z in the box; the extruded geometry has none)
-        if (R::pos(s.w[1])) l_y = R::nonneg((L - s.r[1]) * s.iw[1]);
-        else if (R::neg(s.w[1])) l_y = R::nonneg((P(0) - s.r[1]) * s.iw[1]);
+    const bool lateral = box || gd == 2;  // lateral faces: y (and z in the box; the extruded geometry has none)
+    if (lateral) {
+        l_y = face_distance(s.r[1], s.w[1], s.iw[1], L);
         if (R::lt(l_y, l_b)) {
             l_b = l_y;
             face = 2;
         }
         if (box) {
-            if (R::pos(s.w[2])) l_z = R::nonneg((L - s.r[2]) * s.iw[2]);
-            else if (R::neg(s.w[2])) l_z = R::nonneg((P(0) - s.r[2]) * s.iw[2]);
+            l_z = face_distance(s.r[2], s.w[2], s.iw[2], L);
             if (R::lt(l_z, l_b)) {
                 l_b = l_z;
                 face = 2;
@@ -401,52 +525,48 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
         }
     }
 
-    if (R::le(l_b, l_c) && R::le(l_b, l_i)) {
-        if (face != 2) {
-            const P xf = (face == 0) ? P(0) : L;
-            plan_flight(f, s, cp, s.r[0], xf, l_b, m);
-            s.r[0] = xf;
-            if (box || gd == 2) s.r[1] += l_b * s.w[1];
-            if (box) s.r[2] += l_b * s.w[2];
-            const int ev = (face == 0) ? EV_LEAK_X0 : EV_LEAK_XL;
-            trace_row<P, TRACE>(tr, ev, s, (double)l_b);
-            return ev;
-        }
-        const P x1 = s.r[0] + l_b * s.w[0];
-        plan_flight(f, s, cp, s.r[0], x1, l_b, m);
-        s.r[0] = x1;
-        if (R::eq(l_y, l_b)) {
+    // the event: boundary, else collision, else interface.  Every lane then
+    // moves and scores its flight on one converged path.
+    const bool bnd = R::le(l_b, l_c) && R::le(l_b, l_i);
+    const bool coll = !bnd && R::le(l_c, l_i);
+    const bool leak = bnd && face != 2;
+    const P l = bnd ? l_b : (coll ? l_c : l_i);
+    const P x1 = leak ? ((face == 0) ? P(0) : L) : s.r[0] + l * s.w[0];
+    plan_flight(f, s, cp, s.r[0], x1, l, m);
+    s.r[0] = x1;
+    if (lateral) {
+        if (bnd && face == 2 && R::eq(l_y, l_b)) {  // specular reflection on a y face
             s.r[1] = R::pos(s.w[1]) ? L : P(0);
             s.w[1] = -s.w[1];
             s.iw[1] = -s.iw[1];
         } else {
-            s.r[1] += l_b * s.w[1];
+            s.r[1] += l * s.w[1];
         }
-        if (R::eq(l_z, l_b)) {
+    }
+    if (box) {
+        if (bnd && face == 2 && R::eq(l_z, l_b)) {  // and/or on a z face
             s.r[2] = R::pos(s.w[2]) ? L : P(0);
             s.w[2] = -s.w[2];
             s.iw[2] = -s.iw[2];
-        } else if (box) {
-            s.r[2] += l_b * s.w[2];
+        } else {
+            s.r[2] += l * s.w[2];
         }
+    }
+    if (leak) {
+        const int ev = (face == 0) ? EV_LEAK_X0 : EV_LEAK_XL;
+        trace_row<P, TRACE>(tr, ev, s, (double)l);
+        return ev;
+    }
+    if (bnd) {
         ++s.n_refl;
-        trace_row<P, TRACE>(tr, EV_REFLECT, s, (double)l_b);
+        trace_row<P, TRACE>(tr, EV_REFLECT, s, (double)l);
         return -1;
     }
-
-    const bool coll = R::le(l_c, l_i);
-    const P l = coll ? l_c : l_i;
-    const P x1 = s.r[0] + l * s.w[0];
-    plan_flight(f, s, cp, s.r[0], x1, l, m);
-    s.r[0] = x1;
-    if (box || gd == 2) s.r[1] += l * s.w[1];
-    if (box) s.r[2] += l * s.w[2];
     if (coll) {
         ++s.n_coll;
         if (draw_below(s, key, R::thr_c53(cp, m), R::thr_c24(cp, m))) {
             if (gd == 1) {
                 // u < 1/2 exactly when the top bit of the draw is clear
-                uint32_t hi, lo;
                 draw_words(s, key, hi, lo);
                 const P w = (hi >> 31) == 0u ? P(1) : P(-1);
                 s.w[0] = w;
@@ -454,11 +574,8 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
             } else if (gd == 11 || gd == 13) {
                 set_direction(s, P(2) * draw(s, key) - P(1), P(0), P(0));  // mu = 2 xi - 1
             } else {
-                const P mu = P(2) * draw(s, key) - P(1);
-                P sn, cs;
-                R::sincos_2pi(draw(s, key), &sn, &cs);
-                const P st = sqrt(P(1) - mu * mu);
-                set_direction(s, st * cs, st * sn, mu);
+                s.pend = DIR_SCATTER;  // mu = 2 xi - 1, then phi
+                if (!DEFER) resolve_direction(s, cp, key);
             }
             trace_row<P, TRACE>(tr, EV_SCATTER, s, (double)l);
             return -1;
@@ -662,6 +779,8 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
     const int rb = a.region_bytes;
     unsigned char *regions = smem + (size_t)warp * 2 * rb;
     for (int i = lane; i < 2 * rb / 8; i += 32) reinterpret_cast<unsigned long long *>(regions)[i] = 0ull;
+    load_math_tables<P>(threadIdx.x, blockDim.x);
+    if constexpr (sizeof(P) == 8) __syncthreads();
     __syncwarp();
 
     // warp-uniform feeding state
@@ -740,7 +859,7 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
                 lcase = a.runs[feed_run].case_index;
                 lreg = feed_reg;
                 lbatch = feed_batch;
-                source<P, G>(s, a.cases[lcase], key, cursor + rank);
+                source<P, G, true>(s, a.cases[lcase], key, cursor + rank);
                 alive = true;
             }
             if (feed_reg == 0) fed0 += (int)take;
@@ -752,7 +871,11 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
         f.k0 = 0;
         f.k1 = -1;
         int out = -1;
-        if (alive) out = step<P, false, G>(s, a.cases[lcase], key, a.max_events, f, nullptr);
+        if (alive) {
+            // directions of the lanes born in this round and of those that scattered in the last
+            resolve_direction(s, a.cases[lcase], key);
+            out = step<P, false, G, true>(s, a.cases[lcase], key, a.max_events, f, nullptr);
+        }
         const uint32_t goff = (lreg == 2) ? ((uint32_t)lcase * (uint32_t)a.t.nbatch + lbatch) * (uint32_t)a.t.nbins_stride : 0u;
         warp_deposit<P>(regions, rb, lreg, a.t.flux, goff, f, lane);
         if (out >= 0) {
@@ -784,6 +907,7 @@ __global__ void trace_kernel(const TraceArgs a) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const CaseParams &cp = a.cases[a.case_index];
     const RoundKeys key = make_round_keys(a.seed);
+    load_math_tables<P>(0, 1);
     History<P> s;
     Flight<P> f;
     source<P>(s, cp, key, a.history);

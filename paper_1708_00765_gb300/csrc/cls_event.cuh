@@ -174,6 +174,8 @@ __global__ void __launch_bounds__(256, EventMinBlocks<P>::value) event_kernel(co
     const int rb = a.region_bytes;
     unsigned char *regions = smem + (size_t)warp * 2 * rb;
     for (int i = lane; i < 2 * rb / 8; i += 32) reinterpret_cast<unsigned long long *>(regions)[i] = 0ull;
+    load_math_tables<P>(threadIdx.x, blockDim.x);
+    if constexpr (sizeof(P) == 8) __syncthreads();
     __syncwarp();
     const uint32_t W = a.bank_slots;  // particles per warp and buffer (multiple of 32)
     const size_t buf_bytes = (size_t)W * 16 * BankLayout<P>::kFields;

@@ -87,6 +87,30 @@ def test_uniform_mapping_matches_oracle():
         assert np.array_equal(u32.astype(np.float64), np.floor(ref * 2**24) / 2**24)
 
 
+def test_device_log_and_sincos_accuracy():
+    """The FP64 walk's ln(1 - u) is within one ulp and its sin/cos(2 pi u)
+    within 2^-52 of extended-precision references, over random draws and the
+    edges of the table ranges (u = 0, u < 2^-9, u near 1/2 and 1)."""
+    rng = np.random.default_rng(11)
+    edge = [0, 1, 2, 3, 2**44 - 1, 2**44, 2**44 + 1, 2**45 - 1, 2**45, 2**52 - 1, 2**52, 2**52 + 1,
+            2**53 - 2, 2**53 - 1, 3 * 2**51, 2**51, 2**50]
+    k = np.concatenate([np.array(edge, dtype=np.uint64),
+                        rng.integers(0, 2**53, size=200_000, dtype=np.uint64),
+                        (rng.integers(0, 2**53, size=50_000, dtype=np.uint64)
+                         >> rng.integers(0, 53, size=50_000).astype(np.uint64))])
+    ln1m, sn, cs = cls.debug_math(k)
+    ld = np.longdouble
+    n = ld(2) ** 53
+    ref_log = np.log((n - k.astype(ld)) / n)
+    ulp = np.spacing(np.abs(ref_log.astype(np.float64)))
+    err = np.abs(ln1m.astype(ld) - ref_log) / ulp.astype(ld)
+    assert ln1m[0] == 0.0 and float(err[1:].max()) <= 1.0, float(err.max())
+    two_pi = ld("6.283185307179586476925286766559005768394")
+    ang = two_pi * (k.astype(ld) / n)
+    assert float(np.max(np.abs(sn.astype(ld) - np.sin(ang)))) <= 2.0**-52
+    assert float(np.max(np.abs(cs.astype(ld) - np.cos(ang)))) <= 2.0**-52
+
+
 # -------------------------------------------------------------- traces
 
 @pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10, workloads.suite_case("1c", nbins=10),
