@@ -256,11 +256,14 @@ int cls_debug_uniform(uint64_t seed, uint32_t case_id, const uint64_t *h, const 
 
 /* The FP64 walk's elementary functions of a draw: for u = k[i] 2^-53
  * (0 <= k[i] < 2^53), ln1m[i] = ln(1 - u) (the distances l_c = -ln(1-u)/Sigma
- * and l_i = -Lambda ln(1-u) of paper Sec. 4) and sin2pi[i], cos2pi[i] =
- * sin, cos of 2 pi u (the azimuth of isotropic directions, paper Sec. 4.3).
- * Host arrays of n entries; any output may be NULL; synchronous.
+ * and l_i = -Lambda ln(1-u) of paper Sec. 4), sin2pi[i], cos2pi[i] = sin, cos
+ * of 2 pi u (the azimuth of isotropic directions, paper Sec. 4.3), u[i] = u,
+ * mu[i] = 2u - 1 (an isotropic direction cosine) and recip_mu[i] = 1/mu[i]
+ * (the inverse direction cosines of the boundary distances).  Host arrays of
+ * n entries; any output may be NULL; synchronous.
  * Errors: CLS_E_INVAL (k[i] >= 2^53, n < 1), CLS_E_CUDA, CLS_E_NOMEM. */
-int cls_debug_math(const uint64_t *k, int n, double *ln1m, double *sin2pi, double *cos2pi);
+int cls_debug_math(const uint64_t *k, int n, double *ln1m, double *sin2pi, double *cos2pi, double *u, double *mu,
+                   double *recip_mu);
 
 /* ------------------------------------------------- allocation-free run */
 

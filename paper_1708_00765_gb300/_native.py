@@ -109,7 +109,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "cls_num_cases": ([H], i),
         "cls_debug_philox": ([P(u32), i, P(u32), P(u32)], i),
         "cls_debug_uniform": ([u64, u32, P(u64), P(u64), i, P(d), P(ctypes.c_float)], i),
-        "cls_debug_math": ([P(u64), i, P(d), P(d), P(d)], i),
+        "cls_debug_math": ([P(u64), i, P(d), P(d), P(d), P(d), P(d), P(d)], i),
         "cls_run_noalloc": ([P(d), i, u64, u64, u64, i, i, H, H, H, H], i),
         "cls_autotune": ([H, u64, u64, H], i),
         "cls_finalize_raw": ([P(cls_raw_t), P(d), P(u64), d, P(cls_tallies_t)], i),
@@ -278,12 +278,13 @@ def debug_uniform(seed: int, case_id: int, h, j):
 
 
 def debug_math(k):
-    """cls_debug_math: the FP64 walk's ln(1 - u), sin(2 pi u), cos(2 pi u) for u = k 2^-53."""
+    """cls_debug_math: the FP64 walk's ln(1 - u), sin(2 pi u), cos(2 pi u), u, mu = 2u - 1
+    and 1/mu for u = k 2^-53, as a dict of arrays."""
     k = np.ascontiguousarray(k, dtype=np.uint64)
     n = k.size
-    ln1m, sn, cs = np.zeros(n), np.zeros(n), np.zeros(n)
-    _check(load().cls_debug_math(_ptr(k, ctypes.c_uint64), n, _ptr(ln1m), _ptr(sn), _ptr(cs)), "cls_debug_math")
-    return ln1m, sn, cs
+    out = {name: np.zeros(n) for name in ("ln1m", "sin2pi", "cos2pi", "u", "mu", "recip_mu")}
+    _check(load().cls_debug_math(_ptr(k, ctypes.c_uint64), n, *(_ptr(out[name]) for name in out)), "cls_debug_math")
+    return out
 
 
 def run_noalloc(params, first: int, n: int, seed: int, nbatch: int, nbins_stride: int, d_flux: int, d_stats: int,

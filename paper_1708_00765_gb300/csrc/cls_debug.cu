@@ -58,9 +58,15 @@ __global__ void math_kernel(const uint64_t *k, int n, double *out) {
     if (i >= n) return;
     double sn, cs;
     cls::sincos_2pi_k(k[i], &sn, &cs);
-    out[3 * (size_t)i + 0] = cls::log_one_minus(k[i]);
-    out[3 * (size_t)i + 1] = sn;
-    out[3 * (size_t)i + 2] = cs;
+    const uint32_t hi = (uint32_t)(k[i] >> 21), lo = (uint32_t)(k[i] << 11);  // words whose top 53 bits are k
+    const double mu = cls::Real<double>::two_u_minus_one(hi, lo);
+    double *o = out + 6 * (size_t)i;
+    o[0] = cls::log_one_minus(k[i]);
+    o[1] = sn;
+    o[2] = cs;
+    o[3] = cls::Real<double>::uniform(hi, lo);
+    o[4] = mu;
+    o[5] = cls::Real<double>::recip(mu);
 }
 }  // namespace
 
@@ -104,26 +110,26 @@ extern "C" int cls_debug_uniform(uint64_t seed, uint32_t case_id, const uint64_t
     return e == cudaSuccess ? CLS_OK : CLS_E_CUDA;
 }
 
-extern "C" int cls_debug_math(const uint64_t *k, int n, double *ln1m, double *sin2pi, double *cos2pi) {
+extern "C" int cls_debug_math(const uint64_t *k, int n, double *ln1m, double *sin2pi, double *cos2pi, double *u,
+                              double *mu, double *recip_mu) {
     if (!k || n < 1) return CLS_E_INVAL;
     for (int i = 0; i < n; ++i)
         if (k[i] >= (1ull << 53)) return CLS_E_INVAL;
     uint64_t *dk = nullptr;
-    if (cudaMalloc(&dk, (size_t)n * (sizeof(uint64_t) + 3 * sizeof(double))) != cudaSuccess) return CLS_E_NOMEM;
+    if (cudaMalloc(&dk, (size_t)n * (sizeof(uint64_t) + 6 * sizeof(double))) != cudaSuccess) return CLS_E_NOMEM;
     double *dout = reinterpret_cast<double *>(dk + n);
     cudaError_t e = cudaMemcpy(dk, k, n * sizeof(uint64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         math_kernel<<<(n + 255) / 256, 256>>>(dk, n, dout);
         e = cudaGetLastError();
     }
-    std::vector<double> host(3 * (size_t)n);
+    std::vector<double> host(6 * (size_t)n);
     if (e == cudaSuccess) e = cudaMemcpy(host.data(), dout, host.size() * sizeof(double), cudaMemcpyDeviceToHost);
     cudaFree(dk);
     if (e != cudaSuccess) return CLS_E_CUDA;
-    for (int i = 0; i < n; ++i) {
-        if (ln1m) ln1m[i] = host[3 * (size_t)i];
-        if (sin2pi) sin2pi[i] = host[3 * (size_t)i + 1];
-        if (cos2pi) cos2pi[i] = host[3 * (size_t)i + 2];
-    }
+    double *outs[6] = {ln1m, sin2pi, cos2pi, u, mu, recip_mu};
+    for (int c = 0; c < 6; ++c)
+        if (outs[c])
+            for (int i = 0; i < n; ++i) outs[c][i] = host[6 * (size_t)i + c];
     return CLS_OK;
 }

@@ -91,8 +91,8 @@ __device__ __forceinline__ void sincos_2pi_k(unsigned long long k, double *sn, d
     const double d2 = d * d;
     const double cm1 = d2 * fma(d2, fma(d2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
     const double sd = fma(d * d2, fma(d2, fma(d2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), d);
-    *sn = sc.x + fma(sc.y, sd, sc.x * cm1);
-    *cs = sc.y + fma(sc.y, cm1, -(sc.x * sd));
+    *sn = fma(sc.y, sd, fma(sc.x, cm1, sc.x));  // S cos(delta) + C sin(delta)
+    *cs = fma(-sc.x, sd, fma(sc.y, cm1, sc.y)); // C cos(delta) - S sin(delta)
 }
 
 // ------------------------------------------------------------------ Philox
@@ -126,9 +126,24 @@ struct Real<double> {
     static __device__ __forceinline__ unsigned long long k53(uint32_t hi, uint32_t lo) {
         return (((unsigned long long)hi << 32) | (unsigned long long)lo) >> 11;
     }
+    // m 2^e, exactly, for |m| < 2^53: the bit pattern is assembled in the
+    // integer pipes (leading-zero count, shift), keeping the conversion off
+    // the FP64 pipe
+    static __device__ __forceinline__ double scaled_int(long long m, int e) {
+        const unsigned long long sgn = m < 0 ? (1ull << 63) : 0ull;
+        const unsigned long long a = (unsigned long long)(m < 0 ? -m : m);
+        const int p = 63 - __clzll((long long)(a | 1ull));  // leading bit
+        const unsigned long long bits =
+            sgn | ((unsigned long long)(p + e + 1023) << 52) | ((a << (52 - p)) & 0xFFFFFFFFFFFFFull);
+        return a == 0ull ? 0.0 : __longlong_as_double((long long)bits);
+    }
     // 53-bit uniform u = k 2^-53 in [0, 1) from the (hi, lo) output words
     static __device__ __forceinline__ double uniform(uint32_t hi, uint32_t lo) {
-        return (double)k53(hi, lo) * 0x1p-53;
+        return scaled_int((long long)k53(hi, lo), -53);
+    }
+    // 2u - 1 = (k - 2^52) 2^-52, exactly
+    static __device__ __forceinline__ double two_u_minus_one(uint32_t hi, uint32_t lo) {
+        return scaled_int((long long)k53(hi, lo) - (1ll << 52), -52);
     }
     // 1 - u, exactly: (2^53 - k) 2^-53
     static __device__ __forceinline__ double one_minus(uint32_t hi, uint32_t lo) {
@@ -172,7 +187,29 @@ struct Real<double> {
     static __device__ __forceinline__ double interface(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
         return -c.lambda[m] * log_one_minus(k53(hi, lo));
     }
-    static __device__ __forceinline__ double recip(double a) { return 1.0 / a; }
+    // 1/a by Newton-Raphson iteration for the reciprocal, r <- r + r (1 - a r)
+    // (each step squares the relative error; P. Markstein, IBM J. Res. Dev. 34,
+    // 1990), two steps from the FP32 approximate reciprocal of a's leading 24
+    // bits (relative error below 2^-22), so within an ulp or so of 1/a.
+    // |a| outside [2^-120, 2^121) takes the division.
+    static __device__ __forceinline__ double recip(double a) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+        const unsigned int hi = (unsigned int)(b >> 32);
+        const int ex = (int)((hi >> 20) & 0x7FF) - 1023;
+        if (ex < -120 || ex > 120) return 1.0 / a;
+        const unsigned int fb = (hi & 0x80000000u) | ((unsigned int)(ex + 127) << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu);
+        float rf;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
+        const unsigned int rb = __float_as_uint(rf);
+        const int rex = (int)((rb >> 23) & 0xFF) - 127;
+        const unsigned long long db = ((unsigned long long)(rb & 0x80000000u) << 32) |
+                                      ((unsigned long long)(rex + 1023) << 52) | ((unsigned long long)(rb & 0x7FFFFFu) << 29);
+        double r = __longlong_as_double((long long)db);
+        double e = fma(-a, r, 1.0);
+        r = fma(r, e, r);
+        e = fma(-a, r, 1.0);
+        return fma(r, e, r);
+    }
     // (sin, cos) of 2 pi u from the draw's words
     static __device__ __forceinline__ void sincos_2pi(uint32_t hi, uint32_t lo, double *s, double *co) {
         sincos_2pi_k(k53(hi, lo), s, co);
@@ -187,6 +224,7 @@ struct Real<float> {
     using Bin = float;
     // the same draw truncated to its top 24 bits: u = k 2^-24
     static __device__ __forceinline__ float uniform(uint32_t hi, uint32_t) { return (float)(hi >> 8) * 0x1p-24f; }
+    static __device__ __forceinline__ float two_u_minus_one(uint32_t hi, uint32_t lo) { return 2.0f * uniform(hi, lo) - 1.0f; }
     static __device__ __forceinline__ float one_minus(uint32_t hi, uint32_t) {
         return (float)((1u << 24) - (hi >> 8)) * 0x1p-24f;
     }
@@ -282,6 +320,14 @@ __device__ __forceinline__ P draw_one_minus(History<P> &s, const RoundKeys &key)
     return Real<P>::one_minus(hi, lo);
 }
 
+// 2u - 1 for the next draw u (isotropic direction cosine)
+template <typename P>
+__device__ __forceinline__ P draw_iso(History<P> &s, const RoundKeys &key) {
+    uint32_t hi, lo;
+    draw_words(s, key, hi, lo);
+    return Real<P>::two_u_minus_one(hi, lo);
+}
+
 // (sin, cos) of 2 pi u for the next draw u
 template <typename P>
 __device__ __forceinline__ void draw_sincos_2pi(History<P> &s, const RoundKeys &key, P *sn, P *cs) {
@@ -327,8 +373,9 @@ template <typename P>
 __device__ __forceinline__ void resolve_direction(History<P> &s, const CaseParams &cp, const RoundKeys &key) {
     if (s.pend == DIR_NONE) return;
     const bool cosine = s.pend == DIR_SOURCE_COSINE;
-    const P u = draw(s, key);
-    const P mu = cosine ? sqrt(u) : P(2) * u - P(1);
+    uint32_t hi, lo;
+    draw_words(s, key, hi, lo);
+    const P mu = cosine ? sqrt(Real<P>::uniform(hi, lo)) : Real<P>::two_u_minus_one(hi, lo);
     P sn, cs;
     draw_sincos_2pi(s, key, &sn, &cs);
     const P st = sqrt(P(1) - mu * mu);
@@ -367,7 +414,7 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, cons
     if (cp.source == 1) {
         s.r[0] = L * draw(s, key);
         if (gd == 11 || gd == 13) {
-            set_direction(s, P(2) * draw(s, key) - P(1), P(0), P(0));
+            set_direction(s, draw_iso(s, key), P(0), P(0));
         } else {
             uint32_t hi, lo;
             draw_words(s, key, hi, lo);
@@ -572,7 +619,7 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
                 s.w[0] = w;
                 s.iw[0] = w;
             } else if (gd == 11 || gd == 13) {
-                set_direction(s, P(2) * draw(s, key) - P(1), P(0), P(0));  // mu = 2 xi - 1
+                set_direction(s, draw_iso(s, key), P(0), P(0));  // mu = 2 xi - 1
             } else {
                 s.pend = DIR_SCATTER;  // mu = 2 xi - 1, then phi
                 if (!DEFER) resolve_direction(s, cp, key);

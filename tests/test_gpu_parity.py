@@ -87,10 +87,11 @@ def test_uniform_mapping_matches_oracle():
         assert np.array_equal(u32.astype(np.float64), np.floor(ref * 2**24) / 2**24)
 
 
-def test_device_log_and_sincos_accuracy():
+def test_device_log_sincos_reciprocal_accuracy():
     """The FP64 walk's ln(1 - u) is within one ulp and its sin/cos(2 pi u)
-    within 2^-52 of extended-precision references, over random draws and the
-    edges of the table ranges (u = 0, u < 2^-9, u near 1/2 and 1)."""
+    within 2^-52 of extended-precision references; u and mu = 2u - 1 are
+    exact and 1/mu within one ulp; over random draws and the edges of the
+    table ranges (u = 0, u < 2^-9, u near 1/2 and 1)."""
     rng = np.random.default_rng(11)
     edge = [0, 1, 2, 3, 2**44 - 1, 2**44, 2**44 + 1, 2**45 - 1, 2**45, 2**52 - 1, 2**52, 2**52 + 1,
             2**53 - 2, 2**53 - 1, 3 * 2**51, 2**51, 2**50]
@@ -98,17 +99,25 @@ def test_device_log_and_sincos_accuracy():
                         rng.integers(0, 2**53, size=200_000, dtype=np.uint64),
                         (rng.integers(0, 2**53, size=50_000, dtype=np.uint64)
                          >> rng.integers(0, 53, size=50_000).astype(np.uint64))])
-    ln1m, sn, cs = cls.debug_math(k)
+    out = cls.debug_math(k)
     ld = np.longdouble
     n = ld(2) ** 53
+
+    def ulps(got, ref):
+        return np.abs(got.astype(ld) - ref) / np.spacing(np.abs(ref.astype(np.float64))).astype(ld)
+
     ref_log = np.log((n - k.astype(ld)) / n)
-    ulp = np.spacing(np.abs(ref_log.astype(np.float64)))
-    err = np.abs(ln1m.astype(ld) - ref_log) / ulp.astype(ld)
-    assert ln1m[0] == 0.0 and float(err[1:].max()) <= 1.0, float(err.max())
+    assert out["ln1m"][0] == 0.0 and float(ulps(out["ln1m"], ref_log)[1:].max()) <= 1.0
     two_pi = ld("6.283185307179586476925286766559005768394")
     ang = two_pi * (k.astype(ld) / n)
-    assert float(np.max(np.abs(sn.astype(ld) - np.sin(ang)))) <= 2.0**-52
-    assert float(np.max(np.abs(cs.astype(ld) - np.cos(ang)))) <= 2.0**-52
+    assert float(np.max(np.abs(out["sin2pi"].astype(ld) - np.sin(ang)))) <= 2.0**-52
+    assert float(np.max(np.abs(out["cos2pi"].astype(ld) - np.cos(ang)))) <= 2.0**-52
+    u = k.astype(np.float64) * 2.0**-53  # exact: k < 2^53
+    assert np.array_equal(out["u"], u)
+    assert np.array_equal(out["mu"], 2.0 * u - 1.0)
+    nz = out["mu"] != 0.0
+    assert np.all(np.isinf(out["recip_mu"][~nz]))
+    assert float(ulps(out["recip_mu"][nz], 1 / out["mu"][nz].astype(ld)).max()) <= 1.0
 
 
 # -------------------------------------------------------------- traces
