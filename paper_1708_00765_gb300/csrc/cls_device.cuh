@@ -35,6 +35,7 @@ struct __align__(16) LogEntry {
 };
 __shared__ LogEntry cls_log_tab[CLS_LOG_TABLE_N];
 __shared__ double2 cls_sincos_tab[CLS_SINCOS_TABLE_N];
+__shared__ double2 cls_eln2_tab[54];  // {E ln2_hi (exact), E ln2_lo} for E = 0, -1, ..., -53
 
 template <typename P>
 __device__ __forceinline__ void load_math_tables(int tid, int nthreads) {
@@ -43,6 +44,7 @@ __device__ __forceinline__ void load_math_tables(int tid, int nthreads) {
             cls_log_tab[i] = LogEntry{cls_log_table_init[i][0], cls_log_table_init[i][1], cls_log_table_init[i][2], 0.0};
         for (int i = tid; i < CLS_SINCOS_TABLE_N; i += nthreads)
             cls_sincos_tab[i] = make_double2(cls_sincos_table_init[i][0], cls_sincos_table_init[i][1]);
+        for (int i = tid; i < 54; i += nthreads) cls_eln2_tab[i] = make_double2(-i * CLS_LN2_HI, -i * CLS_LN2_LO);
     }
 }
 
@@ -63,19 +65,19 @@ __device__ __forceinline__ double log_one_minus(unsigned long long k) {
     const int s = __clzll((long long)n) - 11;                     // n << s: leading bit at bit 52
     const unsigned long long mb = (n << s) + (1022ull << 52);     // bits of m in [1, 2)
     const int idx = (k >> 44) == 0ull ? 256 : (int)((mb >> 44) & 255ull);
-    const int E = (idx >= 128 ? 1 : 0) - 1 - s;                   // e = -1 - s, plus the folded ln 2
+    const int E = (idx >= 128 ? 1 : 0) - 1 - s;                   // e = -1 - s, plus the folded ln 2; -53 <= E <= 0
     const double m = __longlong_as_double((long long)mb);
     const double2 Ft = *reinterpret_cast<const double2 *>(&cls_log_tab[idx].F);
     const double t_lo = cls_log_tab[idx].t_lo;
+    const double2 eln2 = cls_eln2_tab[-E];
     const double r = fma(m, Ft.x, -1.0);
-    const double Ed = small_int_to_double(E);
     const double r2 = r * r;
     double q = fma(r, -1.0 / 6.0, 1.0 / 5.0);  // q = -1/2 + r/3 - r^2/4 + r^3/5 - r^4/6
     q = fma(q, r, -0.25);
     q = fma(q, r, 1.0 / 3.0);
     q = fma(q, r, -0.5);
-    const double head = fma(Ed, CLS_LN2_HI, Ft.y);  // exact
-    const double tail = fma(Ed, CLS_LN2_LO, t_lo);
+    const double head = eln2.x + Ft.y;  // exact: both are multiples of 2^-47 below 2^6
+    const double tail = eln2.y + t_lo;
     const double res = head + (r + fma(r2, q, tail));
     return k == 0ull ? 0.0 : res;
 }
@@ -179,8 +181,18 @@ struct Real<double> {
         const unsigned long long v = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh;
         return (int)min(v, (unsigned long long)cap);
     }
-    static __device__ __forceinline__ double of_int(int k) { return small_int_to_double(k); }
-    // l_c = -ln(1 - u) / Sigma_m, as -ln(1 - u) * (1 / Sigma_m), from the draw's words
+    // t - k for finite t >= 0 and k = floor_index(t, cap) <= floor(t): the bits
+    // below the binary point, plus floor(t) - k (non-zero beyond the last
+    // bin), re-assembled in the integer pipes
+    static __device__ __forceinline__ double frac(double t, int k) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+        const int e = (int)(b >> 52) - 1023;
+        if (e > 30) return t - small_int_to_double(k);
+        const int sh = 52 - max(e, 0);
+        const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const unsigned long long m = (((M >> sh) - (unsigned long long)k) << sh) + (M & ((1ull << sh) - 1ull));
+        return e < 0 ? t : scaled_int((long long)m, -sh);
+    }    // l_c = -ln(1 - u) / Sigma_m, as -ln(1 - u) * (1 / Sigma_m), from the draw's words
     static __device__ __forceinline__ double collision(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
         return -log_one_minus(k53(hi, lo)) * c.inv_sigma[m];
     }
@@ -246,7 +258,7 @@ struct Real<float> {
     static __device__ __forceinline__ float inv_dx(const CaseParams &c) { return c.inv_dx_f; }
     static __device__ __forceinline__ bool is_zero(float x) { return x == 0.0f; }
     static __device__ __forceinline__ int floor_index(float t, int cap) { return min((int)t, cap); }
-    static __device__ __forceinline__ float of_int(int k) { return (float)k; }
+    static __device__ __forceinline__ float frac(float t, int k) { return t - (float)k; }
     static __device__ __forceinline__ float collision(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
         return -__logf(one_minus(hi, lo)) * c.inv_sigma_f[m];
     }
@@ -475,8 +487,9 @@ template <typename P>
 __device__ __forceinline__ void plan_flight(Flight<P> &f, History<P> &s, const CaseParams &cp, P x0, P x1, P l,
                                             int m) {
     using R = Real<P>;
-    if (m == 0) s.track0 += l;
-    else s.track1 += l;
+    const P t = (m == 0 ? s.track0 : s.track1) + l;  // one add, the sum selected
+    s.track0 = (m == 0) ? t : s.track0;
+    s.track1 = (m == 0) ? s.track1 : t;
     f.k0 = 0;
     f.k1 = -1;
     if (!R::pos(l)) return;
@@ -495,19 +508,21 @@ __device__ __forceinline__ void plan_flight(Flight<P> &f, History<P> &s, const C
     const P lo = R::lt(a, b) ? a : b;
     P hi = R::lt(a, b) ? b : a;
     hi = R::lt(L, hi) ? L : hi;
-    const int k0 = R::floor_index(lo * inv_dx, nb - 1);
-    const int k1 = R::floor_index(hi * inv_dx, nb - 1);
+    // bin coordinates x / dx: bin index = integer part; the end bins receive
+    // (1 - frac) dx / |wx| and frac dx / |wx|
+    const P ulo = lo * inv_dx, uhi = hi * inv_dx;
+    const int k0 = R::floor_index(ulo, nb - 1);
+    const int k1 = R::floor_index(uhi, nb - 1);
     f.k0 = k0;
     f.k1 = k1;
     if (k0 == k1) {  // the flight lies inside one bin: its length itself
         f.a0 = l;
         return;
     }
-    const P iaw = fabs(s.iw[0]);
-    const P dx = R::dx(cp);
-    f.a0 = R::nonneg(R::of_int(k0 + 1) * dx - lo) * iaw;
-    f.a1 = R::nonneg(hi - R::of_int(k1) * dx) * iaw;
-    f.c = dx * iaw;
+    const P c = R::dx(cp) * fabs(s.iw[0]);
+    f.a0 = R::nonneg(fma(-R::frac(ulo, k0), c, c));
+    f.a1 = R::frac(uhi, k1) * c;
+    f.c = c;
 }
 
 // Distance along the flight to the face ahead on one axis: (L - r)/omega
@@ -653,8 +668,8 @@ __device__ __forceinline__ void finish_history(unsigned char *region, int nbs, c
     const double t = t0 + t1;
     atomicAdd(&st[S_T], t);
     atomicAdd(&st[S_T2], t * t);
-    if (t0 != 0.0) atomicAdd(&st[S_TRACK0], t0);
-    if (t1 != 0.0) atomicAdd(&st[S_TRACK1], t1);
+    if (__double_as_longlong(t0) != 0) atomicAdd(&st[S_TRACK0], t0);
+    if (__double_as_longlong(t1) != 0) atomicAdd(&st[S_TRACK1], t1);
     const int c = (outcome == EV_LEAK_X0) ? C_R : (outcome == EV_LEAK_XL) ? C_T : (outcome == EV_ABSORB) ? C_A : C_CAPPED;
     atomicAdd(&ct[c], 1ull);
     if (s.n_coll) atomicAdd(&ct[C_COLL], (unsigned long long)s.n_coll);
@@ -734,8 +749,8 @@ __device__ __forceinline__ void finish_history_global(const LaunchArgs &a, int c
     const double t = t0 + t1;
     atomicAdd(&st[S_T], t);
     atomicAdd(&st[S_T2], t * t);
-    if (t0 != 0.0) atomicAdd(&st[S_TRACK0], t0);
-    if (t1 != 0.0) atomicAdd(&st[S_TRACK1], t1);
+    if (__double_as_longlong(t0) != 0) atomicAdd(&st[S_TRACK0], t0);
+    if (__double_as_longlong(t1) != 0) atomicAdd(&st[S_TRACK1], t1);
     const int c = (outcome == EV_LEAK_X0) ? C_R : (outcome == EV_LEAK_XL) ? C_T : (outcome == EV_ABSORB) ? C_A : C_CAPPED;
     atomicAdd(&ct[c], 1ull);
     if (with_event_counts) {

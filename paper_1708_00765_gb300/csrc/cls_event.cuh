@@ -151,8 +151,8 @@ __device__ __forceinline__ void finish_event_history(unsigned char *region, int 
     const double t = t0 + t1;
     atomicAdd(&st[S_T], t);
     atomicAdd(&st[S_T2], t * t);
-    if (t0 != 0.0) atomicAdd(&st[S_TRACK0], t0);
-    if (t1 != 0.0) atomicAdd(&st[S_TRACK1], t1);
+    if (__double_as_longlong(t0) != 0) atomicAdd(&st[S_TRACK0], t0);
+    if (__double_as_longlong(t1) != 0) atomicAdd(&st[S_TRACK1], t1);
     const int c = (outcome == EV_LEAK_X0) ? C_R : (outcome == EV_LEAK_XL) ? C_T : (outcome == EV_ABSORB) ? C_A : C_CAPPED;
     atomicAdd(&ct[c], 1ull);
     atomicMax(&ct[C_MAXEV], (unsigned long long)s.events);
