@@ -61,7 +61,7 @@ __global__ void math_kernel(const uint64_t *k, int n, double *out) {
     const uint32_t hi = (uint32_t)(k[i] >> 21), lo = (uint32_t)(k[i] << 11);  // words whose top 53 bits are k
     const double mu = cls::Real<double>::two_u_minus_one(hi, lo);
     double *o = out + 6 * (size_t)i;
-    o[0] = cls::log_one_minus(k[i]);
+    o[0] = -cls::exp_variate_shared(k[i]);
     o[1] = sn;
     o[2] = cs;
     o[3] = cls::Real<double>::uniform(hi, lo);

@@ -19,67 +19,43 @@
 #include <cuda_runtime.h>
 
 #include "cls_internal.h"
-#include "cls_math_tables.h"
+#include "cls_intlog.h"
 
 namespace cls {
 
 #define CLS_FULL_MASK 0xffffffffu
 
 // ------------------------------------------------- FP64 logarithm, sine/cosine
-// The FP64 walk takes its logarithms and its sine/cosine pairs straight from
-// the 53-bit integer k of a draw (u = k 2^-53), through tables that every FP64
-// kernel copies into shared memory when it starts (load_math_tables).  Both
-// keep the FP64 pipe, the walk's bottleneck, to about a dozen operations each.
-struct __align__(16) LogEntry {
-    double F, t_hi, t_lo, pad;
-};
-__shared__ LogEntry cls_log_tab[CLS_LOG_TABLE_N];
+// The FP64 walk takes its logarithms (cls_intlog.h, integer arithmetic) and its
+// sine/cosine pairs straight from the 53-bit integer k of a draw
+// (u = k 2^-53), through tables that every FP64 kernel copies into shared
+// memory when it starts (load_math_tables).  Both keep work off the FP64 pipe,
+// the walk's bottleneck.
+__shared__ uint16_t cls_logn_tab[CLS_LOG_TABLE_N];
+__shared__ __align__(16) uint64_t cls_logt_tab[CLS_LOG_TABLE_N][2];
 __shared__ double2 cls_sincos_tab[CLS_SINCOS_TABLE_N];
-__shared__ double2 cls_eln2_tab[54];  // {E ln2_hi (exact), E ln2_lo} for E = 0, -1, ..., -53
 
 template <typename P>
 __device__ __forceinline__ void load_math_tables(int tid, int nthreads) {
     if constexpr (sizeof(P) == 8) {
-        for (int i = tid; i < CLS_LOG_TABLE_N; i += nthreads)
-            cls_log_tab[i] = LogEntry{cls_log_table_init[i][0], cls_log_table_init[i][1], cls_log_table_init[i][2], 0.0};
+        for (int i = tid; i < CLS_LOG_TABLE_N; i += nthreads) {
+            cls_logn_tab[i] = cls_log_n_init[i];
+            cls_logt_tab[i][0] = cls_log_t_init[i][0];
+            cls_logt_tab[i][1] = cls_log_t_init[i][1];
+        }
         for (int i = tid; i < CLS_SINCOS_TABLE_N; i += nthreads)
             cls_sincos_tab[i] = make_double2(cls_sincos_table_init[i][0], cls_sincos_table_init[i][1]);
-        for (int i = tid; i < 54; i += nthreads) cls_eln2_tab[i] = make_double2(-i * CLS_LN2_HI, -i * CLS_LN2_LO);
     }
+}
+
+// -ln(1 - u) for u = k 2^-53, from the shared-memory tables
+__device__ __forceinline__ double exp_variate_shared(unsigned long long k) {
+    return exp_variate(k, IntLogTables{cls_logn_tab, cls_logt_tab});
 }
 
 // the integer E as a double, exactly (|E| < 2^51), by the 1.5 2^52 shift
 __device__ __forceinline__ double small_int_to_double(long long e) {
     return __longlong_as_double(0x4338000000000000ll + e) - 0x1.8p52;
-}
-
-// ln(1 - u) for u = k 2^-53, 0 <= k < 2^53: the table-driven method of
-// Tang (ACM TOMS 16, 1990).  1 - u = n 2^-53 = m 2^e with m in [1, 2); the
-// top 8 fraction bits i of m select F_i ~ 1/c_i, so that r = m F_i - 1 has
-// |r| <= 2^-9 and ln(1 - u) = E ln 2 + T_i + ln(1 + r), with ln(1 + r) from
-// its Taylor series to r^6 (truncation below 2^-56 relative).  Arguments with
-// u < 2^-9 use r = -u exactly (table entry 256), and u = 0 gives 0.  The head
-// E ln2_hi + T_hi is exact; the result is within about one ulp.
-__device__ __forceinline__ double log_one_minus(unsigned long long k) {
-    const unsigned long long n = (1ull << 53) - k - (k == 0ull ? 1ull : 0ull);
-    const int s = __clzll((long long)n) - 11;                     // n << s: leading bit at bit 52
-    const unsigned long long mb = (n << s) + (1022ull << 52);     // bits of m in [1, 2)
-    const int idx = (k >> 44) == 0ull ? 256 : (int)((mb >> 44) & 255ull);
-    const int E = (idx >= 128 ? 1 : 0) - 1 - s;                   // e = -1 - s, plus the folded ln 2; -53 <= E <= 0
-    const double m = __longlong_as_double((long long)mb);
-    const double2 Ft = *reinterpret_cast<const double2 *>(&cls_log_tab[idx].F);
-    const double t_lo = cls_log_tab[idx].t_lo;
-    const double2 eln2 = cls_eln2_tab[-E];
-    const double r = fma(m, Ft.x, -1.0);
-    const double r2 = r * r;
-    double q = fma(r, -1.0 / 6.0, 1.0 / 5.0);  // q = -1/2 + r/3 - r^2/4 + r^3/5 - r^4/6
-    q = fma(q, r, -0.25);
-    q = fma(q, r, 1.0 / 3.0);
-    q = fma(q, r, -0.5);
-    const double head = eln2.x + Ft.y;  // exact: both are multiples of 2^-47 below 2^6
-    const double tail = eln2.y + t_lo;
-    const double res = head + (r + fma(r2, q, tail));
-    return k == 0ull ? 0.0 : res;
 }
 
 // (sin, cos) of 2 pi u for u = k 2^-53: angle addition from the nearest
@@ -194,10 +170,10 @@ struct Real<double> {
         return e < 0 ? t : scaled_int((long long)m, -sh);
     }    // l_c = -ln(1 - u) / Sigma_m, as -ln(1 - u) * (1 / Sigma_m), from the draw's words
     static __device__ __forceinline__ double collision(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
-        return -log_one_minus(k53(hi, lo)) * c.inv_sigma[m];
+        return exp_variate_shared(k53(hi, lo)) * c.inv_sigma[m];
     }
     static __device__ __forceinline__ double interface(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
-        return -c.lambda[m] * log_one_minus(k53(hi, lo));
+        return c.lambda[m] * exp_variate_shared(k53(hi, lo));
     }
     // 1/a by Newton-Raphson iteration for the reciprocal, r <- r + r (1 - a r)
     // (each step squares the relative error; P. Markstein, IBM J. Res. Dev. 34,

@@ -1,0 +1,156 @@
+// cls_intlog.h -- the exponential variate -ln(1 - u) of the FP64 walk, in
+// 64/128-bit integer arithmetic.
+//
+// The walk draws two distances per event, l_c = -ln(1 - u)/Sigma_m and
+// l_i = -Lambda_m ln(1 - u) (paper Sec. 4).  On GB300 the FP64 pipe is the
+// walk's bottleneck while the integer pipes idle, so the logarithm is
+// evaluated in fixed point: the table-driven reduction of Tang (ACM TOMS 16,
+// 1990) with an exact 64-bit product for the reduced argument, the Taylor
+// series of ln(1 + r) by Horner's rule in Q31/Q63 fixed point (precision
+// tapered to what each term needs), the sum in 128-bit fixed point with 120
+// fraction bits, and one rounding to the nearest double at the end.  The
+// result is within one ulp of -ln(1 - u).
+//
+// Host and device compile the same code (the host build serves tests).
+#pragma once
+
+#include <stdint.h>
+#include <string.h>
+
+#include "cls_math_tables.h"
+
+#ifdef __CUDACC__
+#define CLS_HD __host__ __device__ __forceinline__
+#else
+#define CLS_HD static inline
+#endif
+
+namespace cls {
+
+struct U128 {
+    uint64_t lo, hi;
+};
+
+CLS_HD uint64_t umulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+CLS_HD int64_t smulhi64(int64_t a, int64_t b) {
+#ifdef __CUDA_ARCH__
+    return __mul64hi(a, b);
+#else
+    return (int64_t)(((__int128)a * b) >> 64);
+#endif
+}
+
+CLS_HD int clz64(uint64_t x) {  // x != 0
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)x);
+#else
+    return __builtin_clzll(x);
+#endif
+}
+
+CLS_HD double bits_to_double(uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double d;
+    memcpy(&d, &b, sizeof d);
+    return d;
+#endif
+}
+
+// floor(a b / 2^63) for signed Q63 operands
+CLS_HD int64_t mulq63(int64_t a, int64_t b) {
+    return (int64_t)(((uint64_t)smulhi64(a, b) << 1) | (((uint64_t)a * (uint64_t)b) >> 63));
+}
+
+// floor(a b / 2^63), unsigned
+CLS_HD uint64_t umulq63(uint64_t a, uint64_t b) {
+    return (umulhi64(a, b) << 1) | ((a * b) >> 63);
+}
+
+// m 2^-scale rounded to the nearest double (ties to even), for m != 0
+CLS_HD double u128_to_double(U128 m, int scale) {
+    const bool big = m.hi != 0;
+    const int lz = big ? clz64(m.hi) : 64 + clz64(m.lo);
+    // shift the leading one to bit 127
+    const int sh = lz & 63;
+    uint64_t hi = big ? m.hi : m.lo;
+    uint64_t lo = big ? m.lo : 0ull;
+    if (sh) {
+        hi = (hi << sh) | (lo >> (64 - sh));
+        lo <<= sh;
+    }
+    uint64_t mant = hi >> 11;  // 53 bits, leading one at bit 52
+    const uint64_t round = (hi >> 10) & 1ull;
+    const uint64_t sticky = (hi & 0x3FFull) | lo;
+    mant += round & ((sticky != 0ull ? 1ull : 0ull) | (mant & 1ull));
+    // value in [2^(127 - lz - scale), 2^(128 - lz - scale)); a carry out of
+    // the rounding moves into the exponent field
+    const uint64_t ex = (uint64_t)(127 - lz - scale + 1023 - 1);
+    return bits_to_double((ex << 52) + mant);
+}
+
+// Tables in the memory the caller reads them from (shared memory on the GPU).
+struct IntLogTables {
+    const uint16_t *n;      // N_i
+    const uint64_t (*t)[2]; // T_i 2^120, {low, high}
+};
+
+// -ln(1 - u) >= 0 for u = k 2^-53, 0 <= k < 2^53.
+CLS_HD double exp_variate(uint64_t k, IntLogTables tab) {
+    if (k == 0ull) return 0.0;
+    if (k < (1ull << 44)) {
+        // u < 2^-9: -ln(1 - u) = u (1 + v), v = u G(u),
+        // G = 1/2 + u/3 + u^2/4 + u^3/5 + u^4/6 + u^5/7 (next term below 2^-66)
+        const uint64_t U = k << 10;  // u 2^63, exact
+        const uint32_t u31 = (uint32_t)(U >> 32);
+        const uint32_t g4 = 0x15555555u + (uint32_t)(((uint64_t)u31 * 0x12492492u) >> 31);  // 1/6 + u/7
+        const uint32_t g3 = 0x1999999Au + (uint32_t)(((uint64_t)u31 * g4) >> 31);          // 1/5 + u g4
+        const uint64_t g2 = (1ull << 61) + umulq63(U, (uint64_t)g3 << 32);                 // 1/4 + u g3
+        const uint64_t g1 = 0x2AAAAAAAAAAAAAABull + umulq63(U, g2);                        // 1/3 + u g2
+        const uint64_t g = (1ull << 62) + umulq63(U, g1);                                  // 1/2 + u g1
+        const uint64_t W = (1ull << 63) + umulq63(U, g);                                   // (1 + v) 2^63
+        const U128 m = {k * W, umulhi64(k, W)};                                            // u (1 + v) 2^116
+        return u128_to_double(m, 116);
+    }
+    // 1 - u = n 2^-53 = (1 + f) 2^(p - 53); N_i from the top 8 bits of f
+    const uint64_t n = (1ull << 53) - k;
+    const int lz = clz64(n);                  // 11 .. 63
+    const uint64_t nn = n << (lz - 11);       // (1 + f) 2^52
+    const int i = (int)(nn >> 44) & 255;
+    const int E = lz - 10;                    // 53 - p >= 1
+    // r = (1 + f) N_i / 2048 - 1, exactly, in Q63; |r| < 2^-8.6
+    const int64_t R = (int64_t)(nn * (uint64_t)tab.n[i] - (1ull << 63));
+    // ln(1 + r) = r + r^2 P(r), P = -1/2 + r/3 - r^2/4 + r^3/5 - r^4/6 + r^5/7
+    // (next term below 2^-69); Q31 where 2^-31 suffices, else Q63
+    const int32_t r31 = (int32_t)(R >> 32);
+    const int32_t p6 = -0x15555555 + (int32_t)(((int64_t)r31 * 0x12492492) >> 31);  // -1/6 + r/7
+    const int32_t p5 = 0x1999999A + (int32_t)(((int64_t)r31 * p6) >> 31);           // 1/5 + r p6
+    const int64_t p4 = -(1ll << 61) + mulq63(R, (int64_t)((uint64_t)(int64_t)p5 << 32));                 // -1/4 + r p5
+    const int64_t p3 = 0x2AAAAAAAAAAAAAABll + mulq63(R, p4);                        // 1/3 + r p4
+    const int64_t p2 = -(1ll << 62) + mulq63(R, p3);                                // -1/2 + r p3
+    const int64_t rq = R + mulq63(mulq63(R, R), p2);                                // ln(1 + r) 2^63
+    // ln(1 - u) 2^120 = T_i - E ln2 + rq 2^57, two's complement (negative)
+    const uint64_t t_lo = tab.t[i][0], t_hi = tab.t[i][1];
+    const uint64_t e_lo = CLS_LN2_Q120_LO * (uint64_t)E;
+    const uint64_t e_hi = CLS_LN2_Q120_HI * (uint64_t)E + umulhi64(CLS_LN2_Q120_LO, (uint64_t)E);
+    uint64_t s_lo = t_lo - e_lo;
+    uint64_t s_hi = t_hi - e_hi - (t_lo < e_lo ? 1ull : 0ull);
+    const uint64_t a_lo = (uint64_t)rq << 57;
+    const uint64_t a_hi = (uint64_t)(rq >> 7);
+    const uint64_t x_lo = s_lo + a_lo;
+    s_hi += a_hi + (x_lo < s_lo ? 1ull : 0ull);
+    s_lo = x_lo;
+    // magnitude -s
+    const U128 m = {0ull - s_lo, ~s_hi + (s_lo == 0ull ? 1ull : 0ull)};
+    return u128_to_double(m, 120);
+}
+
+}  // namespace cls

@@ -2,19 +2,16 @@
 
 Run from this directory (`python gen_math_tables.py`); the output is committed.
 Every value is computed here in exact or 60-digit decimal arithmetic (Python's
-standard `decimal` module) and rounded once to the nearest double.
+standard `decimal` module) and rounded once, to the nearest double or to the
+nearest multiple of 2^-120.
 
 Logarithm (table-driven, after P. T. P. Tang, "Table-driven implementation of
-the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16, 1990):
-for a double m in [1, 2) whose top 8 fraction bits are i, take
-c_i = 1 + (i + 1/2)/256, F_i = the double nearest 1/c_i, and
-r = m F_i - 1 (|r| <= 2^-9), so ln m = -ln F_i + ln(1 + r).  Entries with
-m >= 3/2 fold one ln 2 into the table: T_i = -ln(2 F_i), and the caller adds
-one to the binary exponent, so arguments just below 1 meet no cancellation
-against a large multiple of ln 2.  T_i is split into a head rounded to a
-multiple of 2^-47 and a tail (double); ln 2 likewise, so E ln2_hi + T_hi is
-exact for |E| < 64.  Entry 256 (F = 1/2, T = 0, exponent + 1) serves the
-arguments 1 - u with u < 2^-9, for which r = -u exactly.
+the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16, 1990),
+for the walk's integer evaluation of -ln(1 - u): for m in [1, 2) whose top 8
+fraction bits are i, N_i = round(2048 / c_i), c_i = 1 + (i + 1/2)/256, so that
+r = m N_i / 2048 - 1 is an exact 64-bit product with |r| < 2^-8.6, and
+ln m = T_i + ln(1 + r), T_i = -ln(N_i / 2048), tabulated as a 128-bit
+fixed-point number with 120 fraction bits (as is ln 2).
 
 Sine/cosine of 2 pi j / 256, j = 0..255, each rounded to the nearest double
 (exact zeros and ones at the quadrant points).
@@ -36,13 +33,6 @@ def dec(fr: Fraction) -> Decimal:
 def to_double(x: Decimal) -> float:
     # Python's float() of a decimal string is correctly rounded
     return float(x)
-
-
-def quantize(x: Decimal, bits: int) -> Fraction:
-    """x rounded to the nearest multiple of 2^-bits, exactly."""
-    scale = Decimal(2) ** bits
-    n = int((x * scale).to_integral_value())
-    return Fraction(n, 2 ** bits)
 
 
 def ln(x: Decimal) -> Decimal:
@@ -88,26 +78,18 @@ def hexd(v: float) -> str:
     return v.hex() if v != 0.0 else "0x0p+0"
 
 
-def log_table() -> tuple[list[tuple[float, float, float]], float, float]:
-    ln2 = ln(Decimal(2))
-    ln2_hi = quantize(ln2, 47)
-    ln2_lo = to_double(ln2 - dec(ln2_hi))
+def log_table() -> tuple[list[tuple[int, int]], int]:
+    """[(N_i, T_i 2^120 rounded)], ln 2 2^120 rounded."""
+    scale = Decimal(2) ** 120
+    ln2 = int((ln(Decimal(2)) * scale).to_integral_value())
     rows = []
-    for i in range(257):
-        if i < 256:
-            c = Fraction(1) + Fraction(2 * i + 1, 512)
-            F = float(Fraction(1) / c)  # nearest double to 1/c
-            fold = i >= 128
-            T = -ln(dec(Fraction(F) * (2 if fold else 1)))
-        else:
-            F = 0.5
-            T = Decimal(0)
-        T_hi = quantize(T, 47)
-        T_lo = to_double(T - dec(T_hi))
-        rows.append((F, float(T_hi), T_lo))
-        assert Fraction(float(T_hi)) == T_hi
-    assert Fraction(float(ln2_hi)) == ln2_hi
-    return rows, float(ln2_hi), ln2_lo
+    for i in range(256):
+        c = Fraction(1) + Fraction(2 * i + 1, 512)
+        N = round(Fraction(2048) / c)
+        assert 1024 < N <= 2048
+        T = -ln(dec(Fraction(N, 2048)))
+        rows.append((N, int((T * scale).to_integral_value())))
+    return rows, ln2
 
 
 def sincos_table() -> list[tuple[float, float]]:
@@ -124,29 +106,41 @@ def sincos_table() -> list[tuple[float, float]]:
 
 
 def main() -> None:
-    logs, ln2_hi, ln2_lo = log_table()
+    logs, ln2 = log_table()
     sc = sincos_table()
+    M64 = (1 << 64) - 1
     out = [
         "// Generated by gen_math_tables.py; do not edit.",
         "#pragma once",
         "",
+        "#include <stdint.h>",
+        "",
+        "#ifndef CLS_TABLE_SPACE",
+        "#define CLS_TABLE_SPACE __device__",
+        "#endif",
+        "",
         "namespace cls {",
         "",
-        "// ln 2 = LN2_HI + LN2_LO, LN2_HI a multiple of 2^-47",
-        f"#define CLS_LN2_HI {hexd(ln2_hi)}",
-        f"#define CLS_LN2_LO {hexd(ln2_lo)}",
-        "#define CLS_LOG_TABLE_N 257",
+        "// ln 2 2^120, rounded: high and low 64-bit words",
+        f"#define CLS_LN2_Q120_HI 0x{ln2 >> 64:016x}ull",
+        f"#define CLS_LN2_Q120_LO 0x{ln2 & M64:016x}ull",
+        "#define CLS_LOG_TABLE_N 256",
         "#define CLS_SINCOS_TABLE_N 256",
         "",
-        "// {F_i, T_hi, T_lo}: r = m F_i - 1, ln m = T_hi + T_lo + ln(1 + r) (+ ln 2 for i >= 128)",
-        "__device__ const double cls_log_table_init[CLS_LOG_TABLE_N][3] = {",
+        "// N_i = round(2048 / c_i), c_i = 1 + (i + 1/2)/256",
+        "CLS_TABLE_SPACE const uint16_t cls_log_n_init[CLS_LOG_TABLE_N] = {",
     ]
-    for F, th, tl in logs:
-        out.append(f"    {{{hexd(F)}, {hexd(th)}, {hexd(tl)}}},")
+    for j in range(0, 256, 16):
+        out.append("    " + ", ".join(str(N) for N, _ in logs[j:j + 16]) + ",")
+    out += ["};", "",
+            "// T_i = -ln(N_i / 2048) 2^120, rounded: {low, high} 64-bit words",
+            "CLS_TABLE_SPACE const uint64_t cls_log_t_init[CLS_LOG_TABLE_N][2] = {"]
+    for _, T in logs:
+        out.append(f"    {{0x{T & M64:016x}ull, 0x{T >> 64:016x}ull}},")
     out += ["};", "", "// {sin, cos} of 2 pi j / 256",
-            "__device__ const double cls_sincos_table_init[CLS_SINCOS_TABLE_N][2] = {"]
-    for s, c in sc:
-        out.append(f"    {{{hexd(s)}, {hexd(c)}}},")
+            "CLS_TABLE_SPACE const double cls_sincos_table_init[CLS_SINCOS_TABLE_N][2] = {"]
+    for s_, c_ in sc:
+        out.append(f"    {{{hexd(s_)}, {hexd(c_)}}},")
     out += ["};", "", "}  // namespace cls", ""]
     with open(os.path.join(HERE, "cls_math_tables.h"), "w") as fh:
         fh.write("\n".join(out))
