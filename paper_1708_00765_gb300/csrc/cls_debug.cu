@@ -57,7 +57,7 @@ __global__ void math_kernel(const uint64_t *k, int n, double *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double sn, cs;
-    cls::sincos_2pi_k(k[i], &sn, &cs);
+    cls::sincos_2pi_shared(k[i], &sn, &cs);
     const uint32_t hi = (uint32_t)(k[i] >> 21), lo = (uint32_t)(k[i] << 11);  // words whose top 53 bits are k
     const double mu = cls::Real<double>::two_u_minus_one(hi, lo);
     double *o = out + 6 * (size_t)i;

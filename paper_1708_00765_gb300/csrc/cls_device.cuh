@@ -19,21 +19,21 @@
 #include <cuda_runtime.h>
 
 #include "cls_internal.h"
-#include "cls_intlog.h"
+#include "cls_intmath.h"
 
 namespace cls {
 
 #define CLS_FULL_MASK 0xffffffffu
 
 // ------------------------------------------------- FP64 logarithm, sine/cosine
-// The FP64 walk takes its logarithms (cls_intlog.h, integer arithmetic) and its
-// sine/cosine pairs straight from the 53-bit integer k of a draw
-// (u = k 2^-53), through tables that every FP64 kernel copies into shared
-// memory when it starts (load_math_tables).  Both keep work off the FP64 pipe,
-// the walk's bottleneck.
+// The FP64 walk takes its logarithms and its sine/cosine pairs straight from
+// the 53-bit integer k of a draw (u = k 2^-53), in integer arithmetic
+// (cls_intmath.h), through tables that every FP64 kernel copies into shared
+// memory when it starts (load_math_tables): the FP64 pipe, the walk's
+// bottleneck, sees neither.
 __shared__ uint16_t cls_logn_tab[CLS_LOG_TABLE_N];
 __shared__ __align__(16) uint64_t cls_logt_tab[CLS_LOG_TABLE_N][2];
-__shared__ double2 cls_sincos_tab[CLS_SINCOS_TABLE_N];
+__shared__ __align__(16) int64_t cls_sincos_tab[CLS_SINCOS_TABLE_N][2];
 
 template <typename P>
 __device__ __forceinline__ void load_math_tables(int tid, int nthreads) {
@@ -43,8 +43,10 @@ __device__ __forceinline__ void load_math_tables(int tid, int nthreads) {
             cls_logt_tab[i][0] = cls_log_t_init[i][0];
             cls_logt_tab[i][1] = cls_log_t_init[i][1];
         }
-        for (int i = tid; i < CLS_SINCOS_TABLE_N; i += nthreads)
-            cls_sincos_tab[i] = make_double2(cls_sincos_table_init[i][0], cls_sincos_table_init[i][1]);
+        for (int i = tid; i < CLS_SINCOS_TABLE_N; i += nthreads) {
+            cls_sincos_tab[i][0] = cls_sincos_q62_init[i][0];
+            cls_sincos_tab[i][1] = cls_sincos_q62_init[i][1];
+        }
     }
 }
 
@@ -53,24 +55,14 @@ __device__ __forceinline__ double exp_variate_shared(unsigned long long k) {
     return exp_variate(k, IntLogTables{cls_logn_tab, cls_logt_tab});
 }
 
+// (sin, cos) of 2 pi u for u = k 2^-53, from the shared-memory table
+__device__ __forceinline__ void sincos_2pi_shared(unsigned long long k, double *sn, double *cs) {
+    sincos_2pi_int(k, cls_sincos_tab, sn, cs);
+}
+
 // the integer E as a double, exactly (|E| < 2^51), by the 1.5 2^52 shift
 __device__ __forceinline__ double small_int_to_double(long long e) {
     return __longlong_as_double(0x4338000000000000ll + e) - 0x1.8p52;
-}
-
-// (sin, cos) of 2 pi u for u = k 2^-53: angle addition from the nearest
-// tabulated angle 2 pi j/256, |delta| <= pi/256, with the Taylor series of
-// sin delta to delta^7 and of cos delta - 1 to delta^6.
-__device__ __forceinline__ void sincos_2pi_k(unsigned long long k, double *sn, double *cs) {
-    const unsigned long long j = (k + (1ull << 44)) >> 45;       // nearest multiple of 2^45, 0..256
-    const long long t = (long long)k - (long long)(j << 45);     // in [-2^44, 2^44)
-    const double2 sc = cls_sincos_tab[j & 255ull];
-    const double d = small_int_to_double(t) * 0x1.921fb54442d18p-51;  // 2 pi t 2^-53
-    const double d2 = d * d;
-    const double cm1 = d2 * fma(d2, fma(d2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
-    const double sd = fma(d * d2, fma(d2, fma(d2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), d);
-    *sn = fma(sc.y, sd, fma(sc.x, cm1, sc.x));  // S cos(delta) + C sin(delta)
-    *cs = fma(-sc.x, sd, fma(sc.y, cm1, sc.y)); // C cos(delta) - S sin(delta)
 }
 
 // ------------------------------------------------------------------ Philox
@@ -149,6 +141,13 @@ struct Real<double> {
     static __device__ __forceinline__ double dx(const CaseParams &c) { return c.dx; }
     static __device__ __forceinline__ double inv_dx(const CaseParams &c) { return c.inv_dx; }
     static __device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+    // |x| and -x on the bit pattern (integer pipes)
+    static __device__ __forceinline__ double abs(double x) {
+        return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll);
+    }
+    static __device__ __forceinline__ double flip(double x) {
+        return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+    }
     // min(floor(t), cap) for finite t >= 0, from the bit pattern
     static __device__ __forceinline__ int floor_index(double t, int cap) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(t);
@@ -200,7 +199,7 @@ struct Real<double> {
     }
     // (sin, cos) of 2 pi u from the draw's words
     static __device__ __forceinline__ void sincos_2pi(uint32_t hi, uint32_t lo, double *s, double *co) {
-        sincos_2pi_k(k53(hi, lo), s, co);
+        sincos_2pi_shared(k53(hi, lo), s, co);
     }
 };
 
@@ -233,6 +232,8 @@ struct Real<float> {
     static __device__ __forceinline__ float dx(const CaseParams &c) { return c.dx_f; }
     static __device__ __forceinline__ float inv_dx(const CaseParams &c) { return c.inv_dx_f; }
     static __device__ __forceinline__ bool is_zero(float x) { return x == 0.0f; }
+    static __device__ __forceinline__ float abs(float x) { return fabsf(x); }
+    static __device__ __forceinline__ float flip(float x) { return -x; }
     static __device__ __forceinline__ int floor_index(float t, int cap) { return min((int)t, cap); }
     static __device__ __forceinline__ float frac(float t, int k) { return t - (float)k; }
     static __device__ __forceinline__ float collision(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
@@ -495,7 +496,7 @@ __device__ __forceinline__ void plan_flight(Flight<P> &f, History<P> &s, const C
         f.a0 = l;
         return;
     }
-    const P c = R::dx(cp) * fabs(s.iw[0]);
+    const P c = R::dx(cp) * R::abs(s.iw[0]);
     f.a0 = R::nonneg(fma(-R::frac(ulo, k0), c, c));
     f.a1 = R::frac(uhi, k1) * c;
     f.c = c;
@@ -537,7 +538,7 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
     const P l_c = R::pos(R::sigma(cp, m)) ? R::nonneg(R::collision(cp, m, hi, lo)) : INF;
     draw_words(s, key, hi, lo);
     P l_i = R::interface(cp, m, hi, lo);
-    if (gd == 11) l_i *= fabs(s.iw[0]);  // slab: the chord projected on x, Lambda/|mu|
+    if (gd == 11) l_i *= R::abs(s.iw[0]);  // slab: the chord projected on x, Lambda/|mu|
     else if (gd == 2) l_i /= sqrt(P(1) - s.w[2] * s.w[2]);  // extruded: in-plane chord along the flight
     l_i = R::nonneg(l_i);
 
@@ -575,8 +576,8 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
     if (lateral) {
         if (bnd && face == 2 && R::eq(l_y, l_b)) {  // specular reflection on a y face
             s.r[1] = R::pos(s.w[1]) ? L : P(0);
-            s.w[1] = -s.w[1];
-            s.iw[1] = -s.iw[1];
+            s.w[1] = R::flip(s.w[1]);
+            s.iw[1] = R::flip(s.iw[1]);
         } else {
             s.r[1] += l * s.w[1];
         }
@@ -584,8 +585,8 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
     if (box) {
         if (bnd && face == 2 && R::eq(l_z, l_b)) {  // and/or on a z face
             s.r[2] = R::pos(s.w[2]) ? L : P(0);
-            s.w[2] = -s.w[2];
-            s.iw[2] = -s.iw[2];
+            s.w[2] = R::flip(s.w[2]);
+            s.iw[2] = R::flip(s.iw[2]);
         } else {
             s.r[2] += l * s.w[2];
         }

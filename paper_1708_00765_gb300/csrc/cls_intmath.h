@@ -1,15 +1,21 @@
-// cls_intlog.h -- the exponential variate -ln(1 - u) of the FP64 walk, in
-// 64/128-bit integer arithmetic.
+// cls_intmath.h -- the elementary functions of the FP64 walk's draws, in
+// 64/128-bit integer arithmetic: the exponential variate -ln(1 - u) and the
+// pair (sin, cos) of 2 pi u, for u = k 2^-53.
 //
 // The walk draws two distances per event, l_c = -ln(1 - u)/Sigma_m and
-// l_i = -Lambda_m ln(1 - u) (paper Sec. 4).  On GB300 the FP64 pipe is the
-// walk's bottleneck while the integer pipes idle, so the logarithm is
-// evaluated in fixed point: the table-driven reduction of Tang (ACM TOMS 16,
-// 1990) with an exact 64-bit product for the reduced argument, the Taylor
-// series of ln(1 + r) by Horner's rule in Q31/Q63 fixed point (precision
-// tapered to what each term needs), the sum in 128-bit fixed point with 120
-// fraction bits, and one rounding to the nearest double at the end.  The
-// result is within one ulp of -ln(1 - u).
+// l_i = -Lambda_m ln(1 - u) (paper Sec. 4), and the azimuth 2 pi u of every
+// new 3D direction (Sec. 4.3).  On GB300 the FP64 pipe is the walk's
+// bottleneck while the integer pipes idle, so these are evaluated in fixed
+// point:
+//  * the logarithm by the table-driven reduction of Tang (ACM TOMS 16, 1990)
+//    with an exact 64-bit product for the reduced argument, the Taylor series
+//    of ln(1 + r) by Horner's rule in Q31/Q63 (precision tapered to what each
+//    term needs), the sum in 128-bit fixed point with 120 fraction bits, and
+//    one rounding to the nearest double: within one ulp;
+//  * sine and cosine by angle addition from the nearest of 256 tabulated
+//    angles (|delta| <= pi/256) with the Taylor series of sin(delta) and
+//    cos(delta) - 1, in Q62-Q69 fixed point: absolute error below 2^-60 before
+//    the final rounding to double.
 //
 // Host and device compile the same code (the host build serves tests).
 #pragma once
@@ -151,6 +157,47 @@ CLS_HD double exp_variate(uint64_t k, IntLogTables tab) {
     // magnitude -s
     const U128 m = {0ull - s_lo, ~s_hi + (s_lo == 0ull ? 1ull : 0ull)};
     return u128_to_double(m, 120);
+}
+
+// v 2^-62 rounded to the nearest double, for a signed Q62 value v
+CLS_HD double q62_to_double(int64_t v) {
+    if (v == 0) return 0.0;
+    const uint64_t sgn = v < 0 ? (1ull << 63) : 0ull;
+    const uint64_t a = v < 0 ? 0ull - (uint64_t)v : (uint64_t)v;
+    const int lz = clz64(a);
+    const uint64_t x = a << lz;  // leading one at bit 63
+    uint64_t mant = x >> 11;
+    const uint64_t round = (x >> 10) & 1ull;
+    const uint64_t sticky = x & 0x3FFull;
+    mant += round & ((sticky != 0ull ? 1ull : 0ull) | (mant & 1ull));
+    const uint64_t ex = (uint64_t)(63 - lz - 62 + 1023 - 1);
+    return bits_to_double(sgn | ((ex << 52) + mant));
+}
+
+// (sin, cos) of 2 pi u for u = k 2^-53, 0 <= k < 2^53; sc: {sin, cos} of
+// 2 pi j/256 times 2^62.
+CLS_HD void sincos_2pi_int(uint64_t k, const int64_t (*sc)[2], double *sn, double *cs) {
+    const uint64_t j = (k + (1ull << 44)) >> 45;           // nearest tabulated angle, 0..256
+    const int64_t t = (int64_t)k - (int64_t)(j << 45);     // in [-2^44, 2^44)
+    const int64_t S = sc[j & 255ull][0], C = sc[j & 255ull][1];
+    // delta = 2 pi t 2^-53 in Q69 (|delta| < 2^-6.3)
+    const int64_t dh = smulhi64(t, CLS_TWO_PI_Q60);
+    const uint64_t dl = (uint64_t)t * (uint64_t)CLS_TWO_PI_Q60;
+    const int64_t d = (int64_t)(((uint64_t)dh << 20) | (dl >> 44));
+    const int64_t d2 = smulhi64(d, d) >> 11;                               // delta^2, Q63
+    // sin(delta) = delta - delta d2 (1/6 - d2 (1/120 - d2/5040))
+    const int64_t b = 0x0111111111111111ll - mulq63(d2, 0x0006806806806807ll);  // 1/120 - d2/5040
+    const int64_t a = 0x1555555555555555ll - mulq63(d2, b);                    // 1/6 - d2 b
+    const int64_t sd = d - mulq63(mulq63(d, d2), a);                           // Q69
+    // cos(delta) - 1 = -d2 (1/2 - d2 (1/24 - d2/720))
+    const int64_t e = 0x0555555555555555ll - mulq63(d2, 0x002d82d82d82d82ell);  // 1/24 - d2/720
+    const int64_t h = (1ll << 62) - mulq63(d2, e);                             // 1/2 - d2 e
+    const int64_t cm1 = -mulq63(d2, h);                                        // Q63
+    // sin(a + delta) = S + S cm1 + C sin(delta); cos(a + delta) = C + C cm1 - S sin(delta)  (Q62)
+    const int64_t s_cm1 = mulq63(S, cm1), c_cm1 = mulq63(C, cm1);
+    const int64_t c_sd = smulhi64(C, sd) >> 5, s_sd = smulhi64(S, sd) >> 5;   // (Q62 Q69) >> 69
+    *sn = q62_to_double(S + s_cm1 + c_sd);
+    *cs = q62_to_double(C + c_cm1 - s_sd);
 }
 
 }  // namespace cls

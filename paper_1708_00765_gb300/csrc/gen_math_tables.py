@@ -2,8 +2,7 @@
 
 Run from this directory (`python gen_math_tables.py`); the output is committed.
 Every value is computed here in exact or 60-digit decimal arithmetic (Python's
-standard `decimal` module) and rounded once, to the nearest double or to the
-nearest multiple of 2^-120.
+standard `decimal` module) and rounded once to a fixed-point integer.
 
 Logarithm (table-driven, after P. T. P. Tang, "Table-driven implementation of
 the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16, 1990),
@@ -13,8 +12,8 @@ r = m N_i / 2048 - 1 is an exact 64-bit product with |r| < 2^-8.6, and
 ln m = T_i + ln(1 + r), T_i = -ln(N_i / 2048), tabulated as a 128-bit
 fixed-point number with 120 fraction bits (as is ln 2).
 
-Sine/cosine of 2 pi j / 256, j = 0..255, each rounded to the nearest double
-(exact zeros and ones at the quadrant points).
+Sine/cosine of 2 pi j / 256, j = 0..255, as 64-bit fixed-point numbers with 62
+fraction bits, rounded (exact zeros and ones at the quadrant points).
 """
 from __future__ import annotations
 
@@ -28,11 +27,6 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 def dec(fr: Fraction) -> Decimal:
     return Decimal(fr.numerator) / Decimal(fr.denominator)
-
-
-def to_double(x: Decimal) -> float:
-    # Python's float() of a decimal string is correctly rounded
-    return float(x)
 
 
 def ln(x: Decimal) -> Decimal:
@@ -74,10 +68,6 @@ def sin_cos(a: Decimal) -> tuple[Decimal, Decimal]:
     return s, c
 
 
-def hexd(v: float) -> str:
-    return v.hex() if v != 0.0 else "0x0p+0"
-
-
 def log_table() -> tuple[list[tuple[int, int]], int]:
     """[(N_i, T_i 2^120 rounded)], ln 2 2^120 rounded."""
     scale = Decimal(2) ** 120
@@ -92,17 +82,23 @@ def log_table() -> tuple[list[tuple[int, int]], int]:
     return rows, ln2
 
 
-def sincos_table() -> list[tuple[float, float]]:
+def sincos_table() -> list[tuple[int, int]]:
+    """[(sin, cos) of 2 pi j / 256, times 2^62, rounded]."""
     twopi = 2 * pi()
+    one = 1 << 62
     rows = []
     for j in range(256):
         if j % 64 == 0:
-            q = j // 64
-            rows.append(((0.0, 1.0), (1.0, 0.0), (0.0, -1.0), (-1.0, 0.0))[q])
+            rows.append(((0, one), (one, 0), (0, -one), (-one, 0))[j // 64])
             continue
         s, c = sin_cos(twopi * j / 256)
-        rows.append((to_double(s), to_double(c)))
+        scale = Decimal(one)
+        rows.append((int((s * scale).to_integral_value()), int((c * scale).to_integral_value())))
     return rows
+
+
+def two_pi_q60() -> int:
+    return int((2 * pi() * Decimal(2) ** 60).to_integral_value())
 
 
 def main() -> None:
@@ -124,6 +120,8 @@ def main() -> None:
         "// ln 2 2^120, rounded: high and low 64-bit words",
         f"#define CLS_LN2_Q120_HI 0x{ln2 >> 64:016x}ull",
         f"#define CLS_LN2_Q120_LO 0x{ln2 & M64:016x}ull",
+        "// 2 pi 2^60, rounded",
+        f"#define CLS_TWO_PI_Q60 0x{two_pi_q60():016x}ll",
         "#define CLS_LOG_TABLE_N 256",
         "#define CLS_SINCOS_TABLE_N 256",
         "",
@@ -137,10 +135,10 @@ def main() -> None:
             "CLS_TABLE_SPACE const uint64_t cls_log_t_init[CLS_LOG_TABLE_N][2] = {"]
     for _, T in logs:
         out.append(f"    {{0x{T & M64:016x}ull, 0x{T >> 64:016x}ull}},")
-    out += ["};", "", "// {sin, cos} of 2 pi j / 256",
-            "CLS_TABLE_SPACE const double cls_sincos_table_init[CLS_SINCOS_TABLE_N][2] = {"]
+    out += ["};", "", "// {sin, cos} of 2 pi j / 256, times 2^62, rounded",
+            "CLS_TABLE_SPACE const int64_t cls_sincos_q62_init[CLS_SINCOS_TABLE_N][2] = {"]
     for s_, c_ in sc:
-        out.append(f"    {{{hexd(s_)}, {hexd(c_)}}},")
+        out.append(f"    {{{s_}ll, {c_}ll}},")
     out += ["};", "", "}  // namespace cls", ""]
     with open(os.path.join(HERE, "cls_math_tables.h"), "w") as fh:
         fh.write("\n".join(out))
