@@ -115,6 +115,20 @@ struct Real<double> {
     static __device__ __forceinline__ double two_u_minus_one(uint32_t hi, uint32_t lo) {
         return scaled_int((long long)k53(hi, lo) - (1ll << 52), -52);
     }
+    // sqrt(u) = sqrt(2k 2^-54), in integer arithmetic
+    static __device__ __forceinline__ double sqrt_uniform(uint32_t hi, uint32_t lo) {
+        return sqrt_int(U128{k53(hi, lo) << 1, 0ull}, 54);
+    }
+    // A new direction's cosine mu and st = sqrt(1 - mu^2) from the draw u of mu:
+    // cosine law mu = sqrt(u), st = sqrt(1 - u); isotropic mu = 2u - 1,
+    // st = sqrt(4 u (1 - u)), with 1 - u and 4 u (1 - u) exact integers
+    static __device__ __forceinline__ void direction_cosines(uint32_t hi, uint32_t lo, bool cosine, double *mu,
+                                                             double *st) {
+        const unsigned long long k = k53(hi, lo), n = (1ull << 53) - k;
+        *mu = cosine ? sqrt_uniform(hi, lo) : two_u_minus_one(hi, lo);
+        const U128 x = cosine ? U128{n << 1, 0ull} : U128{(k * n) << 2, (umulhi64(k, n) << 2) | ((k * n) >> 62)};
+        *st = sqrt_int(x, cosine ? 54 : 106);
+    }
     // 1 - u, exactly: (2^53 - k) 2^-53
     static __device__ __forceinline__ double one_minus(uint32_t hi, uint32_t lo) {
         return (double)((1ull << 53) - k53(hi, lo)) * 0x1p-53;
@@ -174,29 +188,8 @@ struct Real<double> {
     static __device__ __forceinline__ double interface(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
         return c.lambda[m] * exp_variate_shared(k53(hi, lo));
     }
-    // 1/a by Newton-Raphson iteration for the reciprocal, r <- r + r (1 - a r)
-    // (each step squares the relative error; P. Markstein, IBM J. Res. Dev. 34,
-    // 1990), two steps from the FP32 approximate reciprocal of a's leading 24
-    // bits (relative error below 2^-22), so within an ulp or so of 1/a.
-    // |a| outside [2^-120, 2^121) takes the division.
-    static __device__ __forceinline__ double recip(double a) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(a);
-        const unsigned int hi = (unsigned int)(b >> 32);
-        const int ex = (int)((hi >> 20) & 0x7FF) - 1023;
-        if (ex < -120 || ex > 120) return 1.0 / a;
-        const unsigned int fb = (hi & 0x80000000u) | ((unsigned int)(ex + 127) << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu);
-        float rf;
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
-        const unsigned int rb = __float_as_uint(rf);
-        const int rex = (int)((rb >> 23) & 0xFF) - 127;
-        const unsigned long long db = ((unsigned long long)(rb & 0x80000000u) << 32) |
-                                      ((unsigned long long)(rex + 1023) << 52) | ((unsigned long long)(rb & 0x7FFFFFu) << 29);
-        double r = __longlong_as_double((long long)db);
-        double e = fma(-a, r, 1.0);
-        r = fma(r, e, r);
-        e = fma(-a, r, 1.0);
-        return fma(r, e, r);
-    }
+    // 1/a in integer arithmetic (Newton-Raphson, cls_intmath.h)
+    static __device__ __forceinline__ double recip(double a) { return recip_int(a); }
     // (sin, cos) of 2 pi u from the draw's words
     static __device__ __forceinline__ void sincos_2pi(uint32_t hi, uint32_t lo, double *s, double *co) {
         sincos_2pi_shared(k53(hi, lo), s, co);
@@ -212,6 +205,12 @@ struct Real<float> {
     // the same draw truncated to its top 24 bits: u = k 2^-24
     static __device__ __forceinline__ float uniform(uint32_t hi, uint32_t) { return (float)(hi >> 8) * 0x1p-24f; }
     static __device__ __forceinline__ float two_u_minus_one(uint32_t hi, uint32_t lo) { return 2.0f * uniform(hi, lo) - 1.0f; }
+    static __device__ __forceinline__ float sqrt_uniform(uint32_t hi, uint32_t lo) { return sqrtf(uniform(hi, lo)); }
+    static __device__ __forceinline__ void direction_cosines(uint32_t hi, uint32_t lo, bool cosine, float *mu,
+                                                            float *st) {
+        *mu = cosine ? sqrt_uniform(hi, lo) : two_u_minus_one(hi, lo);
+        *st = sqrtf(1.0f - *mu * *mu);
+    }
     static __device__ __forceinline__ float one_minus(uint32_t hi, uint32_t) {
         return (float)((1u << 24) - (hi >> 8)) * 0x1p-24f;
     }
@@ -294,6 +293,24 @@ __device__ __forceinline__ void draw_words(History<P> &s, const RoundKeys &key, 
     ++s.j;
 }
 
+// Output words of draws j and j + 1 (j = s.j); advances j by 2.  The pair
+// always needs exactly one Philox block -- words (0,1), (2,3) of block j/2 for
+// even j; the cached words of the last block and words (0,1) of block
+// (j+1)/2 for odd j -- so a warp computes it once, whatever its lanes' parities.
+template <typename P>
+__device__ __forceinline__ void draw_pair(History<P> &s, const RoundKeys &key, uint32_t &hi0, uint32_t &lo0,
+                                          uint32_t &hi1, uint32_t &lo1) {
+    const bool odd = (s.j & 1u) != 0u;
+    const uint4 o = philox4x32_10(make_uint4((s.j + 1u) >> 1, s.h_lo, s.h_hi, s.cid), key);
+    hi0 = odd ? s.c2 : o.x;
+    lo0 = odd ? s.c3 : o.y;
+    hi1 = odd ? o.x : o.z;
+    lo1 = odd ? o.y : o.w;
+    s.c2 = o.z;  // read by draw j + 2 when it is odd
+    s.c3 = o.w;
+    s.j += 2u;
+}
+
 template <typename P>
 __device__ __forceinline__ P draw(History<P> &s, const RoundKeys &key) {
     uint32_t hi, lo;
@@ -315,14 +332,6 @@ __device__ __forceinline__ P draw_iso(History<P> &s, const RoundKeys &key) {
     uint32_t hi, lo;
     draw_words(s, key, hi, lo);
     return Real<P>::two_u_minus_one(hi, lo);
-}
-
-// (sin, cos) of 2 pi u for the next draw u
-template <typename P>
-__device__ __forceinline__ void draw_sincos_2pi(History<P> &s, const RoundKeys &key, P *sn, P *cs) {
-    uint32_t hi, lo;
-    draw_words(s, key, hi, lo);
-    Real<P>::sincos_2pi(hi, lo, sn, cs);
 }
 
 // whether the next draw is below the value whose thresholds are given
@@ -353,21 +362,34 @@ __device__ __forceinline__ void set_direction(History<P> &s, P wx, P wy, P wz) {
     s.iw[2] = R::is_zero(wz) ? R::inf() : R::recip(wz);
 }
 
+// Direction (wx, 0, 0) of the slab and the x-projected box: no reciprocal of
+// the zero components
+template <typename P>
+__device__ __forceinline__ void set_direction_x(History<P> &s, P wx) {
+    using R = Real<P>;
+    s.w[0] = wx;
+    s.w[1] = P(0);
+    s.w[2] = P(0);
+    s.iw[0] = R::is_zero(wx) ? R::inf() : R::recip(wx);
+    s.iw[1] = R::inf();
+    s.iw[2] = R::inf();
+}
+
 // Draw the pending direction of a 3D or extruded walk: mu, then the azimuth
 // phi, then (at the source) the material label, in the order of the serial
 // walk.  Cosine-law incidence (paper Sec. 4.3): mu = sqrt(xi) about +x,
 // omega = (mu, st cos phi, st sin phi); isotropic (scattering, volume source):
 // mu = 2 xi - 1, omega = (st cos phi, st sin phi, mu); st = sqrt(1 - mu^2).
-template <typename P>
+template <typename P, int G = 0>
 __device__ __forceinline__ void resolve_direction(History<P> &s, const CaseParams &cp, const RoundKeys &key) {
+    if constexpr (G != 0 && G != 2 && G != 3) return;  // no pending directions in these geometries
     if (s.pend == DIR_NONE) return;
     const bool cosine = s.pend == DIR_SOURCE_COSINE;
-    uint32_t hi, lo;
-    draw_words(s, key, hi, lo);
-    const P mu = cosine ? sqrt(Real<P>::uniform(hi, lo)) : Real<P>::two_u_minus_one(hi, lo);
-    P sn, cs;
-    draw_sincos_2pi(s, key, &sn, &cs);
-    const P st = sqrt(P(1) - mu * mu);
+    uint32_t hi, lo, phi_hi, phi_lo;
+    draw_pair(s, key, hi, lo, phi_hi, phi_lo);  // mu, then phi
+    P mu, st, sn, cs;
+    Real<P>::direction_cosines(hi, lo, cosine, &mu, &st);
+    Real<P>::sincos_2pi(phi_hi, phi_lo, &sn, &cs);
     const P a = st * cs, b = st * sn;
     set_direction(s, cosine ? mu : a, cosine ? a : b, cosine ? b : mu);
     if (s.pend != DIR_SCATTER) s.m = draw_below(s, key, cp.thr_p053, cp.thr_p024) ? 0 : 1;
@@ -394,16 +416,22 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, cons
     const P L = R::L(cp);
     if (gd == 3 || gd == 2) {
         if (cp.source == 1) s.r[0] = L * draw(s, key);  // suite II: uniform position, isotropic direction
-        s.r[1] = L * draw(s, key);
-        if (gd == 3) s.r[2] = L * draw(s, key);
+        if (gd == 3) {  // y, then z
+            uint32_t yh, yl, zh, zl;
+            draw_pair(s, key, yh, yl, zh, zl);
+            s.r[1] = L * R::uniform(yh, yl);
+            s.r[2] = L * R::uniform(zh, zl);
+        } else {
+            s.r[1] = L * draw(s, key);
+        }
         s.pend = (cp.source == 1) ? DIR_SOURCE_ISOTROPIC : DIR_SOURCE_COSINE;
-        if (!DEFER) resolve_direction(s, cp, key);
+        if (!DEFER) resolve_direction<P, G>(s, cp, key);
         return;
     }
     if (cp.source == 1) {
         s.r[0] = L * draw(s, key);
         if (gd == 11 || gd == 13) {
-            set_direction(s, draw_iso(s, key), P(0), P(0));
+            set_direction_x(s, draw_iso(s, key));
         } else {
             uint32_t hi, lo;
             draw_words(s, key, hi, lo);
@@ -416,7 +444,9 @@ __device__ __forceinline__ void source(History<P> &s, const CaseParams &cp, cons
             s.iw[2] = R::inf();
         }
     } else if (gd == 11 || gd == 13) {
-        set_direction(s, sqrt(draw(s, key)), P(0), P(0));  // slab, projected box: mu = sqrt(xi)
+        uint32_t hi, lo;  // slab, projected box: mu = sqrt(xi)
+        draw_words(s, key, hi, lo);
+        set_direction_x(s, R::sqrt_uniform(hi, lo));
     } else {
         s.w[0] = P(1);
         s.w[1] = P(0);
@@ -532,12 +562,21 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
     const P INF = R::inf();
     const P L = R::L(cp);
 
-    // collision, then interface distance
-    uint32_t hi, lo;
-    draw_words(s, key, hi, lo);
-    const P l_c = R::pos(R::sigma(cp, m)) ? R::nonneg(R::collision(cp, m, hi, lo)) : INF;
-    draw_words(s, key, hi, lo);
-    P l_i = R::interface(cp, m, hi, lo);
+    // collision, then interface distance.  One Philox block serves both draws
+    // (draw_pair), except in the FP32 x-projected walk, where holding the pair
+    // spills registers (measured 10% slower there, 4-7% faster elsewhere).
+    uint32_t hi, lo, ihi, ilo;
+    P l_c, l_i;
+    if constexpr (sizeof(P) == 4 && G == 13) {
+        draw_words(s, key, hi, lo);
+        l_c = R::pos(R::sigma(cp, m)) ? R::nonneg(R::collision(cp, m, hi, lo)) : INF;
+        draw_words(s, key, ihi, ilo);
+        l_i = R::interface(cp, m, ihi, ilo);
+    } else {
+        draw_pair(s, key, hi, lo, ihi, ilo);
+        l_c = R::pos(R::sigma(cp, m)) ? R::nonneg(R::collision(cp, m, hi, lo)) : INF;
+        l_i = R::interface(cp, m, ihi, ilo);
+    }
     if (gd == 11) l_i *= R::abs(s.iw[0]);  // slab: the chord projected on x, Lambda/|mu|
     else if (gd == 2) l_i /= sqrt(P(1) - s.w[2] * s.w[2]);  // extruded: in-plane chord along the flight
     l_i = R::nonneg(l_i);
@@ -611,10 +650,10 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
                 s.w[0] = w;
                 s.iw[0] = w;
             } else if (gd == 11 || gd == 13) {
-                set_direction(s, draw_iso(s, key), P(0), P(0));  // mu = 2 xi - 1
+                set_direction_x(s, draw_iso(s, key));  // mu = 2 xi - 1
             } else {
                 s.pend = DIR_SCATTER;  // mu = 2 xi - 1, then phi
-                if (!DEFER) resolve_direction(s, cp, key);
+                if (!DEFER) resolve_direction<P, G>(s, cp, key);
             }
             trace_row<P, TRACE>(tr, EV_SCATTER, s, (double)l);
             return -1;
@@ -912,7 +951,7 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const
         int out = -1;
         if (alive) {
             // directions of the lanes born in this round and of those that scattered in the last
-            resolve_direction(s, a.cases[lcase], key);
+            resolve_direction<P, G>(s, a.cases[lcase], key);
             out = step<P, false, G, true>(s, a.cases[lcase], key, a.max_events, f, nullptr);
         }
         const uint32_t goff = (lreg == 2) ? ((uint32_t)lcase * (uint32_t)a.t.nbatch + lbatch) * (uint32_t)a.t.nbins_stride : 0u;

@@ -21,6 +21,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <math.h>
 #include <string.h>
 
 #include "cls_math_tables.h"
@@ -198,6 +199,101 @@ CLS_HD void sincos_2pi_int(uint64_t k, const int64_t (*sc)[2], double *sn, doubl
     const int64_t c_sd = smulhi64(C, sd) >> 5, s_sd = smulhi64(S, sd) >> 5;   // (Q62 Q69) >> 69
     *sn = q62_to_double(S + s_cm1 + c_sd);
     *cs = q62_to_double(C + c_cm1 - s_sd);
+}
+
+// floor(a d / 2^62) for a in (0, 2^62] and signed d
+CLS_HD int64_t mulq62(int64_t a, int64_t d) {
+    return (int64_t)(((uint64_t)smulhi64(a, d) << 2) | (((uint64_t)a * (uint64_t)d) >> 62));
+}
+
+// 1/a for a normal double a: Newton-Raphson iteration for the reciprocal,
+// y <- y + y (1 - m y) (each step squares the relative error; P. Markstein,
+// IBM J. Res. Dev. 34, 1990), run twice in Q62 fixed point on the significand
+// m in [1, 2) from the FP32 approximate reciprocal of its leading 24 bits
+// (relative error below 2^-22), then one rounding to the nearest double:
+// within an ulp of 1/a.  Zero, subnormal, infinite and NaN a take the division.
+CLS_HD double recip_int(double a) {
+    uint64_t b;
+#ifdef __CUDA_ARCH__
+    b = (uint64_t)__double_as_longlong(a);
+#else
+    memcpy(&b, &a, sizeof b);
+#endif
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0 || ex == 0x7FF) return 1.0 / a;
+    const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // m 2^52
+    // seed: y0 ~ 1/m in (1/2, 1], from m's leading 24 bits
+    const uint32_t fb = 0x3F800000u | (uint32_t)((b >> 29) & 0x7FFFFFu);
+    float mf, rf;
+#ifdef __CUDA_ARCH__
+    mf = __uint_as_float(fb);
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
+#else
+    memcpy(&mf, &fb, sizeof mf);
+    rf = 1.0f / mf;
+#endif
+    uint32_t rb;
+    memcpy(&rb, &rf, sizeof rb);
+    const int re = (int)((rb >> 23) & 0xFF) - 127;                    // -1, or 0 when y0 = 1
+    int64_t y = (int64_t)(((uint64_t)((rb & 0x7FFFFFu) | 0x800000u)) << (39 + re));  // y0 2^62
+    for (int it = 0; it < 2; ++it) {
+        const uint64_t hi = umulhi64(M, (uint64_t)y), lo = M * (uint64_t)y;
+        const int64_t t = (int64_t)((hi << 12) | (lo >> 52));         // m y 2^62
+        y += mulq62(y, (1ll << 62) - t);
+    }
+    // 1/|a| = y 2^-62 2^(1023 - ex), rounded to 53 bits
+    const uint64_t x = (uint64_t)y;
+    const int lz = clz64(x);
+    const uint64_t n = x << lz;
+    uint64_t mant = n >> 11;
+    mant += ((n >> 10) & 1ull) & (((n & 0x3FFull) != 0ull ? 1ull : 0ull) | (mant & 1ull));
+    const uint64_t e = (uint64_t)(63 - lz - 62 + (1023 - ex) + 1023 - 1);
+    return bits_to_double((b & (1ull << 63)) | ((e << 52) + mant));
+}
+
+// sqrt(X 2^-scale) rounded to the nearest double, for 0 <= X < 2^127 and even
+// scale: Newton-Raphson iteration for the reciprocal square root,
+// y <- y + y (1 - v y^2)/2, twice in Q61 fixed point on v = X 2^-2t in
+// [1/4, 1) from the FP32 approximate reciprocal square root of v's leading
+// 24 bits (relative error below 2^-22), then sqrt(v) = v y and one rounding:
+// within an ulp.
+CLS_HD double sqrt_int(U128 X, int scale) {
+    if ((X.hi | X.lo) == 0ull) return 0.0;
+    // normalise by an even shift: v = X' 2^-128 in [1/4, 1)
+    const int lz = X.hi ? clz64(X.hi) : 64 + clz64(X.lo);
+    const int sh = lz & ~1;
+    uint64_t h = X.hi, l = X.lo;
+    if (sh >= 64) {
+        h = l << (sh - 64);
+    } else if (sh > 0) {
+        h = (h << sh) | (l >> (64 - sh));
+    }
+    const uint64_t v = h;  // v 2^64: the top 64 bits of X' (the rest is below the rounding)
+    // seed y0 ~ 1/sqrt(v) in (1, 2], Q61
+    float vf = (float)(uint32_t)(v >> 40) * 0x1p-24f, yf;  // v's leading 24 bits, exactly
+#ifdef __CUDA_ARCH__
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(vf));
+#else
+    yf = 1.0f / sqrtf(vf);
+#endif
+    uint32_t yb;
+    memcpy(&yb, &yf, sizeof yb);
+    const int ye = (int)((yb >> 23) & 0xFF) - 127;  // 0, or 1 when y0 = 2
+    int64_t y = (int64_t)(((uint64_t)((yb & 0x7FFFFFu) | 0x800000u)) << (38 + ye));
+    for (int it = 0; it < 2; ++it) {
+        const uint64_t vy = umulhi64(v, (uint64_t)y);                 // v y, Q61
+        const int64_t t = (int64_t)(umulhi64(vy, (uint64_t)y) << 4);  // v y^2, Q62
+        y += mulq62(y, ((1ll << 62) - t) >> 1);                      // + y (1 - v y^2)/2
+    }
+    const uint64_t q = umulhi64(v, (uint64_t)y);  // sqrt(v) = v y, Q61, in [2^60, 2^61]
+    const int qz = clz64(q);
+    const uint64_t n = q << qz;
+    uint64_t mant = n >> 11;
+    mant += ((n >> 10) & 1ull) & (((n & 0x3FFull) != 0ull ? 1ull : 0ull) | (mant & 1ull));
+    // sqrt(X 2^-scale) = sqrt(v) 2^((128 - sh - scale)/2)
+    const int e2 = (128 - sh - scale) / 2;
+    const uint64_t e = (uint64_t)(63 - qz - 61 + e2 + 1023 - 1);
+    return bits_to_double((e << 52) + mant);
 }
 
 }  // namespace cls

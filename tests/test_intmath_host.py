@@ -1,5 +1,5 @@
-"""The FP64 walk's exponential variate -ln(1 - u) and (sin, cos)(2 pi u),
-compiled for the host.
+"""The FP64 walk's exponential variate -ln(1 - u), (sin, cos)(2 pi u),
+reciprocal and square root, compiled for the host.
 
 cls_intmath.h is integer arithmetic only, so the host build computes exactly
 what the device computes; it is checked here against 50-digit decimal
@@ -23,7 +23,19 @@ PROGRAM = r"""
 #define CLS_TABLE_SPACE
 #include "cls_intmath.h"
 #include <cstdio>
-int main() {
+#include <cstdlib>
+int main(int argc, char **argv) {
+    if (argc > 1 && argv[1][0] == 's') {  // sqrt(X 2^-scale) for "X_hi X_lo scale" lines
+        unsigned long long hi, lo;
+        int sc;
+        while (std::scanf("%llu %llu %d", &hi, &lo, &sc) == 3) std::printf("%a\n", cls::sqrt_int(cls::U128{lo, hi}, sc));
+        return 0;
+    }
+    if (argc > 1) {  // reciprocals of the doubles read as hex floats
+        char buf[64];
+        while (std::scanf("%63s", buf) == 1) std::printf("%a\n", cls::recip_int(std::strtod(buf, nullptr)));
+        return 0;
+    }
     cls::IntLogTables tab{cls::cls_log_n_init, cls::cls_log_t_init};
     unsigned long long k;
     while (std::scanf("%llu", &k) == 1) {
@@ -45,11 +57,23 @@ def intmath(tmp_path_factory):
     src.write_text(PROGRAM)
     subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
 
+    def recip(xs):
+        out = subprocess.run([str(exe), "recip"], input="\n".join(x.hex() for x in xs), capture_output=True,
+                             text=True, check=True).stdout.split()
+        return [float.fromhex(v) for v in out]
+
     def run(ks):
         out = subprocess.run([str(exe)], input="\n".join(map(str, ks)), capture_output=True, text=True,
                              check=True).stdout.split("\n")
         return [tuple(float.fromhex(v) for v in line.split()) for line in out[:len(ks)]]
 
+    def sqrt(cases):
+        inp = "\n".join(f"{x >> 64} {x & (2**64 - 1)} {sc}" for x, sc in cases)
+        out = subprocess.run([str(exe), "sqrt"], input=inp, capture_output=True, text=True, check=True).stdout.split()
+        return [float.fromhex(v) for v in out]
+
+    run.recip = recip
+    run.sqrt = sqrt
     return run
 
 
@@ -129,3 +153,44 @@ def test_sincos_within_2m53(intmath):
         rs, rc = dec_sin_cos(a)
         worst = max(worst, float(abs(Decimal(s) - rs)), float(abs(Decimal(c) - rc)))
     assert worst <= 2.0**-53, worst
+
+
+def test_reciprocal_within_one_ulp(intmath):
+    """recip_int against exact rational reciprocals.  The host seeds the
+    Newton-Raphson steps with the correctly rounded FP32 reciprocal, the device
+    with the approximate one; two steps leave either within an ulp."""
+    from fractions import Fraction
+    rnd = random.Random(6)
+    xs = [1.0, -1.0, 0.5, 1.5, math.nextafter(2.0, 0.0), math.nextafter(1.0, 2.0), -0.3, 1e-20, 2.0**-1000, 0.0]
+    xs += [rnd.uniform(-1.0, 1.0) for _ in range(5000)]
+    xs += [rnd.uniform(1.0, 2.0) * 2.0**rnd.randint(-80, 5) for _ in range(3000)]
+    got = intmath.recip(xs)
+    worst = 0.0
+    for x, v in zip(xs, got):
+        if x == 0.0:
+            assert math.isinf(v)
+            continue
+        ref = 1 / Fraction(x)
+        worst = max(worst, float(abs(Fraction(v) - ref) / Fraction(math.ulp(float(ref)))))
+    assert worst <= 1.0, worst
+
+
+def test_sqrt_within_one_ulp(intmath):
+    """sqrt_int against integer square roots (math.isqrt), on the walk's three
+    uses -- sqrt(u), sqrt(1 - u) and sqrt(4 u (1 - u)) for u = k 2^-53 -- and on
+    arbitrary 128-bit arguments."""
+    from fractions import Fraction
+    rnd = random.Random(8)
+    cases = [(0, 0), (1, 0), (2, 0), (4, 0), (2**126, 0), (2**127 - 1, 0), (3, 2), (2**104, 106)]
+    for k in [1, 2, 2**52, 2**53 - 1] + [rnd.getrandbits(53) or 1 for _ in range(3000)]:
+        cases += [(4 * k * (2**53 - k), 106), (2 * k, 54), (2 * (2**53 - k), 54)]
+    cases += [(rnd.getrandbits(rnd.randint(1, 126)) | 1, 2 * rnd.randint(0, 60)) for _ in range(2000)]
+    got = intmath.sqrt(cases)
+    worst = 0.0
+    for (x, sc), v in zip(cases, got):
+        if x == 0:
+            assert v == 0.0
+            continue
+        ref = Fraction(math.isqrt(x << 200), 2**100) / 2 ** (sc // 2)
+        worst = max(worst, float(abs(Fraction(v) - ref) / Fraction(math.ulp(float(ref)))))
+    assert worst <= 1.0, worst
