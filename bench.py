@@ -31,17 +31,22 @@ sys.path.insert(0, ROOT)
 METRIC = "histories/s and FOM 1/(sigma^2 T) at equal sigma, FP32-batched vs FP64-plain on 1 GB300"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# Per-event work of the benchmark workload's kernels, from ncu op counters on a
-# 2e6-history launch (profiles/history_kernel_box_L10.md): FP64 flops
-# (DADD + DMUL + 2 DFMA thread instructions) per event of history_kernel<double>,
-# and warp instructions per event of history_kernel<float>.  Re-measured
-# whenever the kernel changes.
+# Algorithmic work per event of the benchmark workload's kernels, fixed numbers
+# (profiles/history_kernel_box_L10.md):
+# * FP64: 148.8 flop per event, the FP64 arithmetic of one event of Algorithm A
+#   evaluated directly in FP64 with FP64 elementary functions (ln, sin/cos,
+#   division), counted as DADD + DMUL + 2 DFMA thread instructions by ncu on
+#   that direct evaluation.  The current kernel evaluates ln and sin/cos in the
+#   integer pipes and executes about 29 FP64 operations per event, so this is
+#   the work in FP64-equivalent flops; the same event done with fewer FP64
+#   operations raises the fraction.
+# * FP32: 40.4 warp instructions per event of history_kernel<float>.
 FP64_FLOP_PER_EVENT = 148.8
 FP32_WARP_INST_PER_EVENT = 40.4
 # DRAM bytes per full-size FP64 launch (1e8 histories) from a one-pass ncu
-# capture of the current kernel (profiles/history_kernel_box_L10.md); set to
-# None whenever the kernel changes until it is captured again.
-FP64_DRAM_BYTES_PER_LAUNCH = 774144
+# capture of the current kernel (profiles/history_kernel_box_L10.md); None
+# whenever the kernel has changed since the capture.
+FP64_DRAM_BYTES_PER_LAUNCH = 963072
 SM_COUNT = 152           # GB300
 DFMA_PER_SM_CLK = 2      # ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / 152 SMs
 ISSUE_PER_SM_CLK = 4     # one warp instruction per scheduler per clock, 4 schedulers
@@ -509,7 +514,7 @@ def main():
         r["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": FP64_DRAM_BYTES_PER_LAUNCH,
                          "kernel": "history_kernel<double>",
-                         "work": f"{FP64_FLOP_PER_EVENT} FP64 flop/event x {r['events_per_launch']:.4g} events/launch",
+                         "work": f"{FP64_FLOP_PER_EVENT} FP64-equivalent flop/event x {r['events_per_launch']:.4g} events/launch",
                          "peak_from": f"{SM_COUNT} SM x {DFMA_PER_SM_CLK} DFMA/clk x 2 flop x {clk_mhz} MHz (sampled)"}
     if "fp32" in results:
         r = results["fp32"]
