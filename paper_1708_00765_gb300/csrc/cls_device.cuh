@@ -125,9 +125,20 @@ struct Real<double> {
     static __device__ __forceinline__ void direction_cosines(uint32_t hi, uint32_t lo, bool cosine, double *mu,
                                                              double *st) {
         const unsigned long long k = k53(hi, lo), n = (1ull << 53) - k;
-        *mu = cosine ? sqrt_uniform(hi, lo) : two_u_minus_one(hi, lo);
-        const U128 x = cosine ? U128{n << 1, 0ull} : U128{(k * n) << 2, (umulhi64(k, n) << 2) | ((k * n) >> 62)};
-        *st = sqrt_int(x, cosine ? 54 : 106);
+        // sqrt(u) (used by the cosine law only), then st, through one copy of sqrt_int
+        U128 x = U128{k << 1, 0ull};
+        const U128 x1 = cosine ? U128{n << 1, 0ull} : U128{(k * n) << 2, (umulhi64(k, n) << 2) | ((k * n) >> 62)};
+        int scale = 54;
+        double r0 = 0.0, r1 = 0.0;
+#pragma unroll 1
+        for (int t = 0; t < 2; ++t) {
+            r0 = r1;
+            r1 = sqrt_int(x, scale);
+            x = x1;
+            scale = cosine ? 54 : 106;
+        }
+        *mu = cosine ? r0 : two_u_minus_one(hi, lo);
+        *st = r1;
     }
     // 1 - u, exactly: (2^53 - k) 2^-53
     static __device__ __forceinline__ double one_minus(uint32_t hi, uint32_t lo) {
@@ -181,12 +192,30 @@ struct Real<double> {
         const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
         const unsigned long long m = (((M >> sh) - (unsigned long long)k) << sh) + (M & ((1ull << sh) - 1ull));
         return e < 0 ? t : scaled_int((long long)m, -sh);
-    }    // l_c = -ln(1 - u) / Sigma_m, as -ln(1 - u) * (1 / Sigma_m), from the draw's words
+    }
+    // l_c = -ln(1 - u) / Sigma_m, as -ln(1 - u) * (1 / Sigma_m), from the draw's words
     static __device__ __forceinline__ double collision(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
         return exp_variate_shared(k53(hi, lo)) * c.inv_sigma[m];
     }
     static __device__ __forceinline__ double interface(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
         return c.lambda[m] * exp_variate_shared(k53(hi, lo));
+    }
+    static __device__ __forceinline__ double inv_sigma(const CaseParams &c, int m) { return c.inv_sigma[m]; }
+    static __device__ __forceinline__ double lambda(const CaseParams &c, int m) { return c.lambda[m]; }
+    // -ln(1 - u) of two draws through one copy of the evaluation (the loop is
+    // kept rolled: the instruction cache is one of the walk's limits)
+    static __device__ __forceinline__ void exp_variates(uint32_t hi0, uint32_t lo0, uint32_t hi1, uint32_t lo1,
+                                                        double *e0, double *e1) {
+        unsigned long long ka = k53(hi0, lo0), kb = k53(hi1, lo1);
+        double a = 0.0, b = 0.0;
+#pragma unroll 1
+        for (int t = 0; t < 2; ++t) {
+            a = b;
+            b = exp_variate_shared(ka);
+            ka = kb;
+        }
+        *e0 = a;
+        *e1 = b;
     }
     // 1/a in integer arithmetic (Newton-Raphson, cls_intmath.h)
     static __device__ __forceinline__ double recip(double a) { return recip_int(a); }
@@ -240,6 +269,13 @@ struct Real<float> {
     }
     static __device__ __forceinline__ float interface(const CaseParams &c, int m, uint32_t hi, uint32_t lo) {
         return -c.lambda_f[m] * __logf(one_minus(hi, lo));
+    }
+    static __device__ __forceinline__ float inv_sigma(const CaseParams &c, int m) { return c.inv_sigma_f[m]; }
+    static __device__ __forceinline__ float lambda(const CaseParams &c, int m) { return c.lambda_f[m]; }
+    static __device__ __forceinline__ void exp_variates(uint32_t hi0, uint32_t lo0, uint32_t hi1, uint32_t lo1, float *e0,
+                                                        float *e1) {
+        *e0 = -__logf(one_minus(hi0, lo0));
+        *e1 = -__logf(one_minus(hi1, lo1));
     }
     static __device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
     static __device__ __forceinline__ void sincos_2pi(uint32_t hi, uint32_t lo, float *s, float *co) {
@@ -357,9 +393,24 @@ __device__ __forceinline__ void set_direction(History<P> &s, P wx, P wy, P wz) {
     s.w[0] = wx;
     s.w[1] = wy;
     s.w[2] = wz;
-    s.iw[0] = R::is_zero(wx) ? R::inf() : R::recip(wx);
-    s.iw[1] = R::is_zero(wy) ? R::inf() : R::recip(wy);
-    s.iw[2] = R::is_zero(wz) ? R::inf() : R::recip(wz);
+    if constexpr (sizeof(P) == 8) {  // one copy of the integer reciprocal, three passes
+        P a = wx, b = wy, c = wz, r0 = P(0), r1 = P(0), r2 = P(0);
+#pragma unroll 1
+        for (int t = 0; t < 3; ++t) {
+            r0 = r1;
+            r1 = r2;
+            r2 = R::is_zero(a) ? R::inf() : R::recip(a);
+            a = b;
+            b = c;
+        }
+        s.iw[0] = r0;
+        s.iw[1] = r1;
+        s.iw[2] = r2;
+    } else {
+        s.iw[0] = R::is_zero(wx) ? R::inf() : R::recip(wx);
+        s.iw[1] = R::is_zero(wy) ? R::inf() : R::recip(wy);
+        s.iw[2] = R::is_zero(wz) ? R::inf() : R::recip(wz);
+    }
 }
 
 // Direction (wx, 0, 0) of the slab and the x-projected box: no reciprocal of
@@ -574,8 +625,10 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
         l_i = R::interface(cp, m, ihi, ilo);
     } else {
         draw_pair(s, key, hi, lo, ihi, ilo);
-        l_c = R::pos(R::sigma(cp, m)) ? R::nonneg(R::collision(cp, m, hi, lo)) : INF;
-        l_i = R::interface(cp, m, ihi, ilo);
+        P e_c, e_i;
+        R::exp_variates(hi, lo, ihi, ilo, &e_c, &e_i);
+        l_c = R::pos(R::sigma(cp, m)) ? R::nonneg(e_c * R::inv_sigma(cp, m)) : INF;
+        l_i = R::lambda(cp, m) * e_i;
     }
     if (gd == 11) l_i *= R::abs(s.iw[0]);  // slab: the chord projected on x, Lambda/|mu|
     else if (gd == 2) l_i /= sqrt(P(1) - s.w[2] * s.w[2]);  // extruded: in-plane chord along the flight
@@ -838,19 +891,21 @@ __device__ __forceinline__ int find_run(const LaunchArgs &a, uint64_t ch) {
 // older region is flushed and re-keyed, and its remaining histories score
 // straight into the FP64 global tallies: the warp never waits for a straggler
 // of a heavy-tailed history-length distribution.
-// Blocks per SM the register allocation must allow: FP64 is bound by the FP64
-// pipe, FP32 by issue and latency, which more resident warps help hide.
+// Launch bounds: FP32 blocks of 256 threads, 4 per SM (64 registers); FP64
+// blocks of at most kHistoryBlockFp64 = 128 threads, 5 per SM (102 registers,
+// 20 warps: the FP64 walk is latency-bound, and more resident warps hide its
+// integer-arithmetic and shared-memory latencies).
 template <typename P>
-struct MinBlocks {
-    static constexpr int value = 2;
+struct HistoryBounds {
+    static constexpr int threads = kHistoryBlockFp64, blocks = 5;
 };
 template <>
-struct MinBlocks<float> {
-    static constexpr int value = 4;
+struct HistoryBounds<float> {
+    static constexpr int threads = 256, blocks = 4;
 };
 
 template <typename P, int G>
-__global__ void __launch_bounds__(256, MinBlocks<P>::value) history_kernel(const LaunchArgs a) {
+__global__ void __launch_bounds__(HistoryBounds<P>::threads, HistoryBounds<P>::blocks) history_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;

@@ -332,7 +332,8 @@ int tracker_shape(cls_handle *h, int region_bytes, Shape *out) {
     const size_t per_warp = 2 * (size_t)region_bytes;
     const int fit_warps = (int)std::min<size_t>(kMaxSmemPerBlock / per_warp, 8);
     if (fit_warps < 1) return CLS_E_INVAL;
-    const int block = 32 * std::min(h->opt.block / 32, fit_warps);
+    const int cap_warps = (!event && fp64) ? kHistoryBlockFp64 / 32 : 8;  // the FP64 history tracker's bound
+    const int block = 32 * std::min(std::min(h->opt.block / 32, fit_warps), cap_warps);
     const size_t smem = (size_t)(block / 32) * per_warp;
     int bps = h->opt.blocks_per_sm;
     if (bps <= 0) {

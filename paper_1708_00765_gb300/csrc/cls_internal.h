@@ -126,6 +126,10 @@ __host__ __device__ inline int region_bytes(int bin_size, int nbins_stride) {
 }
 
 // ceil(v 2^bits) for v in [0, 1], exact (scaling by a power of two is exact).
+// Largest block of the FP64 history tracker (its launch bounds allow 5 such
+// blocks per SM; the host caps the block option at this size for it).
+constexpr int kHistoryBlockFp64 = 128;
+
 inline unsigned long long unit_threshold(double v, int bits) {
     const double scaled = v * (double)(1ull << bits);
     const double c = (scaled == (double)(unsigned long long)scaled) ? scaled : (double)(unsigned long long)scaled + 1.0;

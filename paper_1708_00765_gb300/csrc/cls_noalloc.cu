@@ -167,7 +167,7 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
 
     const size_t per_warp = 2 * (size_t)a.region_bytes;
     int warps = (int)((200 * 1024) / per_warp);
-    warps = warps > 8 ? 8 : warps;
+    warps = warps > kHistoryBlockFp64 / 32 ? kHistoryBlockFp64 / 32 : warps;
     if (warps < 1) return CLS_E_INVAL;
     const int block = 32 * warps;
     const size_t smem = (size_t)warps * per_warp;
