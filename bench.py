@@ -31,22 +31,24 @@ sys.path.insert(0, ROOT)
 METRIC = "histories/s and FOM 1/(sigma^2 T) at equal sigma, FP32-batched vs FP64-plain on 1 GB300"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# Algorithmic work per event of the benchmark workload's kernels, fixed numbers
-# (profiles/history_kernel_box_L10.md):
-# * FP64: 148.8 flop per event, the FP64 arithmetic of one event of Algorithm A
-#   evaluated directly in FP64 with FP64 elementary functions (ln, sin/cos,
-#   division), counted as DADD + DMUL + 2 DFMA thread instructions by ncu on
-#   that direct evaluation.  The current kernel evaluates ln and sin/cos in the
-#   integer pipes and executes about 29 FP64 operations per event, so this is
-#   the work in FP64-equivalent flops; the same event done with fewer FP64
-#   operations raises the fraction.
-# * FP32: 40.4 warp instructions per event of history_kernel<float>.
+# Work per event of the benchmark workload's kernels, for the issue-rate
+# roofline (152 SMs x 4 warp instructions per clock): warp instructions per
+# event counted by ncu (smsp__inst_executed.sum / events) on a 2e6-history
+# launch of the current kernels (profiles/history_kernel_box_L10.md), kept fixed
+# here so that the fraction moves with the speed.
+# FP64_FLOP_PER_EVENT: the same event's FP64 arithmetic evaluated directly in
+# FP64 with FP64 elementary functions (ln, sin/cos, division, sqrt), counted by
+# ncu (DADD + DMUL + 2 DFMA) on that direct evaluation; reported beside the
+# roofline as FP64-equivalent TFLOP/s for context.  The kernel evaluates the
+# elementary functions in the integer pipes and is bound by issue and latency,
+# not by the FP64 pipe.
+FP64_WARP_INST_PER_EVENT = 97.8
+FP32_WARP_INST_PER_EVENT = 36.8
 FP64_FLOP_PER_EVENT = 148.8
-FP32_WARP_INST_PER_EVENT = 40.4
 # DRAM bytes per full-size FP64 launch (1e8 histories) from a one-pass ncu
 # capture of the current kernel (profiles/history_kernel_box_L10.md); None
 # whenever the kernel has changed since the capture.
-FP64_DRAM_BYTES_PER_LAUNCH = 963072
+FP64_DRAM_BYTES_PER_LAUNCH = None
 SM_COUNT = 152           # GB300
 DFMA_PER_SM_CLK = 2      # ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / 152 SMs
 ISSUE_PER_SM_CLK = 4     # one warp instruction per scheduler per clock, 4 schedulers
@@ -509,13 +511,16 @@ def main():
     clk_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     if "fp64" in results:
         r = results["fp64"]
-        achieved = FP64_FLOP_PER_EVENT * r["events_per_launch"] / (r["launch_ms"] * 1e-3) / 1e12
-        peak = SM_COUNT * DFMA_PER_SM_CLK * 2 * clk_mhz * 1e6 / 1e12
-        r["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        ev_s = r["events_per_launch"] / (r["launch_ms"] * 1e-3)
+        achieved = FP64_WARP_INST_PER_EVENT * ev_s / 1e12
+        peak = SM_COUNT * ISSUE_PER_SM_CLK * clk_mhz * 1e6 / 1e12
+        r["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
                          "frac": achieved / peak, "traffic": FP64_DRAM_BYTES_PER_LAUNCH,
                          "kernel": "history_kernel<double>",
-                         "work": f"{FP64_FLOP_PER_EVENT} FP64-equivalent flop/event x {r['events_per_launch']:.4g} events/launch",
-                         "peak_from": f"{SM_COUNT} SM x {DFMA_PER_SM_CLK} DFMA/clk x 2 flop x {clk_mhz} MHz (sampled)"}
+                         "work": f"{FP64_WARP_INST_PER_EVENT} warp instructions/event x {r['events_per_launch']:.4g} events/launch",
+                         "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} issue/clk x {clk_mhz} MHz (sampled)",
+                         "fp64_equivalent_tflops": FP64_FLOP_PER_EVENT * ev_s / 1e12,
+                         "fp64_peak_tflops": SM_COUNT * DFMA_PER_SM_CLK * 2 * clk_mhz * 1e6 / 1e12}
     if "fp32" in results:
         r = results["fp32"]
         achieved = FP32_WARP_INST_PER_EVENT * r["events_per_launch"] / (r["launch_ms"] * 1e-3) / 1e12

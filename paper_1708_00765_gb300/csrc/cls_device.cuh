@@ -25,6 +25,16 @@ namespace cls {
 
 #define CLS_FULL_MASK 0xffffffffu
 
+// Blocks per SM of a kernel at a given dynamic shared memory.  The opt-in for
+// more than 48 KB is set first: without it the occupancy query reports zero
+// blocks for such sizes.
+template <typename K>
+__host__ cudaError_t occupancy_with_smem(int *blocks_per_sm, K kernel, int block, size_t smem) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, block, smem);
+}
+
 // ------------------------------------------------- FP64 logarithm, sine/cosine
 // The FP64 walk takes its logarithms and its sine/cosine pairs straight from
 // the 53-bit integer k of a draw (u = k 2^-53), in integer arithmetic
@@ -723,6 +733,12 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
 // ------------------------------------------------------- tally regions
 // A warp-private shared-memory region (layout: region_bytes() in
 // cls_internal.h): bins of Real<P>::Bin, FP64 statistics, u64 counters.
+// the FP64 difference array of an FP32 region's interior-bin deposits
+template <typename P>
+__device__ __forceinline__ double *region_dif(unsigned char *region, int nbs) {
+    return reinterpret_cast<double *>(region + region_dif_offset((int)sizeof(typename Real<P>::Bin), nbs));
+}
+
 template <typename P>
 __device__ __forceinline__ double *region_stats(unsigned char *region, int nbs) {
     return reinterpret_cast<double *>(region + region_bins_bytes((int)sizeof(typename Real<P>::Bin), nbs));
@@ -748,30 +764,43 @@ __device__ __forceinline__ void finish_history(unsigned char *region, int nbs, c
     atomicMax(&ct[C_MAXEV], (unsigned long long)s.events);
 }
 
-// Score the warp's flights.  Each lane adds its two end bins; the interior
-// bins of all lanes' flights are then spread evenly over the 32 lanes (warp
-// prefix sum of the interior counts, and a 5-step shuffle search for the lane
-// that owns each interior bin), so long flights do not serialise the warp.
+// Score the warp's flights.  Each lane adds its two end bins.  Interior bins
+// (c each, k0 < k < k1): in an FP32 region with a difference array (DIF), two
+// entries of that FP64 array (c at k0 + 1, -c at k1), whose prefix sum the
+// flush adds;
+// otherwise the interior bins of all lanes' flights are spread evenly over the
+// 32 lanes (warp prefix sum of the interior counts, and a 5-step shuffle
+// search for the lane that owns each interior bin), so long flights do not
+// serialise the warp.  FP64 regions score each interior bin exactly: a
+// difference array's prefix sums would cancel between near and far bins.
 // A lane with lreg == 2 scores straight into the FP64 global bins at
 // gflux + goff, those of its (case, batch) (see the region eviction in the
 // trackers).
-template <typename P>
-__device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes, int lreg, double *gflux,
+template <typename P, bool DIF = false>
+__device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes, int nbs, int lreg, double *gflux,
                                              uint32_t goff, const Flight<P> &f, int lane) {
     using B = typename Real<P>::Bin;
+    constexpr bool kDif = sizeof(B) == 4 && DIF;
     const bool has = f.k1 >= f.k0;
     if (has) {
         if (lreg < 2) {
             B *bins = reinterpret_cast<B *>(regions + lreg * rbytes);
             atomicAdd(&bins[f.k0], (B)f.a0);
             if (f.k1 > f.k0) atomicAdd(&bins[f.k1], (B)f.a1);
+            if constexpr (kDif) {
+                if (f.k1 > f.k0 + 1) {
+                    double *dif = region_dif<P>(regions + lreg * rbytes, nbs);
+                    atomicAdd(&dif[f.k0 + 1], (double)f.c);
+                    atomicAdd(&dif[f.k1], -(double)f.c);
+                }
+            }
         } else {
             double *gbins = gflux + goff;
             atomicAdd(&gbins[f.k0], (double)f.a0);
             if (f.k1 > f.k0) atomicAdd(&gbins[f.k1], (double)f.a1);
         }
     }
-    const int ni = has ? max(f.k1 - f.k0 - 1, 0) : 0;
+    const int ni = (has && !(kDif && lreg < 2)) ? max(f.k1 - f.k0 - 1, 0) : 0;
     int incl = ni;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -833,7 +862,7 @@ __device__ __forceinline__ void finish_history_global(const LaunchArgs &a, int c
 
 // Flush a warp region into the global tally block of (case, batch): one global
 // FP64 atomic per non-zero bin, statistic and counter; the region is zeroed.
-template <typename P>
+template <typename P, bool DIF = false>
 __device__ __forceinline__ void flush_region(unsigned char *region, const LaunchArgs &a, int case_index,
                                              uint32_t batch, int lane) {
     using B = typename Real<P>::Bin;
@@ -841,11 +870,34 @@ __device__ __forceinline__ void flush_region(unsigned char *region, const Launch
     const int nb = a.cases[case_index].nbins;
     B *bins = reinterpret_cast<B *>(region);
     double *g = a.t.flux + ((size_t)case_index * a.t.nbatch + batch) * (size_t)nbs;
-    for (int k = lane; k < nb; k += 32) {
-        const B v = bins[k];
-        if (v != B(0)) {
-            atomicAdd(&g[k], (double)v);
-            bins[k] = B(0);
+    if constexpr (DIF && sizeof(B) == 4) {
+        // bins plus the prefix sum of the interior-bin difference array, 32 bins at a time
+        double *dif = region_dif<P>(region, nbs);
+        double carry = 0.0;
+        for (int base = 0; base < nb; base += 32) {
+            const int k = base + lane;
+            double d = (k < nb) ? dif[k] : 0.0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double v = __shfl_up_sync(CLS_FULL_MASK, d, o);
+                if (lane >= o) d += v;
+            }
+            const double interior = carry + d;
+            carry += __shfl_sync(CLS_FULL_MASK, d, 31);
+            if (k < nb) {
+                const double v = (double)bins[k] + interior;
+                if (__double_as_longlong(v) != 0) atomicAdd(&g[k], v);
+                bins[k] = B(0);
+                dif[k] = 0.0;
+            }
+        }
+    } else {
+        for (int k = lane; k < nb; k += 32) {
+            const B v = bins[k];
+            if (v != B(0)) {
+                atomicAdd(&g[k], (double)v);
+                bins[k] = B(0);
+            }
         }
     }
     double *st = region_stats<P>(region, nbs);
@@ -904,7 +956,7 @@ struct HistoryBounds<float> {
     static constexpr int threads = 256, blocks = 4;
 };
 
-template <typename P, int G>
+template <typename P, int G, bool DIF = false>
 __global__ void __launch_bounds__(HistoryBounds<P>::threads, HistoryBounds<P>::blocks) history_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -964,7 +1016,7 @@ __global__ void __launch_bounds__(HistoryBounds<P>::threads, HistoryBounds<P>::b
                     const int old_run = r ? key_run1 : key_run0;
                     const uint32_t old_batch = r ? key_batch1 : key_batch0;
                     if (old_run >= 0) {
-                        flush_region<P>(regions + r * rb, a, a.runs[old_run].case_index, old_batch, lane);
+                        flush_region<P, DIF>(regions + r * rb, a, a.runs[old_run].case_index, old_batch, lane);
                         // lanes still walking a history of the old key go on in global memory
                         if (alive && lreg == r) lreg = 2;
                     }
@@ -1010,7 +1062,7 @@ __global__ void __launch_bounds__(HistoryBounds<P>::threads, HistoryBounds<P>::b
             out = step<P, false, G, true>(s, a.cases[lcase], key, a.max_events, f, nullptr);
         }
         const uint32_t goff = (lreg == 2) ? ((uint32_t)lcase * (uint32_t)a.t.nbatch + lbatch) * (uint32_t)a.t.nbins_stride : 0u;
-        warp_deposit<P>(regions, rb, lreg, a.t.flux, goff, f, lane);
+        warp_deposit<P, DIF>(regions, rb, a.t.nbins_stride, lreg, a.t.flux, goff, f, lane);
         if (out >= 0) {
             if (lreg < 2) finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, out);
             else finish_history_global<P>(a, lcase, s, out, true);
@@ -1019,19 +1071,19 @@ __global__ void __launch_bounds__(HistoryBounds<P>::threads, HistoryBounds<P>::b
         if (a.flush_every) {
             if (fed0 >= a.flush_every) {
                 __syncwarp();
-                flush_region<P>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
+                flush_region<P, DIF>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
                 fed0 = 0;
             }
             if (fed1 >= a.flush_every) {
                 __syncwarp();
-                flush_region<P>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
+                flush_region<P, DIF>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
                 fed1 = 0;
             }
         }
     }
     __syncwarp();
-    if (key_run0 >= 0) flush_region<P>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
-    if (key_run1 >= 0) flush_region<P>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
+    if (key_run0 >= 0) flush_region<P, DIF>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
+    if (key_run1 >= 0) flush_region<P, DIF>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
 }
 
 // ------------------------------------------------------------ trace kernel

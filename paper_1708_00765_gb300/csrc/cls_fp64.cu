@@ -41,12 +41,12 @@ cudaError_t launch_trace_fp64(const TraceArgs &a, cudaStream_t s) {
 
 cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm, int geom) {
     switch (geom) {
-    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 1>, block, smem);
-    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 2>, block, smem);
-    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 3>, block, smem);
-    case 11: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 11>, block, smem);
-    case 13: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 13>, block, smem);
-    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, history_kernel<double, 0>, block, smem);
+    case 1: return occupancy_with_smem(blocks_per_sm, history_kernel<double, 1>, block, smem);
+    case 2: return occupancy_with_smem(blocks_per_sm, history_kernel<double, 2>, block, smem);
+    case 3: return occupancy_with_smem(blocks_per_sm, history_kernel<double, 3>, block, smem);
+    case 11: return occupancy_with_smem(blocks_per_sm, history_kernel<double, 11>, block, smem);
+    case 13: return occupancy_with_smem(blocks_per_sm, history_kernel<double, 13>, block, smem);
+    default: return occupancy_with_smem(blocks_per_sm, history_kernel<double, 0>, block, smem);
     }
 }
 
@@ -55,7 +55,7 @@ int event_bank_fields(int precision) {
 }
 
 cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm, int geom) {
-    return occupancy_event_impl<double>(block, smem, blocks_per_sm, geom);
+    return occupancy_event_impl<double>(block, smem, blocks_per_sm, geom, false);
 }
 
 }  // namespace cls

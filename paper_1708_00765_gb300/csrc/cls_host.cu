@@ -266,14 +266,18 @@ uint64_t batch_len_for(uint64_t n, int nbatch) {
     return (uint64_t)kBatchQuantum * std::max<uint64_t>(1, (n + q - 1) / q);
 }
 
+bool region_dif_for(const cls_handle *h) {
+    return h->opt.precision == CLS_PREC_FP32 && fp32_region_dif(h->nbins_stride);
+}
+
 int region_bytes_for(const cls_handle *h) {
     const int bin = (h->opt.precision == CLS_PREC_FP64) ? 8 : 4;
-    return region_bytes(bin, h->nbins_stride);
+    return region_bytes(bin, h->nbins_stride, region_dif_for(h));
 }
 
 // FP32 tally bins are flushed into the FP64 global tallies after this many
 // histories per region, which bounds the FP32 partial sums.
-constexpr int kFp32FlushHistories = 256;
+constexpr int kFp32FlushHistories = 1024;
 
 // Fill the pinned work list for n histories per case and describe the launch.
 int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, LaunchArgs *a) {
@@ -304,6 +308,7 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, LaunchArgs *a) {
     a->rk = make_round_keys(seed);
     a->max_events = h->opt.max_events;
     a->region_bytes = region_bytes_for(h);
+    a->dif = region_dif_for(h) ? 1 : 0;
     a->flush_every = (h->opt.precision == CLS_PREC_FP32) ? kFp32FlushHistories : 0;
     return CLS_OK;
 }
@@ -338,9 +343,10 @@ int tracker_shape(cls_handle *h, int region_bytes, Shape *out) {
     int bps = h->opt.blocks_per_sm;
     if (bps <= 0) {
         const int g = h->geom;
-        cudaError_t e = event ? (fp64 ? occupancy_event_fp64(block, smem, &bps, g) : occupancy_event_fp32(block, smem, &bps, g))
+        const bool dif = region_dif_for(h);
+        cudaError_t e = event ? (fp64 ? occupancy_event_fp64(block, smem, &bps, g) : occupancy_event_fp32(block, smem, &bps, g, dif))
                               : (fp64 ? occupancy_history_fp64(block, smem, &bps, g)
-                                      : occupancy_history_fp32(block, smem, &bps, g));
+                                      : occupancy_history_fp32(block, smem, &bps, g, dif));
         if (e != cudaSuccess) return CLS_E_CUDA;
         if (bps < 1) return CLS_E_INVAL;  // the block does not fit on an SM
     }

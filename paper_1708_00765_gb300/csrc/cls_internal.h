@@ -99,6 +99,7 @@ struct LaunchArgs {
     uint32_t max_events;
     int region_bytes;     // bytes per warp tally region (see region_bytes())
     int flush_every;      // flush a region after this many histories were fed into it (0: never)
+    int dif;              // FP32 regions carry the difference array of interior-bin deposits
     // event schedule only
     void *bank;            // grid warps x 2 buffers x bank_slots particles (SoA)
     uint32_t bank_slots;   // particles per warp and buffer, a multiple of 32
@@ -121,15 +122,26 @@ struct TraceArgs {
 // for the FP64 walk, FP32 for FP32 tracking), padded to 8 bytes, then S_NUM
 // FP64 statistics and C_NUM u64 counters; padded to 16 bytes.
 __host__ __device__ inline int region_bins_bytes(int bin_size, int nbins_stride) { return (nbins_stride * bin_size + 7) & ~7; }
-__host__ __device__ inline int region_bytes(int bin_size, int nbins_stride) {
-    return (region_bins_bytes(bin_size, nbins_stride) + 8 * (S_NUM + C_NUM) + 15) & ~15;
+// An FP32 region may add an FP64 difference array of the interior-bin
+// deposits after the statistics and counters: a flight adds c at its first
+// interior bin and -c after its last, and the flush takes the prefix sum.
+__host__ __device__ inline int region_dif_offset(int bin_size, int nbins_stride) {
+    return region_bins_bytes(bin_size, nbins_stride) + 8 * (S_NUM + C_NUM);
+}
+__host__ __device__ inline int region_bytes(int bin_size, int nbins_stride, bool dif = false) {
+    return (region_dif_offset(bin_size, nbins_stride) + (dif ? 8 * nbins_stride : 0) + 15) & ~15;
+}
+// FP32 regions carry the difference array while 64 of them (32 warps of two)
+// still fit an SM's shared memory, so that it costs no occupancy.
+__host__ __device__ inline bool fp32_region_dif(int nbins_stride) {
+    return 64 * region_bytes(4, nbins_stride, true) <= 227 * 1024;
 }
 
-// ceil(v 2^bits) for v in [0, 1], exact (scaling by a power of two is exact).
 // Largest block of the FP64 history tracker (its launch bounds allow 5 such
 // blocks per SM; the host caps the block option at this size for it).
 constexpr int kHistoryBlockFp64 = 128;
 
+// ceil(v 2^bits) for v in [0, 1], exact (scaling by a power of two is exact).
 inline unsigned long long unit_threshold(double v, int bits) {
     const double scaled = v * (double)(1ull << bits);
     const double c = (scaled == (double)(unsigned long long)scaled) ? scaled : (double)(unsigned long long)scaled + 1.0;
@@ -145,9 +157,9 @@ cudaError_t launch_event_fp32(const LaunchArgs &a, int grid, int block, size_t s
 cudaError_t launch_trace_fp64(const TraceArgs &a, cudaStream_t s);
 cudaError_t launch_trace_fp32(const TraceArgs &a, cudaStream_t s);
 cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm, int geom);
-cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm, int geom);
+cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm, int geom, bool dif);
 cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm, int geom);
-cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm, int geom);
+cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm, int geom, bool dif);
 int event_bank_fields(int precision); // 16-byte SoA fields per particle (0 = FP64)
 
 }  // namespace cls

@@ -260,6 +260,20 @@ def test_fp32_statistically_equal(params, kind):
     assert same / 200 > 0.8
 
 
+@pytest.mark.parametrize("schedule", ["history", "event"])
+@pytest.mark.parametrize("nbins", [7, 200, 2000])
+def test_fp32_flux_bins_add_up_to_the_track(schedule, nbins):
+    """FP32 tallies: the bins -- FP32 end-bin partials plus the prefix-summed FP64
+    difference array of the interior bins -- add up to the histories' total track
+    length, also on meshes whose tally regions need more than 48 KB of shared
+    memory per block."""
+    params = (1.0, 10.0, 0.5, 0.2, 0.99, 0.99, 10.0, 3, nbins)
+    _, t = gpu_raw(params, 20_000, 5, precision="fp32", schedule=schedule)
+    dx = params[6] / nbins
+    assert t["flux"].sum() * dx == pytest.approx(t["total_flux"], rel=1e-5)
+    assert t["nR"] + t["nT"] + t["nA"] == 20_000
+
+
 # ---------------------------------------------------------------- batches
 
 def test_batch_cases_match_oracle_exactly():
