@@ -48,7 +48,7 @@ FP64_FLOP_PER_EVENT = 148.8
 # DRAM bytes per full-size FP64 launch (1e8 histories) from a one-pass ncu
 # capture of the current kernel (profiles/history_kernel_box_L10.md); None
 # whenever the kernel has changed since the capture.
-FP64_DRAM_BYTES_PER_LAUNCH = None
+FP64_DRAM_BYTES_PER_LAUNCH = 829184
 SM_COUNT = 152           # GB300
 DFMA_PER_SM_CLK = 2      # ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / 152 SMs
 ISSUE_PER_SM_CLK = 4     # one warp instruction per scheduler per clock, 4 schedulers
