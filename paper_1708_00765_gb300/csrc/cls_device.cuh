@@ -945,19 +945,22 @@ __device__ __forceinline__ int find_run(const LaunchArgs &a, uint64_t ch) {
 // of a heavy-tailed history-length distribution.
 // Launch bounds: FP32 blocks of 256 threads, 4 per SM (64 registers); FP64
 // blocks of at most kHistoryBlockFp64 = 128 threads, 5 per SM (102 registers,
-// 20 warps: the FP64 walk is latency-bound, and more resident warps hide its
-// integer-arithmetic and shared-memory latencies).
-template <typename P>
+// 20 warps), 6 (85 registers, 24 warps) for the one-dimensional walks (rod,
+// slab, x-projected box), whose state fits: the FP64 walk is latency-bound,
+// and more resident warps hide its integer-arithmetic and shared-memory
+// latencies (measured: 5% faster for the x-projected box at 6, no gain for the
+// 3D box, which would spill).
+template <typename P, int G>
 struct HistoryBounds {
-    static constexpr int threads = kHistoryBlockFp64, blocks = 5;
+    static constexpr int threads = kHistoryBlockFp64, blocks = (G == 1 || G == 11 || G == 13) ? 6 : 5;
 };
-template <>
-struct HistoryBounds<float> {
+template <int G>
+struct HistoryBounds<float, G> {
     static constexpr int threads = 256, blocks = 4;
 };
 
 template <typename P, int G, bool DIF = false>
-__global__ void __launch_bounds__(HistoryBounds<P>::threads, HistoryBounds<P>::blocks) history_kernel(const LaunchArgs a) {
+__global__ void __launch_bounds__(HistoryBounds<P, G>::threads, HistoryBounds<P, G>::blocks) history_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
