@@ -244,11 +244,18 @@ struct Real<float> {
     // the same draw truncated to its top 24 bits: u = k 2^-24
     static __device__ __forceinline__ float uniform(uint32_t hi, uint32_t) { return (float)(hi >> 8) * 0x1p-24f; }
     static __device__ __forceinline__ float two_u_minus_one(uint32_t hi, uint32_t lo) { return 2.0f * uniform(hi, lo) - 1.0f; }
-    static __device__ __forceinline__ float sqrt_uniform(uint32_t hi, uint32_t lo) { return sqrtf(uniform(hi, lo)); }
+    // FP32 tracking takes the hardware's approximate square root, reciprocal and
+    // sine/cosine (a few FP32 ulps, below the FP32 walk's own rounding noise)
+    static __device__ __forceinline__ float fast_sqrt(float x) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ float sqrt_uniform(uint32_t hi, uint32_t lo) { return fast_sqrt(uniform(hi, lo)); }
     static __device__ __forceinline__ void direction_cosines(uint32_t hi, uint32_t lo, bool cosine, float *mu,
                                                             float *st) {
         *mu = cosine ? sqrt_uniform(hi, lo) : two_u_minus_one(hi, lo);
-        *st = sqrtf(1.0f - *mu * *mu);
+        *st = fast_sqrt(1.0f - *mu * *mu);
     }
     static __device__ __forceinline__ float one_minus(uint32_t hi, uint32_t) {
         return (float)((1u << 24) - (hi >> 8)) * 0x1p-24f;
@@ -287,9 +294,17 @@ struct Real<float> {
         *e0 = -__logf(one_minus(hi0, lo0));
         *e1 = -__logf(one_minus(hi1, lo1));
     }
-    static __device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
+    static __device__ __forceinline__ float recip(float a) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+        return r;
+    }
+    // (sin, cos)(2 pi u) = -(sin, cos)(2 pi (u - 1/2)), the argument in [-pi, pi)
     static __device__ __forceinline__ void sincos_2pi(uint32_t hi, uint32_t lo, float *s, float *co) {
-        sincospif(2.0f * uniform(hi, lo), s, co);
+        float sn, cs;
+        __sincosf(6.28318530717958647692f * (uniform(hi, lo) - 0.5f), &sn, &cs);
+        *s = -sn;
+        *co = -cs;
     }
 };
 
