@@ -34,8 +34,8 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # Work per event of the benchmark workload's kernels, for the issue-rate
 # roofline (152 SMs x 4 warp instructions per clock): warp instructions per
 # event counted by ncu (smsp__inst_executed.sum / events) on a 2e6-history
-# launch of the current kernels (profiles/history_kernel_box_L10.md), kept fixed
-# here so that the fraction moves with the speed.
+# launch of the current kernels (profiles/history_kernel_box_L10.md), updated
+# with each profile of a changed kernel.
 # FP64_FLOP_PER_EVENT: the same event's FP64 arithmetic evaluated directly in
 # FP64 with FP64 elementary functions (ln, sin/cos, division, sqrt), counted by
 # ncu (DADD + DMUL + 2 DFMA) on that direct evaluation; reported beside the
@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # elementary functions in the integer pipes and is bound by issue and latency,
 # not by the FP64 pipe.
 FP64_WARP_INST_PER_EVENT = 97.8
-FP32_WARP_INST_PER_EVENT = 36.8
+FP32_WARP_INST_PER_EVENT = 25.5
 FP64_FLOP_PER_EVENT = 148.8
 # DRAM bytes per full-size FP64 launch (1e8 histories) from a one-pass ncu
 # capture of the current kernel (profiles/history_kernel_box_L10.md); None
