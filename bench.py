@@ -263,14 +263,16 @@ def diffusive_workload(args, rank, world, pg):
 
 
 def batch_workload(args, rank, world, pg):
-    """256-case sweep: FP64 plain (one launch per case, no graph) vs FP32 batched
-    (all cases in one persistent launch replayed from a CUDA graph), equal N per case."""
+    """256-case sweep at 1e7 histories per case: FP64 plain (one launch per case, no
+    graph, default launch shape) vs FP32 and FP64 batched (all cases in one
+    persistent launch replayed from a CUDA graph, launch shape and schedule chosen
+    by the autotuner), equal N per case."""
     import torch
     import paper_1708_00765_gb300 as cls
     from paper_1708_00765_gb300 import workloads
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     cases = workloads.batch_sweep(256, seed=7, nbins=100)
-    n = args.histories or 1_000_000
+    n = args.histories or 10_000_000
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
@@ -294,9 +296,11 @@ def batch_workload(args, rank, world, pg):
         for p in plain:
             p.close()
         arms = {}
+        tuned = {}
         for prec in ("fp32", "fp64"):
             b = cls.Problem(cases, batch=True)
             b.set_option("precision", prec)
+            tuned[prec] = b.autotune(max(4096, min(n // 16, 262_144)), seed=3, stream=stream)
             dev = timed_runs(b, n, 1, args.steps, args.warmup, flush, torch, stream)
             arms[prec] = (max_over_ranks(pg, dev) / args.steps, [b.tallies(k) for k in range(len(cases))])
             b.close()
@@ -320,8 +324,10 @@ def batch_workload(args, rank, world, pg):
             "config": {"workload": "batched sweep, 256 cases (seed 7), 100 bins", "histories_per_case": n,
                        "l2": "flushed between steps"},
             "clocks": sampler.summary(),
-            "fp32_batched": {"histories_per_s": world * len(cases) * n / t32, "s_per_replay": t32},
-            "fp64_batched": {"histories_per_s": world * len(cases) * n / t64b, "s_per_replay": t64b},
+            "fp32_batched": {"histories_per_s": world * len(cases) * n / t32, "s_per_replay": t32,
+                             "autotuned": tuned["fp32"]},
+            "fp64_batched": {"histories_per_s": world * len(cases) * n / t64b, "s_per_replay": t64b,
+                             "autotuned": tuned["fp64"]},
             "fp64_plain": {"histories_per_s": world * len(cases) * n / t64, "s_total": t64,
                            "events_per_s": events64 / t64},
             "fom_ratio_fp32_batched_over_fp64_plain": {"median": ratios[len(ratios) // 2], "min": ratios[0],
