@@ -748,10 +748,24 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
 // ------------------------------------------------------- tally regions
 // A warp-private shared-memory region (layout: region_bytes() in
 // cls_internal.h): bins of Real<P>::Bin, FP64 statistics, u64 counters.
-// the FP64 difference array of an FP32 region's interior-bin deposits
+// The difference array of an FP32 region's interior-bin deposits: 64-bit
+// fixed point with 32 fraction bits, added with native integer atomics (no
+// retry loop when a warp's flights share an entry, as on thin slabs) and
+// prefix-summed exactly at the flush.
 template <typename P>
-__device__ __forceinline__ double *region_dif(unsigned char *region, int nbs) {
-    return reinterpret_cast<double *>(region + region_dif_offset((int)sizeof(typename Real<P>::Bin), nbs));
+__device__ __forceinline__ unsigned long long *region_dif(unsigned char *region, int nbs) {
+    return reinterpret_cast<unsigned long long *>(region + region_dif_offset((int)sizeof(typename Real<P>::Bin), nbs));
+}
+
+// round(c 2^32) for 0 <= c < 2^30, from the float's bit pattern (a float has
+// 24 significant bits, so c >= 2^-8 converts exactly)
+__device__ __forceinline__ unsigned long long fixed32(float c) {
+    const uint32_t b = __float_as_uint(c);
+    const int e = (int)(b >> 23) - 127;  // c = m 2^(e - 23)
+    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = e + 9;                // c 2^32 = m 2^(e + 9)
+    if (e < -126) return 0ull;          // zero and subnormal
+    return sh >= 0 ? (m << sh) : (sh > -40 ? ((m >> (-sh - 1)) + 1ull) >> 1 : 0ull);
 }
 
 template <typename P>
@@ -781,8 +795,8 @@ __device__ __forceinline__ void finish_history(unsigned char *region, int nbs, c
 
 // Score the warp's flights.  Each lane adds its two end bins.  Interior bins
 // (c each, k0 < k < k1): in an FP32 region with a difference array (DIF), two
-// entries of that FP64 array (c at k0 + 1, -c at k1), whose prefix sum the
-// flush adds;
+// entries of that fixed-point array (c at k0 + 1, -c at k1), whose prefix sum
+// the flush adds;
 // otherwise the interior bins of all lanes' flights are spread evenly over the
 // 32 lanes (warp prefix sum of the interior counts, and a 5-step shuffle
 // search for the lane that owns each interior bin), so long flights do not
@@ -804,9 +818,10 @@ __device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes,
             if (f.k1 > f.k0) atomicAdd(&bins[f.k1], (B)f.a1);
             if constexpr (kDif) {
                 if (f.k1 > f.k0 + 1) {
-                    double *dif = region_dif<P>(regions + lreg * rbytes, nbs);
-                    atomicAdd(&dif[f.k0 + 1], (double)f.c);
-                    atomicAdd(&dif[f.k1], -(double)f.c);
+                    unsigned long long *dif = region_dif<P>(regions + lreg * rbytes, nbs);
+                    const unsigned long long q = fixed32((float)f.c);
+                    atomicAdd(&dif[f.k0 + 1], q);
+                    atomicAdd(&dif[f.k1], 0ull - q);  // modulo 2^64: exact
                 }
             }
         } else {
@@ -886,24 +901,24 @@ __device__ __forceinline__ void flush_region(unsigned char *region, const Launch
     B *bins = reinterpret_cast<B *>(region);
     double *g = a.t.flux + ((size_t)case_index * a.t.nbatch + batch) * (size_t)nbs;
     if constexpr (DIF && sizeof(B) == 4) {
-        // bins plus the prefix sum of the interior-bin difference array, 32 bins at a time
-        double *dif = region_dif<P>(region, nbs);
-        double carry = 0.0;
+        // bins plus the exact prefix sum of the fixed-point difference array, 32 bins at a time
+        unsigned long long *dif = region_dif<P>(region, nbs);
+        unsigned long long carry = 0ull;
         for (int base = 0; base < nb; base += 32) {
             const int k = base + lane;
-            double d = (k < nb) ? dif[k] : 0.0;
+            unsigned long long d = (k < nb) ? dif[k] : 0ull;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const double v = __shfl_up_sync(CLS_FULL_MASK, d, o);
+                const unsigned long long v = __shfl_up_sync(CLS_FULL_MASK, d, o);
                 if (lane >= o) d += v;
             }
-            const double interior = carry + d;
+            const long long interior = (long long)(carry + d);  // >= 0 up to rounding of the last bit
             carry += __shfl_sync(CLS_FULL_MASK, d, 31);
             if (k < nb) {
-                const double v = (double)bins[k] + interior;
+                const double v = (double)bins[k] + (double)interior * 0x1p-32;
                 if (__double_as_longlong(v) != 0) atomicAdd(&g[k], v);
                 bins[k] = B(0);
-                dif[k] = 0.0;
+                dif[k] = 0ull;
             }
         }
     } else {

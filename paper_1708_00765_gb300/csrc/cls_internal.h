@@ -122,9 +122,10 @@ struct TraceArgs {
 // for the FP64 walk, FP32 for FP32 tracking), padded to 8 bytes, then S_NUM
 // FP64 statistics and C_NUM u64 counters; padded to 16 bytes.
 __host__ __device__ inline int region_bins_bytes(int bin_size, int nbins_stride) { return (nbins_stride * bin_size + 7) & ~7; }
-// An FP32 region may add an FP64 difference array of the interior-bin
-// deposits after the statistics and counters: a flight adds c at its first
-// interior bin and -c after its last, and the flush takes the prefix sum.
+// An FP32 region may add a difference array of the interior-bin deposits
+// (64-bit fixed point) after the statistics and counters: a flight adds c at
+// its first interior bin and -c after its last, and the flush takes the
+// prefix sum.
 __host__ __device__ inline int region_dif_offset(int bin_size, int nbins_stride) {
     return region_bins_bytes(bin_size, nbins_stride) + 8 * (S_NUM + C_NUM);
 }
