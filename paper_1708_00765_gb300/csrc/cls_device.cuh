@@ -769,21 +769,30 @@ __device__ __forceinline__ unsigned long long fixed32(float c) {
 }
 
 template <typename P>
+__device__ __forceinline__ typename Real<P>::Bin *region_lane_stats(unsigned char *region, int nbs) {
+    using B = typename Real<P>::Bin;
+    return reinterpret_cast<B *>(region + region_lane_stats_offset((int)sizeof(B), nbs));
+}
+
+template <typename P>
 __device__ __forceinline__ double *region_stats(unsigned char *region, int nbs) {
     return reinterpret_cast<double *>(region + region_bins_bytes((int)sizeof(typename Real<P>::Bin), nbs));
 }
 
 template <typename P>
-__device__ __forceinline__ void finish_history(unsigned char *region, int nbs, const History<P> &s, int outcome) {
+__device__ __forceinline__ void finish_history(unsigned char *region, int nbs, const History<P> &s, int outcome,
+                                               int lane) {
     double *st = region_stats<P>(region, nbs);
     unsigned long long *ct = reinterpret_cast<unsigned long long *>(st + S_NUM);
     const double t0 = (double)s.track0;
     const double t1 = (double)s.track1;
     const double t = t0 + t1;
-    atomicAdd(&st[S_T], t);
-    atomicAdd(&st[S_T2], t * t);
-    if (__double_as_longlong(t0) != 0) atomicAdd(&st[S_TRACK0], t0);
-    if (__double_as_longlong(t1) != 0) atomicAdd(&st[S_TRACK1], t1);
+    using B = typename Real<P>::Bin;
+    B *ls = region_lane_stats<P>(region, nbs) + lane;  // this lane's own copy: no atomics
+    ls[32 * S_T] += (B)t;
+    ls[32 * S_T2] += (B)(t * t);
+    ls[32 * S_TRACK0] += (B)t0;
+    ls[32 * S_TRACK1] += (B)t1;
     const int c = (outcome == EV_LEAK_X0) ? C_R : (outcome == EV_LEAK_XL) ? C_T : (outcome == EV_ABSORB) ? C_A : C_CAPPED;
     atomicAdd(&ct[c], 1ull);
     if (s.n_coll) atomicAdd(&ct[C_COLL], (unsigned long long)s.n_coll);
@@ -929,6 +938,16 @@ __device__ __forceinline__ void flush_region(unsigned char *region, const Launch
                 bins[k] = B(0);
             }
         }
+    }
+    // the lanes' own copies of the per-history statistics, summed over the warp
+    B *ls = region_lane_stats<P>(region, nbs);
+#pragma unroll
+    for (int q = 0; q < S_NUM; ++q) {
+        double v = (double)ls[32 * q + lane];
+        ls[32 * q + lane] = B(0);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(CLS_FULL_MASK, v, o);
+        if (lane == 0 && __double_as_longlong(v) != 0) atomicAdd(&a.t.stats[(size_t)case_index * S_NUM + q], v);
     }
     double *st = region_stats<P>(region, nbs);
     if (lane < S_NUM) {
@@ -1097,7 +1116,7 @@ __global__ void __launch_bounds__(HistoryBounds<P, G>::threads, HistoryBounds<P,
         const uint32_t goff = (lreg == 2) ? ((uint32_t)lcase * (uint32_t)a.t.nbatch + lbatch) * (uint32_t)a.t.nbins_stride : 0u;
         warp_deposit<P, DIF>(regions, rb, a.t.nbins_stride, lreg, a.t.flux, goff, f, lane);
         if (out >= 0) {
-            if (lreg < 2) finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, out);
+            if (lreg < 2) finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, out, lane);
             else finish_history_global<P>(a, lcase, s, out, true);
             alive = false;
         }

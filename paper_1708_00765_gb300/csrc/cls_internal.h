@@ -122,12 +122,18 @@ struct TraceArgs {
 // for the FP64 walk, FP32 for FP32 tracking), padded to 8 bytes, then S_NUM
 // FP64 statistics and C_NUM u64 counters; padded to 16 bytes.
 __host__ __device__ inline int region_bins_bytes(int bin_size, int nbins_stride) { return (nbins_stride * bin_size + 7) & ~7; }
-// An FP32 region may add a difference array of the interior-bin deposits
-// (64-bit fixed point) after the statistics and counters: a flight adds c at
-// its first interior bin and -c after its last, and the flush takes the
-// prefix sum.
-__host__ __device__ inline int region_dif_offset(int bin_size, int nbins_stride) {
+// After the statistics and counters, each lane's own copy of the per-history
+// statistics (S_NUM x 32 values of the bin type, statistic-major), which a
+// lane updates without atomics when its history ends; the flush sums them
+// over the warp in FP64.
+__host__ __device__ inline int region_lane_stats_offset(int bin_size, int nbins_stride) {
     return region_bins_bytes(bin_size, nbins_stride) + 8 * (S_NUM + C_NUM);
+}
+// An FP32 region may then add a difference array of the interior-bin deposits
+// (64-bit fixed point): a flight adds c at its first interior bin and -c after
+// its last, and the flush takes the prefix sum.
+__host__ __device__ inline int region_dif_offset(int bin_size, int nbins_stride) {
+    return (region_lane_stats_offset(bin_size, nbins_stride) + bin_size * 32 * S_NUM + 7) & ~7;
 }
 __host__ __device__ inline int region_bytes(int bin_size, int nbins_stride, bool dif = false) {
     return (region_dif_offset(bin_size, nbins_stride) + (dif ? 8 * nbins_stride : 0) + 15) & ~15;
