@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # elementary functions in the integer pipes and is bound by issue and latency,
 # not by the FP64 pipe.
 FP64_WARP_INST_PER_EVENT = 97.8
-FP32_WARP_INST_PER_EVENT = 25.5
+FP32_WARP_INST_PER_EVENT = 26.0
 FP64_FLOP_PER_EVENT = 148.8
 # DRAM bytes per full-size FP64 launch (1e8 histories) from a one-pass ncu
 # capture of the current kernel (profiles/history_kernel_box_L10.md); None
