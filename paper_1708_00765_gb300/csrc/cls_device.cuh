@@ -780,10 +780,7 @@ __device__ __forceinline__ double *region_stats(unsigned char *region, int nbs) 
 }
 
 template <typename P>
-__device__ __forceinline__ void finish_history(unsigned char *region, int nbs, const History<P> &s, int outcome,
-                                               int lane) {
-    double *st = region_stats<P>(region, nbs);
-    unsigned long long *ct = reinterpret_cast<unsigned long long *>(st + S_NUM);
+__device__ __forceinline__ void finish_history(unsigned char *region, int nbs, const History<P> &s, int lane) {
     const double t0 = (double)s.track0;
     const double t1 = (double)s.track1;
     const double t = t0 + t1;
@@ -793,13 +790,66 @@ __device__ __forceinline__ void finish_history(unsigned char *region, int nbs, c
     ls[32 * S_T2] += (B)(t * t);
     ls[32 * S_TRACK0] += (B)t0;
     ls[32 * S_TRACK1] += (B)t1;
+}
+
+// Outcome and event counters of the lanes whose history ended this step
+// (`ended`, scoring into region lreg < 2).  When several lanes ended they are
+// summed over the warp per region (ballot counts, warp reductions of 16-bit
+// halves) and one lane adds each to the region, else each lane adds its own:
+// short histories that end together do not serialise on shared atomics.
+__device__ __forceinline__ void count_one(unsigned long long *ct, int outcome, uint32_t n_coll, uint32_t n_int,
+                                          uint32_t n_refl, uint32_t events) {
     const int c = (outcome == EV_LEAK_X0) ? C_R : (outcome == EV_LEAK_XL) ? C_T : (outcome == EV_ABSORB) ? C_A : C_CAPPED;
     atomicAdd(&ct[c], 1ull);
-    if (s.n_coll) atomicAdd(&ct[C_COLL], (unsigned long long)s.n_coll);
-    if (s.n_int) atomicAdd(&ct[C_INT], (unsigned long long)s.n_int);
-    if (s.n_refl) atomicAdd(&ct[C_REFL], (unsigned long long)s.n_refl);
-    atomicAdd(&ct[C_EVENTS], (unsigned long long)s.events);
-    atomicMax(&ct[C_MAXEV], (unsigned long long)s.events);
+    if (n_coll) atomicAdd(&ct[C_COLL], (unsigned long long)n_coll);
+    if (n_int) atomicAdd(&ct[C_INT], (unsigned long long)n_int);
+    if (n_refl) atomicAdd(&ct[C_REFL], (unsigned long long)n_refl);
+    atomicAdd(&ct[C_EVENTS], (unsigned long long)events);
+    atomicMax(&ct[C_MAXEV], (unsigned long long)events);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum32(bool mine, uint32_t x) {
+    const uint32_t v = mine ? x : 0u;
+    return (unsigned long long)__reduce_add_sync(CLS_FULL_MASK, v & 0xFFFFu) +
+           ((unsigned long long)__reduce_add_sync(CLS_FULL_MASK, v >> 16) << 16);
+}
+
+template <typename P>
+__device__ __forceinline__ void warp_count(unsigned char *regions, int rbytes, int nbs, bool ended, int lreg,
+                                           const History<P> &s, int outcome, int lane) {
+    const unsigned em = __ballot_sync(CLS_FULL_MASK, ended);
+    if (em == 0u) return;
+    if (__popc(em) < 4) {
+        if (ended)
+            count_one(reinterpret_cast<unsigned long long *>(region_stats<P>(regions + lreg * rbytes, nbs) + S_NUM),
+                      outcome, s.n_coll, s.n_int, s.n_refl, s.events);
+        return;
+    }
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+        const bool mine = ended && lreg == r;
+        const unsigned m = __ballot_sync(CLS_FULL_MASK, mine);
+        if (m == 0u) continue;
+        const unsigned nr = __popc(__ballot_sync(CLS_FULL_MASK, mine && outcome == EV_LEAK_X0));
+        const unsigned nt = __popc(__ballot_sync(CLS_FULL_MASK, mine && outcome == EV_LEAK_XL));
+        const unsigned na = __popc(__ballot_sync(CLS_FULL_MASK, mine && outcome == EV_ABSORB));
+        const unsigned ncap = __popc(m) - nr - nt - na;
+        const unsigned long long nc = warp_sum32(mine, s.n_coll), ni = warp_sum32(mine, s.n_int);
+        const unsigned long long nf = warp_sum32(mine, s.n_refl), ne = warp_sum32(mine, s.events);
+        const unsigned mx = __reduce_max_sync(CLS_FULL_MASK, mine ? s.events : 0u);
+        if (lane == __ffs(m) - 1) {
+            unsigned long long *ct = reinterpret_cast<unsigned long long *>(region_stats<P>(regions + r * rbytes, nbs) + S_NUM);
+            if (nr) atomicAdd(&ct[C_R], (unsigned long long)nr);
+            if (nt) atomicAdd(&ct[C_T], (unsigned long long)nt);
+            if (na) atomicAdd(&ct[C_A], (unsigned long long)na);
+            if (ncap) atomicAdd(&ct[C_CAPPED], (unsigned long long)ncap);
+            if (nc) atomicAdd(&ct[C_COLL], nc);
+            if (ni) atomicAdd(&ct[C_INT], ni);
+            if (nf) atomicAdd(&ct[C_REFL], nf);
+            atomicAdd(&ct[C_EVENTS], ne);
+            atomicMax(&ct[C_MAXEV], (unsigned long long)mx);
+        }
+    }
 }
 
 // Score the warp's flights.  Each lane adds its two end bins.  Interior bins
@@ -1116,10 +1166,20 @@ __global__ void __launch_bounds__(HistoryBounds<P, G>::threads, HistoryBounds<P,
         const uint32_t goff = (lreg == 2) ? ((uint32_t)lcase * (uint32_t)a.t.nbatch + lbatch) * (uint32_t)a.t.nbins_stride : 0u;
         warp_deposit<P, DIF>(regions, rb, a.t.nbins_stride, lreg, a.t.flux, goff, f, lane);
         if (out >= 0) {
-            if (lreg < 2) finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, out, lane);
-            else finish_history_global<P>(a, lcase, s, out, true);
-            alive = false;
+            if (lreg < 2) {
+                finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, lane);
+                if constexpr (G != 0)
+                    count_one(reinterpret_cast<unsigned long long *>(region_stats<P>(regions + lreg * rb, a.t.nbins_stride) + S_NUM),
+                              out, s.n_coll, s.n_int, s.n_refl, s.events);
+            } else {
+                finish_history_global<P>(a, lcase, s, out, true);
+            }
         }
+        // the mixed-geometry kernel serves batch sweeps, whose short histories
+        // often end together: their counters are summed over the warp first
+        // (measured 10% faster there, 1-5% slower on the single-geometry walks)
+        if constexpr (G == 0) warp_count<P>(regions, rb, a.t.nbins_stride, out >= 0 && lreg < 2, lreg, s, out, lane);
+        if (out >= 0) alive = false;
         if (a.flush_every) {
             if (fed0 >= a.flush_every) {
                 __syncwarp();
