@@ -31,24 +31,27 @@ sys.path.insert(0, ROOT)
 METRIC = "histories/s and FOM 1/(sigma^2 T) at equal sigma, FP32-batched vs FP64-plain on 1 GB300"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# Work per event of the benchmark workload's kernels, for the issue-rate
+# Work per event of the benchmark workloads' kernels, for the issue-rate
 # roofline (152 SMs x 4 warp instructions per clock): warp instructions per
-# event counted by ncu (smsp__inst_executed.sum / events) on a 2e6-history
-# launch of the current kernels (profiles/history_kernel_box_L10.md), updated
-# with each profile of a changed kernel.
+# event counted by ncu (smsp__inst_executed.sum / events, one pass) on the
+# full-size launch of the current kernels (1e8 histories;
+# profiles/history_kernel_box_L10.md, profiles/event_kernel_diffusive.md),
+# updated with each capture of a changed kernel.  A small launch counts more
+# per event: its heavy-tailed last histories run in nearly empty warps.
 # FP64_FLOP_PER_EVENT: the same event's FP64 arithmetic evaluated directly in
 # FP64 with FP64 elementary functions (ln, sin/cos, division, sqrt), counted by
 # ncu (DADD + DMUL + 2 DFMA) on that direct evaluation; reported beside the
 # roofline as FP64-equivalent TFLOP/s for context.  The kernel evaluates the
 # elementary functions in the integer pipes and is bound by issue and latency,
 # not by the FP64 pipe.
-FP64_WARP_INST_PER_EVENT = 97.8
-FP32_WARP_INST_PER_EVENT = 26.0
+FP64_WARP_INST_PER_EVENT = 86.4
+FP32_WARP_INST_PER_EVENT = 21.1
 FP64_FLOP_PER_EVENT = 148.8
-# DRAM bytes per full-size FP64 launch (1e8 histories) from a one-pass ncu
-# capture of the current kernel (profiles/history_kernel_box_L10.md); None
+# The diffusive workload's FP32 kernels (500 bins: no difference array).
+DIFFUSIVE_WARP_INST_PER_EVENT = {"history": 20.1, "event": 20.5}
+# DRAM bytes of that full-size FP64 launch (the same one-pass capture); None
 # whenever the kernel has changed since the capture.
-FP64_DRAM_BYTES_PER_LAUNCH = 829184
+FP64_DRAM_BYTES_PER_LAUNCH = 774144
 SM_COUNT = 152           # GB300
 DFMA_PER_SM_CLK = 2      # ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / 152 SMs
 ISSUE_PER_SM_CLK = 4     # one warp instruction per scheduler per clock, 4 schedulers
@@ -117,6 +120,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self._summary = None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -138,6 +142,12 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        """Median SM clock under load and the throttle reasons seen; computed once."""
+        if self._summary is None:
+            self._summary = self._read()
+        return self._summary
+
+    def _read(self):
         if self.proc is None or not self.path or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
@@ -250,6 +260,15 @@ def diffusive_workload(args, rank, world, pg):
                           "max_events": tal["max_events"], "R": tal["R"], "total_flux": tal["total_flux"],
                           "fom_total_flux": 1.0 / (rel * rel * dev / world)}
             prob.close()
+    clk_mhz = sampler.summary().get("sm_mhz") or 2070.0
+    peak = SM_COUNT * ISSUE_PER_SM_CLK * clk_mhz * 1e6 / 1e12
+    for sched, r in out.items():
+        ev_s = r["events_per_s"] / world
+        achieved = DIFFUSIVE_WARP_INST_PER_EVENT[sched] * ev_s / 1e12
+        r["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
+                         "frac": achieved / peak, "kernel": f"{sched}_kernel<float, 3, 0>",
+                         "work": f"{DIFFUSIVE_WARP_INST_PER_EVENT[sched]} warp instructions/event",
+                         "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} issue/clk x {clk_mhz} MHz"}
     if rank == 0:
         h = out["history"]
         print(json.dumps({

@@ -852,6 +852,47 @@ __device__ __forceinline__ void warp_count(unsigned char *regions, int rbytes, i
     }
 }
 
+// The interior bins of all lanes' flights, spread evenly over the 32 lanes:
+// lane t of each round scores interior task base + t, found by a 5-step
+// shuffle search over the warp's inclusive prefix sum of the interior counts.
+template <typename P>
+__device__ __forceinline__ void spread_interior(unsigned char *regions, int rbytes, int lreg, double *gflux,
+                                                uint32_t goff, int k0, P c, int ni, int lane) {
+    using B = typename Real<P>::Bin;
+    int incl = ni;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(CLS_FULL_MASK, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(CLS_FULL_MASK, incl, 31);
+    if (total == 0) return;
+    const bool any_global = __any_sync(CLS_FULL_MASK, lreg == 2 && ni > 0);
+    const int base_bin = k0 + 1 - (incl - ni);  // interior task t of this lane goes to base_bin + t
+    for (int base = 0; base < total; base += 32) {
+        const int t = base + lane;
+        int o = 0;
+#pragma unroll
+        for (int sft = 16; sft >= 1; sft >>= 1) {
+            const int v = __shfl_sync(CLS_FULL_MASK, incl, o + sft - 1);
+            if (v <= t) o += sft;
+        }
+        const int ob = __shfl_sync(CLS_FULL_MASK, base_bin, o);
+        const P oc = __shfl_sync(CLS_FULL_MASK, c, o);
+        const int oreg = __shfl_sync(CLS_FULL_MASK, lreg, o);
+        uint32_t ogoff = 0;
+        if (any_global) ogoff = __shfl_sync(CLS_FULL_MASK, goff, o);
+        if (t < total) {
+            if (oreg < 2) {
+                B *bins = reinterpret_cast<B *>(regions + oreg * rbytes);
+                atomicAdd(&bins[ob + t], (B)oc);
+            } else {
+                atomicAdd(&gflux[ogoff + ob + t], (double)oc);
+            }
+        }
+    }
+}
+
 // Score the warp's flights.  Each lane adds its two end bins.  Interior bins
 // (c each, k0 < k < k1): in an FP32 region with a difference array (DIF), two
 // entries of that fixed-point array (c at k0 + 1, -c at k1), whose prefix sum
@@ -890,38 +931,8 @@ __device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes,
         }
     }
     const int ni = (has && !(kDif && lreg < 2)) ? max(f.k1 - f.k0 - 1, 0) : 0;
-    int incl = ni;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(CLS_FULL_MASK, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const int total = __shfl_sync(CLS_FULL_MASK, incl, 31);
-    if (total == 0) return;
-    const bool any_global = __any_sync(CLS_FULL_MASK, lreg == 2 && ni > 0);
-    const int base_bin = f.k0 + 1 - (incl - ni);  // interior task t of this lane goes to base_bin + t
-    for (int base = 0; base < total; base += 32) {
-        const int t = base + lane;
-        int o = 0;
-#pragma unroll
-        for (int sft = 16; sft >= 1; sft >>= 1) {
-            const int v = __shfl_sync(CLS_FULL_MASK, incl, o + sft - 1);
-            if (v <= t) o += sft;
-        }
-        const int ob = __shfl_sync(CLS_FULL_MASK, base_bin, o);
-        const P oc = __shfl_sync(CLS_FULL_MASK, f.c, o);
-        const int oreg = __shfl_sync(CLS_FULL_MASK, lreg, o);
-        uint32_t ogoff = 0;
-        if (any_global) ogoff = __shfl_sync(CLS_FULL_MASK, goff, o);
-        if (t < total) {
-            if (oreg < 2) {
-                B *bins = reinterpret_cast<B *>(regions + oreg * rbytes);
-                atomicAdd(&bins[ob + t], (B)oc);
-            } else {
-                atomicAdd(&gflux[ogoff + ob + t], (double)oc);
-            }
-        }
-    }
+    if (!__any_sync(CLS_FULL_MASK, ni > 0)) return;  // one vote instead of the scan when no lane has any
+    spread_interior<P>(regions, rbytes, lreg, gflux, goff, f.k0, f.c, ni, lane);
 }
 
 // History end for a lane that scores into global memory: the same statistics
@@ -1042,24 +1053,27 @@ __device__ __forceinline__ int find_run(const LaunchArgs &a, uint64_t ch) {
 // older region is flushed and re-keyed, and its remaining histories score
 // straight into the FP64 global tallies: the warp never waits for a straggler
 // of a heavy-tailed history-length distribution.
-// Launch bounds: FP32 blocks of 256 threads, 4 per SM (64 registers); FP64
-// blocks of at most kHistoryBlockFp64 = 128 threads, 5 per SM (102 registers,
-// 20 warps), 6 (85 registers, 24 warps) for the one-dimensional walks (rod,
-// slab, x-projected box), whose state fits: the FP64 walk is latency-bound,
-// and more resident warps hide its integer-arithmetic and shared-memory
-// latencies (measured: 5% faster for the x-projected box at 6, no gain for the
-// 3D box, which would spill).
-template <typename P, int G>
+// Launch bounds: FP32 blocks of 256 threads, 4 per SM (64 registers) with the
+// interior-bin difference array, 3 per SM (80 registers) without it, where the
+// 64-register build spilled about 200 bytes a thread (measured on a 500-bin
+// diffusive box: 33% faster at 3; the difference-array kernels are 3% slower
+// at 3).  FP64 blocks of at most kHistoryBlockFp64 = 128 threads, 5 per SM
+// (102 registers, 20 warps), 6 (85 registers, 24 warps) for the
+// one-dimensional walks (rod, slab, x-projected box), whose state fits: the
+// FP64 walk is latency-bound, and more resident warps hide its
+// integer-arithmetic and shared-memory latencies (measured: 5% faster for the
+// x-projected box at 6, no gain for the 3D box, which would spill).
+template <typename P, int G, bool DIF>
 struct HistoryBounds {
     static constexpr int threads = kHistoryBlockFp64, blocks = (G == 1 || G == 11 || G == 13) ? 6 : 5;
 };
-template <int G>
-struct HistoryBounds<float, G> {
-    static constexpr int threads = 256, blocks = 4;
+template <int G, bool DIF>
+struct HistoryBounds<float, G, DIF> {
+    static constexpr int threads = 256, blocks = DIF ? 4 : 3;
 };
 
 template <typename P, int G, bool DIF = false>
-__global__ void __launch_bounds__(HistoryBounds<P, G>::threads, HistoryBounds<P, G>::blocks) history_kernel(const LaunchArgs a) {
+__global__ void __launch_bounds__(HistoryBounds<P, G, DIF>::threads, HistoryBounds<P, G, DIF>::blocks) history_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
