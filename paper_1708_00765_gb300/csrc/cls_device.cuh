@@ -135,17 +135,19 @@ struct Real<double> {
     static __device__ __forceinline__ void direction_cosines(uint32_t hi, uint32_t lo, bool cosine, double *mu,
                                                              double *st) {
         const unsigned long long k = k53(hi, lo), n = (1ull << 53) - k;
-        // sqrt(u) (used by the cosine law only), then st, through one copy of sqrt_int
-        U128 x = U128{k << 1, 0ull};
+        // sqrt(u) (the cosine law only: a lane starts the loop at t = 1
+        // otherwise), then st, through one copy of sqrt_int
         const U128 x1 = cosine ? U128{n << 1, 0ull} : U128{(k * n) << 2, (umulhi64(k, n) << 2) | ((k * n) >> 62)};
-        int scale = 54;
+        const int s1 = cosine ? 54 : 106;
+        U128 x = cosine ? U128{k << 1, 0ull} : x1;
+        int scale = s1;
         double r0 = 0.0, r1 = 0.0;
 #pragma unroll 1
-        for (int t = 0; t < 2; ++t) {
+        for (int t = cosine ? 0 : 1; t < 2; ++t) {
             r0 = r1;
             r1 = sqrt_int(x, scale);
             x = x1;
-            scale = cosine ? 54 : 106;
+            scale = s1;
         }
         *mu = cosine ? r0 : two_u_minus_one(hi, lo);
         *st = r1;
