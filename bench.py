@@ -323,6 +323,21 @@ def batch_workload(args, rank, world, pg):
             dev = timed_runs(b, n, 1, args.steps, args.warmup, flush, torch, stream)
             arms[prec] = (max_over_ranks(pg, dev) / args.steps, [b.tallies(k) for k in range(len(cases))])
             b.close()
+        # identical outcomes: both precisions walk the same histories (seed 11,
+        # ids 0..n-1 of every case) once more, untimed, recording each history's
+        # outcome (reflected / transmitted / absorbed / capped) on the device
+        codes = {}
+        for prec in ("fp32", "fp64"):
+            b = cls.Problem(cases, batch=True)
+            b.set_option("precision", prec)
+            b.autotune(max(4096, min(n // 16, 262_144)), seed=3, stream=stream)  # cached: the choice above
+            codes[prec] = torch.empty(len(cases) * n, dtype=torch.uint8, device="cuda")
+            b.record_outcomes(codes[prec].data_ptr(), codes[prec].numel())
+            b.run(n, 11, stream=stream)
+            torch.cuda.synchronize()
+            b.close()
+        same = (codes["fp32"] == codes["fp64"]).view(len(cases), n).sum(1, dtype=torch.int64).cpu().numpy() / n
+        del codes
     if rank == 0:
         t32, tal32 = arms["fp32"]
         t64b, tal64b = arms["fp64"]
@@ -353,6 +368,9 @@ def batch_workload(args, rank, world, pg):
                                                        "max": ratios[-1], "cases": len(ratios)},
             "fp32_vs_fp64_z": {"max_abs": max(abs(z) for z in zs), "rms": math.sqrt(sum(z * z for z in zs) / len(zs)),
                                "note": "same seed: correlated draws, so this z is conservative"},
+            "fp32_fp64_identical_outcomes": {"median": float(sorted(same)[len(same) // 2]), "min": float(same.min()),
+                                             "max": float(same.max()), "overall": float(same.mean()),
+                                             "histories_per_case": n, "seed": 11},
         }), flush=True)
 
 

@@ -242,6 +242,29 @@ int cls_batch_tallies(cls_handle *h, int case_idx, cls_tallies_t *out);
 /* Number of cases of the handle (1 for cls_create handles). */
 int cls_num_cases(const cls_handle *h);
 
+/* ------------------------------------------------------ per-history outcomes */
+
+/* Outcome codes of cls_record_outcomes: how a history ended (paper Sec. 2:
+ * leakage through x = 0 counts toward R, through x = L toward T; absorption
+ * toward A; the event cap toward none of them). */
+#define CLS_OUTCOME_REFLECTED 0
+#define CLS_OUTCOME_TRANSMITTED 1
+#define CLS_OUTCOME_ABSORBED 2
+#define CLS_OUTCOME_CAPPED 3
+
+/* Record every history's outcome, one byte per history, in the caller-owned
+ * device buffer d_codes of `capacity` bytes: from the next cls_run or
+ * cls_batch_run on, history h of case k writes
+ * d_codes[k * n + (h - first)] = CLS_OUTCOME_*, where n is that run's
+ * histories per case and first its first history id.  Each run overwrites the
+ * codes of its own histories; the tallies are unaffected.  d_codes = NULL
+ * stops recording.  The buffer must stay allocated while runs that record
+ * into it are in flight.  A run then fails with CLS_E_INVAL when
+ * ncases x n > capacity, and with CLS_E_STATE when the cases' next history
+ * ids differ (CLS_OPT_FIRST_HISTORY sets them all alike).
+ * Errors: CLS_E_INVAL (null handle, or capacity 0 with a buffer). */
+int cls_record_outcomes(cls_handle *h, uint8_t *d_codes, uint64_t capacity);
+
 /* ------------------------------------------------------------ diagnostics */
 
 /* Evaluate this library's device Philox4x32-10 and, for comparison, CUDA's

@@ -112,6 +112,10 @@ def lib():
                                 ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
                                 ctypes.c_int, ctypes.POINTER(_OrcCounts)]
         L.orc_trace.restype = ctypes.c_int
+        L.orc_outcomes.argtypes = [ctypes.POINTER(_OrcCase), ctypes.c_uint32, ctypes.c_uint64,
+                                   ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                   ctypes.POINTER(ctypes.c_uint8)]
+        L.orc_outcomes.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -216,6 +220,19 @@ def run_parallel(case: Case, seed: int, first: int, n: int, *, workers: int | No
     out.update(sum_t=sum_t, sum_t2=sum_t2, track=tuple(track), flux=flux, batch_len=bl,
                nbatch=nbatch, first=first, seed=seed, workers=len(args))
     return out
+
+
+def outcomes(case: Case, seed: int, first: int, n: int, *, case_id: int = 0,
+             max_events: int = DEFAULT_MAX_EVENTS) -> np.ndarray:
+    """Outcome of each history of [first, first+n): uint8 array, 0 reflected, 1 transmitted,
+    2 absorbed, 3 event cap (paper Sec. 2 observables R, T, A)."""
+    oc = _ocase(case)
+    codes = np.zeros(n, dtype=np.uint8)
+    rc = lib().orc_outcomes(ctypes.byref(oc), case_id, seed, first, n, max_events,
+                            codes.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    if rc != 0:
+        raise ValueError("oracle rejected the case or arguments")
+    return codes
 
 
 def trace(case: Case, seed: int, h: int, *, case_id: int = 0, max_events: int = DEFAULT_MAX_EVENTS,

@@ -448,6 +448,33 @@ int orc_run(const orc_case_t *cs, uint32_t case_id, uint64_t seed, uint64_t firs
     return 0;
 }
 
+/* Outcome of each of histories first .. first+n-1 of one case, one byte per
+ * history (0 reflected, 1 transmitted, 2 absorbed, 3 event cap; paper Sec. 2
+ * observables R, T, A).  Tallies are computed and discarded.
+ * Returns 0, or -1 on invalid input. */
+int orc_outcomes(const orc_case_t *cs, uint32_t case_id, uint64_t seed, uint64_t first, uint64_t n,
+                 uint64_t max_events, uint8_t *codes)
+{
+    if (check_case(cs) || !codes)
+        return -1;
+    size_t nb = (size_t)cs->nbins;
+    nsum_t *bins = calloc(nb, sizeof(nsum_t));
+    if (!bins)
+        return -1;
+    orc_counts_t cnt;
+    memset(&cnt, 0, sizeof(cnt));
+    orc_tally_t tal;
+    memset(&tal, 0, sizeof(tal));
+    tal.cs = cs;
+    tal.bins = bins;
+    for (uint64_t i = 0; i < n; i++) {
+        tal.t_hist = 0.0;
+        codes[i] = (uint8_t)run_history(cs, case_id, seed, first + i, max_events, &tal, &cnt, NULL);
+    }
+    free(bins);
+    return 0;
+}
+
 /* Event-by-event trace of history h: rows of 10 doubles
  * (event, draw index after the event, x, y, z, wx, wy, wz, material, flight length).
  * Returns the number of rows written (at most cap), or -1 on invalid input. */

@@ -43,9 +43,14 @@ CLS_SCHED_EVENT = 2
 # every symbol include/cls.h declares
 EXPORTED = ("cls_create", "cls_set_option", "cls_get_option", "cls_run", "cls_tallies", "cls_raw_tallies",
             "cls_reset", "cls_destroy", "cls_strerror", "cls_trace", "cls_batch_create", "cls_batch_run",
-            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_debug_math", "cls_run_noalloc", "cls_autotune", "cls_finalize_raw")
+            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_debug_math", "cls_run_noalloc", "cls_autotune", "cls_finalize_raw",
+            "cls_record_outcomes")
 
 CLS_NOALLOC_MAX_CASES = 64
+CLS_OUTCOME_REFLECTED = 0
+CLS_OUTCOME_TRANSMITTED = 1
+CLS_OUTCOME_ABSORBED = 2
+CLS_OUTCOME_CAPPED = 3
 
 
 class ClsError(RuntimeError):
@@ -113,6 +118,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "cls_run_noalloc": ([P(d), i, u64, u64, u64, i, i, H, H, H, H], i),
         "cls_autotune": ([H, u64, u64, H], i),
         "cls_finalize_raw": ([P(cls_raw_t), P(d), P(u64), d, P(cls_tallies_t)], i),
+        "cls_record_outcomes": ([H, H, u64], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -211,6 +217,12 @@ class Problem:
 
     def reset(self):
         _check(load().cls_reset(self._h), "cls_reset")
+
+    def record_outcomes(self, d_codes: int, capacity: int):
+        """cls_record_outcomes: later runs write each history's CLS_OUTCOME_* code into the
+        device buffer at address d_codes (capacity bytes; 0 stops recording)."""
+        _check(load().cls_record_outcomes(self._h, d_codes or None, capacity if d_codes else 0),
+               "cls_record_outcomes")
 
     def autotune(self, n_pilot: int, seed: int = 1, stream=None) -> dict:
         """cls_autotune: returns the chosen schedule and launch shape."""

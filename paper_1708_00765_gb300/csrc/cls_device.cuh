@@ -937,6 +937,20 @@ __device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes,
     spread_interior<P>(regions, rbytes, lreg, gflux, goff, f.k0, f.c, ni, lane);
 }
 
+// A finished history's outcome into the caller's record, when one is bound
+// (OutcomeRecord): 0 reflected (left through x = 0), 1 transmitted (x = L),
+// 2 absorbed, 3 capped.  One byte per history; the host has checked that the
+// record holds the run's cases x histories.
+__device__ __forceinline__ void record_outcome(const LaunchArgs &a, int case_index, uint32_t h_lo, uint32_t h_hi,
+                                               int outcome) {
+    if (a.outcomes == nullptr) return;
+    const OutcomeRecord r = *a.outcomes;
+    if (r.codes == nullptr) return;
+    const uint64_t h = ((uint64_t)h_hi << 32) | h_lo;
+    const uint8_t code = outcome == EV_LEAK_X0 ? 0 : outcome == EV_LEAK_XL ? 1 : outcome == EV_ABSORB ? 2 : 3;
+    r.codes[(uint64_t)case_index * r.stride + (h - r.first)] = code;
+}
+
 // History end for a lane that scores into global memory: the same statistics
 // and counters as finish_history, added to the case's global tally block.
 template <typename P>
@@ -1182,6 +1196,7 @@ __global__ void __launch_bounds__(HistoryBounds<P, G, DIF>::threads, HistoryBoun
         const uint32_t goff = (lreg == 2) ? ((uint32_t)lcase * (uint32_t)a.t.nbatch + lbatch) * (uint32_t)a.t.nbins_stride : 0u;
         warp_deposit<P, DIF>(regions, rb, a.t.nbins_stride, lreg, a.t.flux, goff, f, lane);
         if (out >= 0) {
+            record_outcome(a, lcase, s.h_lo, s.h_hi, out);
             if (lreg < 2) {
                 finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, lane);
                 if constexpr (G != 0)

@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(256, EventMinBlocks<P>::value) event_kernel(co
                 if (alive) o = step<P, false, G>(s, a.cases[ci], key, a.max_events, f, nullptr);
                 warp_deposit<P, DIF>(regions, rb, nbs, reg, a.t.flux, goff, f, lane);
                 if (o >= 0) {
+                    record_outcome(a, ci, s.h_lo, s.h_hi, o);
                     if (reg < 2) finish_event_history<P>(regions + reg * rb, nbs, s, o);
                     else finish_history_global<P>(a, ci, s, o, false);
                     alive = false;

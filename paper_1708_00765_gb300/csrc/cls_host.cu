@@ -65,8 +65,10 @@ struct cls_handle {
     unsigned long long *d_counters = nullptr;
     unsigned long long *d_chunk_counter = nullptr;
     // per-run work
-    RunCase *h_runs = nullptr;  // pinned
+    RunCase *h_runs = nullptr;  // pinned; the OutcomeRecord follows the cases' RunCases
     RunCase *d_runs = nullptr;
+    uint8_t *outcome_codes = nullptr;  // caller's per-history outcome buffer (device), or null
+    uint64_t outcome_cap = 0;
     cudaEvent_t runs_copied = nullptr;
     std::vector<int> order;  // case indices, largest estimated cost first
     std::vector<uint64_t> next_history;
@@ -99,6 +101,13 @@ int cuda_fail(cudaError_t e) { return e == cudaSuccess ? CLS_OK : CLS_E_CUDA; }
     } while (0)
 
 bool finite(double v) { return std::isfinite(v); }
+
+// The run's work list: one RunCase per case, then the OutcomeRecord.
+size_t runs_bytes(size_t ncases) { return ncases * sizeof(RunCase) + sizeof(OutcomeRecord); }
+
+OutcomeRecord *outcome_record(RunCase *runs, size_t ncases) {
+    return reinterpret_cast<OutcomeRecord *>(reinterpret_cast<unsigned char *>(runs) + ncases * sizeof(RunCase));
+}
 
 int validate(const double *p) {
     const double s0 = p[0], s1 = p[1], l0 = p[2], l1 = p[3], c0 = p[4], c1 = p[5], L = p[6];
@@ -242,9 +251,9 @@ int create_common(const double *params, int ncases, bool batch, cls_handle **out
     h->nbatch = h->opt.nbatch;
     int rc = CLS_OK;
     if (cudaMalloc(&h->d_cases, ncases * sizeof(CaseParams)) != cudaSuccess ||
-        cudaMalloc(&h->d_runs, ncases * sizeof(RunCase)) != cudaSuccess ||
+        cudaMalloc(&h->d_runs, runs_bytes(ncases)) != cudaSuccess ||
         cudaMalloc(&h->d_chunk_counter, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&h->h_runs, ncases * sizeof(RunCase)) != cudaSuccess) {
+        cudaMallocHost(&h->h_runs, runs_bytes(ncases)) != cudaSuccess) {
         rc = CLS_E_NOMEM;
     }
     if (!rc) rc = alloc_tallies(h);
@@ -296,6 +305,15 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, LaunchArgs *a) {
         r.pad = 0;
         chunk_begin += (n + h->opt.chunk - 1) / h->opt.chunk;
     }
+    OutcomeRecord *rec = outcome_record(h->h_runs, nc);
+    *rec = OutcomeRecord{nullptr, 0, 0};
+    if (h->outcome_codes) {
+        // every case's row starts at the same history id and holds n codes
+        for (int k = 1; k < nc; ++k)
+            if (h->next_history[k] != h->next_history[0]) return CLS_E_STATE;
+        if (n > h->outcome_cap / (uint64_t)nc) return CLS_E_INVAL;
+        *rec = OutcomeRecord{h->outcome_codes, h->next_history[0], n};
+    }
     std::memset(a, 0, sizeof(*a));
     a->cases = h->d_cases;
     a->runs = h->d_runs;
@@ -310,6 +328,7 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, LaunchArgs *a) {
     a->region_bytes = region_bytes_for(h);
     a->dif = region_dif_for(h) ? 1 : 0;
     a->flush_every = (h->opt.precision == CLS_PREC_FP32) ? kFp32FlushHistories : 0;
+    a->outcomes = outcome_record(h->d_runs, nc);
     return CLS_OK;
 }
 
@@ -780,7 +799,7 @@ int cls_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
     if (rc) return rc;
     rc = record_pair(h, s, true);
     if (rc) return rc;
-    CLS_CUDA(cudaMemcpyAsync(h->d_runs, h->h_runs, h->cases.size() * sizeof(RunCase), cudaMemcpyHostToDevice, s));
+    CLS_CUDA(cudaMemcpyAsync(h->d_runs, h->h_runs, runs_bytes(h->cases.size()), cudaMemcpyHostToDevice, s));
     CLS_CUDA(cudaEventRecord(h->runs_copied, s));
     CLS_CUDA(cudaMemsetAsync(h->d_chunk_counter, 0, sizeof(unsigned long long), s));
     rc = launch_tracker(h, a, sh, s);
@@ -836,13 +855,20 @@ int cls_batch_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
     }
     rc = record_pair(h, s, true);
     if (rc) return rc;
-    CLS_CUDA(cudaMemcpyAsync(h->d_runs, h->h_runs, h->cases.size() * sizeof(RunCase), cudaMemcpyHostToDevice, s));
+    CLS_CUDA(cudaMemcpyAsync(h->d_runs, h->h_runs, runs_bytes(h->cases.size()), cudaMemcpyHostToDevice, s));
     CLS_CUDA(cudaEventRecord(h->runs_copied, s));
     CLS_CUDA(cudaGraphLaunch(h->graph_exec, s));
     rc = record_pair(h, s, false);
     if (rc) return rc;
     h->last_stream = s;
     account_run(h, n);
+    return CLS_OK;
+}
+
+int cls_record_outcomes(cls_handle *h, uint8_t *d_codes, uint64_t capacity) {
+    if (!h || (d_codes && capacity == 0)) return CLS_E_INVAL;
+    h->outcome_codes = d_codes;
+    h->outcome_cap = d_codes ? capacity : 0;
     return CLS_OK;
 }
 

@@ -46,6 +46,17 @@ struct RunCase {
     int32_t pad;
 };
 
+// The caller's per-history outcome record (cls_record_outcomes), kept in
+// device memory right after the run's RunCase array, so that a captured batch
+// graph reads the current binding at every replay.  History h of case k
+// writes codes[k * stride + (h - first)]: CLS_OUTCOME_* (0 reflected, 1
+// transmitted, 2 absorbed, 3 capped).  codes == nullptr: nothing is recorded.
+struct OutcomeRecord {
+    uint8_t *codes;
+    uint64_t first;   // first history id of the run (the same for every case)
+    uint64_t stride;  // the run's histories per case
+};
+
 // Order of the counters and statistics in every tally block and smem region.
 enum Counter { C_R = 0, C_T, C_A, C_COLL, C_INT, C_REFL, C_EVENTS, C_CAPPED, C_MAXEV, C_NUM };
 enum Stat { S_T = 0, S_T2, S_TRACK0, S_TRACK1, S_NUM };
@@ -100,6 +111,7 @@ struct LaunchArgs {
     int region_bytes;     // bytes per warp tally region (see region_bytes())
     int flush_every;      // flush a region after this many histories were fed into it (0: never)
     int dif;              // FP32 regions carry the difference array of interior-bin deposits
+    const OutcomeRecord *outcomes;  // per-history outcome record, or nullptr (never recorded)
     // event schedule only
     void *bank;            // grid warps x 2 buffers x bank_slots particles (SoA)
     uint32_t bank_slots;   // particles per warp and buffer, a multiple of 32

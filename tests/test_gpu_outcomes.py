@@ -1,0 +1,112 @@
+"""Per-history outcome records (cls_record_outcomes) through the C ABI.
+
+FP64: every history's outcome (reflected, transmitted, absorbed, capped --
+the paper's R, T, A observables, Sec. 2) equals the oracle's, history by
+history, for both schedules, single cases and graph-replayed batches.  FP32:
+the fraction of histories with the FP64 run's outcome on the same seed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1708_00765_gb300 as cls  # noqa: E402
+from paper_1708_00765_gb300 import workloads  # noqa: E402
+
+
+def ocase(p):
+    return oracle.Case(*p[:7], int(p[7]), int(p[8]))
+
+
+def gpu_codes(params, n, seed, batch=False, runs=1, **opts):
+    """Outcome codes of `runs` consecutive runs of n histories per case (the last run's)
+    and the last run's first history id, plus the handle's raw tallies of case 0."""
+    prob = cls.Problem(params, batch=batch)
+    for k, v in opts.items():
+        prob.set_option(k, v)
+    ncases = prob.params.shape[0]
+    buf = torch.full((ncases * n,), 255, dtype=torch.uint8, device="cuda")
+    prob.record_outcomes(buf.data_ptr(), buf.numel())
+    for _ in range(runs):
+        prob.run(n, seed)
+    torch.cuda.synchronize()
+    raw = prob.raw_tallies(0)
+    prob.close()
+    return buf.cpu().numpy().reshape(ncases, n), (runs - 1) * n, raw
+
+
+@pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10, workloads.BOX_L10_X])
+@pytest.mark.parametrize("schedule", ["history", "event"])
+def test_fp64_outcomes_match_oracle_history_by_history(params, schedule):
+    n = 3000
+    codes, first, raw = gpu_codes(params, n, 17, runs=2, schedule=schedule)
+    ref = oracle.outcomes(ocase(params), 17, first, n)
+    assert np.array_equal(codes[0], ref)
+    # the tallies count both runs; the record holds the last one
+    ref_all = np.concatenate([oracle.outcomes(ocase(params), 17, 0, n), ref])
+    assert np.bincount(ref_all, minlength=4).tolist() == [raw["nR"], raw["nT"], raw["nA"], raw["n_capped"]]
+
+
+def test_batch_outcomes_match_oracle_after_graph_replay():
+    params = workloads.batch_sweep(12, seed=7, nbins=20)
+    n = 1024
+    codes, first, _ = gpu_codes(params, n, 9, batch=True, runs=3)
+    assert first == 2 * n
+    for k in range(params.shape[0]):
+        ref = oracle.outcomes(ocase(params[k]), 9, first, n, case_id=k)
+        assert np.array_equal(codes[k], ref), k
+
+
+def test_event_cap_is_recorded_as_capped():
+    codes, _, raw = gpu_codes(workloads.BOX_L10, 2000, 3, max_events=4)
+    assert set(np.unique(codes).tolist()) <= {0, 1, 2, 3}
+    assert int((codes == 3).sum()) == raw["n_capped"] > 0
+    ref = oracle.outcomes(ocase(workloads.BOX_L10), 3, 0, 2000, max_events=4)
+    assert np.array_equal(codes[0], ref)
+
+
+def test_recording_does_not_change_the_tallies():
+    params = workloads.BOX_L10
+    a = cls.Problem(params)
+    a.run(20_000, 5)
+    ta = a.raw_tallies()
+    a.close()
+    _, _, tb = gpu_codes(params, 20_000, 5)
+    for k in ("nR", "nT", "nA", "n_coll", "n_interface", "n_reflect", "n_events", "max_events"):
+        assert ta[k] == tb[k], k
+    assert ta["sum_t"] == pytest.approx(tb["sum_t"], rel=1e-12)
+
+
+def test_record_too_small_is_refused_and_null_stops_recording():
+    prob = cls.Problem(workloads.ROD_L10)
+    buf = torch.full((100,), 255, dtype=torch.uint8, device="cuda")
+    prob.record_outcomes(buf.data_ptr(), buf.numel())
+    with pytest.raises(cls.ClsError) as e:
+        prob.run(101, 1)
+    assert e.value.code == cls.CLS_E_INVAL
+    prob.record_outcomes(0, 0)
+    prob.run(101, 1)
+    torch.cuda.synchronize()
+    assert int((buf == 255).sum()) == 100  # nothing written by either run
+    prob.close()
+
+
+@pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10])
+def test_fp32_outcomes_mostly_identical_to_fp64(params):
+    """FP32 tracking draws the same variates truncated to 24 bits: most histories end
+    the same way as in FP64; the counts of each outcome stay within 4 standard errors."""
+    n = 100_000
+    c64, _, _ = gpu_codes(params, n, 21)
+    c32, _, _ = gpu_codes(params, n, 21, precision="fp32")
+    same = float(np.mean(c64 == c32))
+    assert same > 0.8
+    for code in (0, 1, 2):
+        p = float(np.mean(c64 == code))
+        sd = max(np.sqrt(2 * p * (1 - p) / n), 1.0 / n)
+        assert abs(float(np.mean(c32 == code)) - p) < 4 * sd

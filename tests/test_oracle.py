@@ -89,6 +89,22 @@ def test_event_cap_terminates_and_is_counted():
     assert raw["nR"] + raw["nT"] + raw["nA"] + raw["n_capped"] == 500
 
 
+@pytest.mark.parametrize("case", [C1, C2, SLAB, BOXX])
+def test_outcomes_agree_with_counts_and_traces(case):
+    """Per-history outcomes: their histogram is the run's R, T, A counts, and each
+    history's code is the terminating event of its trace (leak at x = 0, at x = L,
+    absorption)."""
+    codes = oracle.outcomes(case, 4, 50, 1500)
+    raw = oracle.run(case, 4, 50, 1500)
+    assert codes.dtype == np.uint8 and codes.shape == (1500,)
+    assert np.bincount(codes, minlength=4).tolist() == [raw["nR"], raw["nT"], raw["nA"], raw["n_capped"]]
+    for i in (0, 1, 7, 500, 1499):
+        rows, _ = oracle.trace(case, 4, 50 + i)
+        assert codes[i] == {0: 0, 1: 1, 4: 2}[int(rows[-1, 0])]
+    capped = oracle.outcomes(case, 4, 50, 300, max_events=2)
+    assert np.all((capped == 3) | (codes[:300] == capped))
+
+
 def test_invalid_cases_rejected():
     for bad in (oracle.Case(0.5, 5.0, 0.0, 0.5, 0.5, 0.9, 10.0, 1, 100),
                 oracle.Case(0.5, 5.0, 2.0, 0.5, 1.5, 0.9, 10.0, 1, 100),
