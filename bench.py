@@ -49,6 +49,11 @@ FP32_WARP_INST_PER_EVENT = 21.1
 FP64_FLOP_PER_EVENT = 148.8
 # The diffusive workload's FP32 kernels (500 bins: no difference array).
 DIFFUSIVE_WARP_INST_PER_EVENT = {"history": 20.1, "event": 20.5}
+# The batched sweep's FP32 kernel (history_kernel<float, 0, 1>, 256 cases x
+# 1e7 histories in one launch, autotuned shape): warp instructions per event
+# and DRAM bytes of one full-size replay, the same one-pass ncu capture.
+BATCH_FP32_WARP_INST_PER_EVENT = 27.0
+BATCH_FP32_DRAM_BYTES_PER_LAUNCH = 12989440
 # DRAM bytes of that full-size FP64 launch (the same one-pass capture); None
 # whenever the kernel has changed since the capture.
 FP64_DRAM_BYTES_PER_LAUNCH = 774144
@@ -295,28 +300,32 @@ def batch_workload(args, rank, world, pg):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    t64 = t64b = None
+    tal64 = []
+    same = None
     with sampler:
         # FP64 plain: one handle and one launch per case
-        plain = [cls.Problem(c) for c in cases]
+        plain = [] if args.no_fp64 else [cls.Problem(c) for c in cases]
         for p in plain:
             p.run(min(n, 20_000), 1, stream=stream)  # warm-up
             p.reset()
         torch.cuda.synchronize()
-        flush.zero_()
-        start = torch.cuda.Event(enable_timing=True)
-        stop = torch.cuda.Event(enable_timing=True)
-        start.record(stream)
-        for p in plain:
-            p.run(n, 1, stream=stream)
-        stop.record(stream)
-        torch.cuda.synchronize()
-        t64 = max_over_ranks(pg, start.elapsed_time(stop) * 1e-3)
-        tal64 = [p.tallies() for p in plain]
-        for p in plain:
-            p.close()
+        if plain:
+            flush.zero_()
+            start = torch.cuda.Event(enable_timing=True)
+            stop = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            for p in plain:
+                p.run(n, 1, stream=stream)
+            stop.record(stream)
+            torch.cuda.synchronize()
+            t64 = max_over_ranks(pg, start.elapsed_time(stop) * 1e-3)
+            tal64 = [p.tallies() for p in plain]
+            for p in plain:
+                p.close()
         arms = {}
         tuned = {}
-        for prec in ("fp32", "fp64"):
+        for prec in ("fp32",) if args.no_fp64 else ("fp32", "fp64"):
             b = cls.Problem(cases, batch=True)
             b.set_option("precision", prec)
             tuned[prec] = b.autotune(max(4096, min(n // 16, 262_144)), seed=3, stream=stream)
@@ -327,7 +336,7 @@ def batch_workload(args, rank, world, pg):
         # ids 0..n-1 of every case) once more, untimed, recording each history's
         # outcome (reflected / transmitted / absorbed / capped) on the device
         codes = {}
-        for prec in ("fp32", "fp64"):
+        for prec in () if args.no_fp64 else ("fp32", "fp64"):
             b = cls.Problem(cases, batch=True)
             b.set_option("precision", prec)
             b.autotune(max(4096, min(n // 16, 262_144)), seed=3, stream=stream)  # cached: the choice above
@@ -336,10 +345,28 @@ def batch_workload(args, rank, world, pg):
             b.run(n, 11, stream=stream)
             torch.cuda.synchronize()
             b.close()
-        same = (codes["fp32"] == codes["fp64"]).view(len(cases), n).sum(1, dtype=torch.int64).cpu().numpy() / n
+        if codes:
+            same = (codes["fp32"] == codes["fp64"]).view(len(cases), n).sum(1, dtype=torch.int64).cpu().numpy() / n
         del codes
+    t32, tal32 = arms["fp32"]
+    events32 = sum(t["n_events"] for t in tal32) / args.steps  # per replay (tallies of the timed steps)
+    clk_mhz = sampler.summary().get("sm_mhz") or 2070.0
+    peak = SM_COUNT * ISSUE_PER_SM_CLK * clk_mhz * 1e6 / 1e12
+    roofline = None
+    if BATCH_FP32_WARP_INST_PER_EVENT is not None:
+        achieved = BATCH_FP32_WARP_INST_PER_EVENT * events32 / t32 / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
+                    "frac": achieved / peak,
+                    "traffic": BATCH_FP32_DRAM_BYTES_PER_LAUNCH if n == 10_000_000 else None,
+                    "kernel": "history_kernel<float, 0, 1>",
+                    "work": f"{BATCH_FP32_WARP_INST_PER_EVENT} warp instructions/event x {events32:.4g} events/replay",
+                    "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} issue/clk x {clk_mhz} MHz (sampled)"}
+    if rank == 0 and args.no_fp64:
+        print(json.dumps({"profiling": "FP32 batched arm only", "fp32_batched": {
+            "histories_per_s": world * len(cases) * n / t32, "s_per_replay": t32, "events_per_replay": events32,
+            "autotuned": tuned["fp32"]}, "roofline": roofline, "clocks": sampler.summary()}), flush=True)
+        return
     if rank == 0:
-        t32, tal32 = arms["fp32"]
         t64b, tal64b = arms["fp64"]
         ratios = []
         zs = []
@@ -347,7 +374,9 @@ def batch_workload(args, rank, world, pg):
             s64 = a["sigma_total_flux"]
             s32 = b["sigma_total_flux"]
             if s64 > 0 and s32 > 0:
-                ratios.append((s64 * s64 * t64) / (s32 * s32 * t32))
+                # FOM = 1 / (sigma^2 T), sigma and T of the same histories: the
+                # batched tallies hold the timed steps' histories (steps x n)
+                ratios.append((s64 * s64 * t64) / (s32 * s32 * t32 * args.steps))
                 zs.append((b["total_flux"] - a["total_flux"]) / math.hypot(s64, s32))
         ratios.sort()
         events64 = sum(a["n_events"] for a in tal64)
@@ -359,7 +388,8 @@ def batch_workload(args, rank, world, pg):
                        "l2": "flushed between steps"},
             "clocks": sampler.summary(),
             "fp32_batched": {"histories_per_s": world * len(cases) * n / t32, "s_per_replay": t32,
-                             "autotuned": tuned["fp32"]},
+                             "events_per_replay": events32, "autotuned": tuned["fp32"]},
+            "roofline": roofline,
             "fp64_batched": {"histories_per_s": world * len(cases) * n / t64b, "s_per_replay": t64b,
                              "autotuned": tuned["fp64"]},
             "fp64_plain": {"histories_per_s": world * len(cases) * n / t64, "s_total": t64,

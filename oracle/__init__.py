@@ -235,6 +235,25 @@ def outcomes(case: Case, seed: int, first: int, n: int, *, case_id: int = 0,
     return codes
 
 
+def _run_case(args):
+    case_t, seed, first, n, case_id = args
+    return run(Case(*case_t), seed, first, n, case_id=case_id)
+
+
+def run_many(cases, seed: int, first: int, n: int, *, case_ids=None, workers: int | None = None) -> list:
+    """run() of several cases (case k with Philox counter word case_ids[k], default k),
+    one task per case over a spawn-started process pool; a list of raw tallies."""
+    import multiprocessing as mp
+    case_ids = list(range(len(cases))) if case_ids is None else list(case_ids)
+    build()
+    args = [(astuple(c), seed, first, n, k) for c, k in zip(cases, case_ids)]
+    workers = min(workers or os.cpu_count() or 1, len(args))
+    if workers <= 1:
+        return [_run_case(a) for a in args]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_run_case, args)
+
+
 def trace(case: Case, seed: int, h: int, *, case_id: int = 0, max_events: int = DEFAULT_MAX_EVENTS,
           cap: int = 100_000):
     """Event-by-event trace of one history: array of rows

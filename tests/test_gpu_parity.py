@@ -292,6 +292,33 @@ def test_batch_cases_match_oracle_exactly():
     prob.close()
 
 
+def test_fp32_batch_within_combined_sigma_of_oracle_per_case():
+    """FP32-tracking batch, case by case, against the FP64 oracle on an independent seed
+    and a history-id subset: R, T, A and <phi> within 4.5 combined standard errors
+    (about 100 z-scores), their rms below 1.5."""
+    params = workloads.batch_sweep(32, seed=7, nbins=20)
+    prob = cls.Problem(params, batch=True)
+    prob.set_option("precision", "fp32")
+    prob.run(200_000, 31)
+    t32 = [prob.tallies(k) for k in range(params.shape[0])]
+    prob.close()
+    cases = [ocase(p) for p in params]
+    raws = oracle.run_many(cases, 32, 0, 20_000)
+    zs = []
+    for k, (c, raw) in enumerate(zip(cases, raws)):
+        ref = oracle.finalize(raw, c)
+        for key, skey in (("R", "sigma_R"), ("T", "sigma_T"), ("A", "sigma_A"), ("total_flux", "sigma_total_flux")):
+            comb = math.hypot(t32[k][skey], ref[skey])
+            if comb > 0:
+                zs.append((t32[k][key] - ref[key]) / comb)
+            else:
+                assert t32[k][key] == ref[key], (k, key)
+    zs = np.array(zs)
+    assert len(zs) > 80
+    assert np.max(np.abs(zs)) < 4.5
+    assert np.sqrt(np.mean(zs * zs)) < 1.5
+
+
 # ------------------------------------------------------- event schedule
 
 @pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10])

@@ -105,6 +105,16 @@ def test_outcomes_agree_with_counts_and_traces(case):
     assert np.all((capped == 3) | (codes[:300] == capped))
 
 
+def test_run_many_equals_run_per_case():
+    cases = [C1, SLAB, oracle.Case(1.0, 2.0, 0.3, 0.7, 1.0, 0.0, 2.0, 3, 7)]
+    many = oracle.run_many(cases, 6, 10, 400, case_ids=[3, 0, 9], workers=2)
+    for c, k, got in zip(cases, (3, 0, 9), many):
+        ref = oracle.run(c, 6, 10, 400, case_id=k)
+        for key in ("nR", "nT", "nA", "n_coll", "n_int", "n_events", "max_events"):
+            assert got[key] == ref[key]
+        assert got["sum_t"] == ref["sum_t"] and np.array_equal(got["flux"], ref["flux"])
+
+
 def test_invalid_cases_rejected():
     for bad in (oracle.Case(0.5, 5.0, 0.0, 0.5, 0.5, 0.9, 10.0, 1, 100),
                 oracle.Case(0.5, 5.0, 2.0, 0.5, 1.5, 0.9, 10.0, 1, 100),
