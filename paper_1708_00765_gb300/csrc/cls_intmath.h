@@ -136,14 +136,21 @@ CLS_HD double exp_variate(uint64_t k, IntLogTables tab) {
     // r = (1 + f) N_i / 2048 - 1, exactly, in Q63; |r| < 2^-8.6
     const int64_t R = (int64_t)(nn * (uint64_t)tab.n[i] - (1ull << 63));
     // ln(1 + r) = r + r^2 P(r), P = -1/2 + r/3 - r^2/4 + r^3/5 - r^4/6 + r^5/7
-    // (next term below 2^-69); Q31 where 2^-31 suffices, else Q63
+    // (next term below 2^-69), in Estrin's grouping (G. Estrin, Proc. Western
+    // Joint Computer Conference, 1960): P = q0 + r^2 q1 + r^4 q2 with
+    // q0 = -1/2 + r/3, q1 = -1/4 + r/5, q2 = -1/6 + r/7, so that the products
+    // do not form one long dependent chain.  rq = R + R^2 P needs P to 2^-46
+    // (|r| < 2^-8.6): q0 in Q63; q1 (times r^2 < 2^-17) and q2 (times
+    // r^4 < 2^-34) in Q31, their products with r^2 2^47 and r^4 2^62 in 32 bits.
     const int32_t r31 = (int32_t)(R >> 32);
-    const int32_t p6 = -0x15555555 + (int32_t)(((int64_t)r31 * 0x12492492) >> 31);  // -1/6 + r/7
-    const int32_t p5 = 0x1999999A + (int32_t)(((int64_t)r31 * p6) >> 31);           // 1/5 + r p6
-    const int64_t p4 = -(1ll << 61) + mulq63(R, (int64_t)((uint64_t)(int64_t)p5 << 32));                 // -1/4 + r p5
-    const int64_t p3 = 0x2AAAAAAAAAAAAAABll + mulq63(R, p4);                        // 1/3 + r p4
-    const int64_t p2 = -(1ll << 62) + mulq63(R, p3);                                // -1/2 + r p3
-    const int64_t rq = R + mulq63(mulq63(R, R), p2);                                // ln(1 + r) 2^63
+    const int64_t r2 = mulq63(R, R);                                                   // r^2 2^63
+    const int64_t q0 = -(1ll << 62) + mulq63(R, 0x2AAAAAAAAAAAAAABll);                 // -1/2 + r/3
+    const int32_t q1 = -0x20000000 + (int32_t)(((int64_t)r31 * 0x1999999A) >> 31);    // -1/4 + r/5
+    const int32_t q2 = -0x15555555 + (int32_t)(((int64_t)r31 * 0x12492492) >> 31);    // -1/6 + r/7
+    const int32_t r2s = (int32_t)(r2 >> 16);                                           // r^2 2^47
+    const int32_t r4s = (int32_t)(((int64_t)r2s * r2s) >> 32);                         // r^4 2^62
+    const int64_t P = q0 + (((int64_t)q1 * r2s) >> 15) + (((int64_t)q2 * r4s) >> 30);  // Q63
+    const int64_t rq = R + mulq63(r2, P);                                              // ln(1 + r) 2^63
     // ln(1 - u) 2^120 = T_i - E ln2 + rq 2^57, two's complement (negative)
     const uint64_t t_lo = tab.t[i][0], t_hi = tab.t[i][1];
     const uint64_t e_lo = CLS_LN2_Q120_LO * (uint64_t)E;
@@ -208,10 +215,11 @@ CLS_HD int64_t mulq62(int64_t a, int64_t d) {
 
 // 1/a for a normal double a: Newton-Raphson iteration for the reciprocal,
 // y <- y + y (1 - m y) (each step squares the relative error; P. Markstein,
-// IBM J. Res. Dev. 34, 1990), run twice in Q62 fixed point on the significand
-// m in [1, 2) from the FP32 approximate reciprocal of its leading 24 bits
-// (relative error below 2^-22), then one rounding to the nearest double:
-// within an ulp of 1/a.  Zero, subnormal, infinite and NaN a take the division.
+// IBM J. Res. Dev. 34, 1990), on the significand m in [1, 2) from the FP32
+// approximate reciprocal of its leading 24 bits (relative error below 2^-22):
+// one step in 32-bit arithmetic (to about 2^-30), one in Q62 fixed point (to
+// about 2^-59), then one rounding to the nearest double: within an ulp of 1/a.
+// Zero, subnormal, infinite and NaN a take the division.
 CLS_HD double recip_int(double a) {
     uint64_t b;
 #ifdef __CUDA_ARCH__
@@ -235,8 +243,14 @@ CLS_HD double recip_int(double a) {
     uint32_t rb;
     memcpy(&rb, &rf, sizeof rb);
     const int re = (int)((rb >> 23) & 0xFF) - 127;                    // -1, or 0 when y0 = 1
-    int64_t y = (int64_t)(((uint64_t)((rb & 0x7FFFFFu) | 0x800000u)) << (39 + re));  // y0 2^62
-    for (int it = 0; it < 2; ++it) {
+    // first step in 32-bit arithmetic (y0 and m to 31 fraction bits): y1
+    // within about 2^-30 of 1/m
+    const uint32_t y31 = ((rb & 0x7FFFFFu) | 0x800000u) << (8 + re);  // y0 2^31, at most 2^31
+    const uint32_t m31 = (uint32_t)(M >> 21);                         // m 2^31, truncated
+    const int64_t e0 = (int64_t)((1ull << 62) - (uint64_t)m31 * y31);  // (1 - m y0) 2^62, |.| < 2^41
+    int64_t y = (int64_t)((uint64_t)y31 << 31) + (int64_t)y31 * (e0 >> 31);  // y1 2^62
+    // second step in Q62
+    {
         const uint64_t hi = umulhi64(M, (uint64_t)y), lo = M * (uint64_t)y;
         const int64_t t = (int64_t)((hi << 12) | (lo >> 52));         // m y 2^62
         y += mulq62(y, (1ll << 62) - t);
@@ -253,10 +267,10 @@ CLS_HD double recip_int(double a) {
 
 // sqrt(X 2^-scale) rounded to the nearest double, for 0 <= X < 2^127 and even
 // scale: Newton-Raphson iteration for the reciprocal square root,
-// y <- y + y (1 - v y^2)/2, twice in Q61 fixed point on v = X 2^-2t in
-// [1/4, 1) from the FP32 approximate reciprocal square root of v's leading
-// 24 bits (relative error below 2^-22), then sqrt(v) = v y and one rounding:
-// within an ulp.
+// y <- y + y (1 - v y^2)/2, on v = X 2^-2t in [1/4, 1) from the FP32
+// approximate reciprocal square root of v's leading 24 bits (relative error
+// below 2^-22): one step in 32-bit arithmetic (to about 2^-29), one in Q61
+// fixed point, then sqrt(v) = v y and one rounding: within an ulp.
 CLS_HD double sqrt_int(U128 X, int scale) {
     if ((X.hi | X.lo) == 0ull) return 0.0;
     // normalise by an even shift: v = X' 2^-128 in [1/4, 1)
@@ -279,8 +293,15 @@ CLS_HD double sqrt_int(U128 X, int scale) {
     uint32_t yb;
     memcpy(&yb, &yf, sizeof yb);
     const int ye = (int)((yb >> 23) & 0xFF) - 127;  // 0, or 1 when y0 = 2
-    int64_t y = (int64_t)(((uint64_t)((yb & 0x7FFFFFu) | 0x800000u)) << (38 + ye));
-    for (int it = 0; it < 2; ++it) {
+    // first step in 32-bit arithmetic (y0 and v to 30 fraction bits): y1
+    // within about 2^-29 of 1/sqrt(v)
+    const uint32_t y30 = ((yb & 0x7FFFFFu) | 0x800000u) << (7 + ye);  // y0 2^30, at most 2^31
+    const uint32_t v32 = (uint32_t)(v >> 32);                          // v 2^32, truncated
+    const uint32_t vy30 = (uint32_t)(((uint64_t)v32 * y30) >> 32);     // v y0 2^30
+    const int64_t e0 = (int64_t)((1ull << 60) - (uint64_t)vy30 * y30);  // (1 - v y0^2) 2^60
+    int64_t y = (int64_t)((uint64_t)y30 << 31) + (int64_t)y30 * (e0 >> 30);  // y1 2^61
+    // second step in Q61
+    {
         const uint64_t vy = umulhi64(v, (uint64_t)y);                 // v y, Q61
         const int64_t t = (int64_t)(umulhi64(vy, (uint64_t)y) << 4);  // v y^2, Q62
         y += mulq62(y, ((1ll << 62) - t) >> 1);                      // + y (1 - v y^2)/2

@@ -158,7 +158,7 @@ def test_sincos_within_2m53(intmath):
 def test_reciprocal_within_one_ulp(intmath):
     """recip_int against exact rational reciprocals.  The host seeds the
     Newton-Raphson steps with the correctly rounded FP32 reciprocal, the device
-    with the approximate one; two steps leave either within an ulp."""
+    with the approximate one; the two Newton steps (32-bit, then Q62) leave either within an ulp."""
     from fractions import Fraction
     rnd = random.Random(6)
     xs = [1.0, -1.0, 0.5, 1.5, math.nextafter(2.0, 0.0), math.nextafter(1.0, 2.0), -0.3, 1e-20, 2.0**-1000, 0.0]
