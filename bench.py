@@ -44,19 +44,19 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # roofline as FP64-equivalent TFLOP/s for context.  The kernel evaluates the
 # elementary functions in the integer pipes and is bound by issue and latency,
 # not by the FP64 pipe.
-FP64_WARP_INST_PER_EVENT = 86.4
-FP32_WARP_INST_PER_EVENT = 21.1
+FP64_WARP_INST_PER_EVENT = 76.4
+FP32_WARP_INST_PER_EVENT = 21.2
 FP64_FLOP_PER_EVENT = 148.8
 # The diffusive workload's FP32 kernels (500 bins: no difference array).
-DIFFUSIVE_WARP_INST_PER_EVENT = {"history": 20.1, "event": 20.5}
+DIFFUSIVE_WARP_INST_PER_EVENT = {"history": 20.3, "event": 20.7}
 # The batched sweep's FP32 kernel (history_kernel<float, 0, 1>, 256 cases x
 # 1e7 histories in one launch, autotuned shape): warp instructions per event
 # and DRAM bytes of one full-size replay, the same one-pass ncu capture.
 BATCH_FP32_WARP_INST_PER_EVENT = 27.0
-BATCH_FP32_DRAM_BYTES_PER_LAUNCH = 12989440
+BATCH_FP32_DRAM_BYTES_PER_LAUNCH = 13024256
 # DRAM bytes of that full-size FP64 launch (the same one-pass capture); None
 # whenever the kernel has changed since the capture.
-FP64_DRAM_BYTES_PER_LAUNCH = 774144
+FP64_DRAM_BYTES_PER_LAUNCH = 750080
 SM_COUNT = 152           # GB300
 DFMA_PER_SM_CLK = 2      # ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / 152 SMs
 ISSUE_PER_SM_CLK = 4     # one warp instruction per scheduler per clock, 4 schedulers

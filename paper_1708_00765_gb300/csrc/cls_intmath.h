@@ -194,12 +194,17 @@ CLS_HD void sincos_2pi_int(uint64_t k, const int64_t (*sc)[2], double *sn, doubl
     const int64_t d = (int64_t)(((uint64_t)dh << 20) | (dl >> 44));
     const int64_t d2 = smulhi64(d, d) >> 11;                               // delta^2, Q63
     // sin(delta) = delta - delta d2 (1/6 - d2 (1/120 - d2/5040))
-    const int64_t b = 0x0111111111111111ll - mulq63(d2, 0x0006806806806807ll);  // 1/120 - d2/5040
-    const int64_t a = 0x1555555555555555ll - mulq63(d2, b);                    // 1/6 - d2 b
-    const int64_t sd = d - mulq63(mulq63(d, d2), a);                           // Q69
     // cos(delta) - 1 = -d2 (1/2 - d2 (1/24 - d2/720))
-    const int64_t e = 0x0555555555555555ll - mulq63(d2, 0x002d82d82d82d82ell);  // 1/24 - d2/720
-    const int64_t h = (1ll << 62) - mulq63(d2, e);                             // 1/2 - d2 e
+    // The inner terms need only 32-bit operands: b = 1/120 - d2/5040 (used
+    // times delta d2^2 < 2^-31) in Q31, and the products d2 b and d2/720
+    // (used times delta d2 < 2^-18, and d2^2 < 2^-25) from d2 2^43 and
+    // 32-bit coefficients, each within 2^-43.
+    const int32_t d2h = (int32_t)(d2 >> 20);                                            // d2 2^43
+    const int32_t b31 = 0x01111111 - (int32_t)(((int64_t)d2h * 0x00068068) >> 43);       // 1/120 - d2/5040, Q31
+    const int64_t a = 0x1555555555555555ll - (((int64_t)d2h * b31) >> 11);              // 1/6 - d2 b
+    const int64_t sd = d - mulq63(mulq63(d, d2), a);                                    // Q69
+    const int64_t e = 0x0555555555555555ll - (((int64_t)d2h * 0x002D82D8) >> 11);       // 1/24 - d2/720
+    const int64_t h = (1ll << 62) - mulq63(d2, e);                                      // 1/2 - d2 e
     const int64_t cm1 = -mulq63(d2, h);                                        // Q63
     // sin(a + delta) = S + S cm1 + C sin(delta); cos(a + delta) = C + C cm1 - S sin(delta)  (Q62)
     const int64_t s_cm1 = mulq63(S, cm1), c_cm1 = mulq63(C, cm1);
