@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "histories/s and FOM 1/(sigma^2 T) at equal sigma, FP32-batched vs FP64-plain on 1 GB300"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+BOX_WORKLOAD = "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, cosine incidence, 200 bins"
 
 # Work per event of the benchmark workloads' kernels, for the issue-rate
 # roofline (152 SMs x 4 warp instructions per clock): warp instructions per
@@ -206,8 +207,8 @@ def reference_arm(args, rank, world, pg):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(d for _, _, d in rates) / len(rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, 200 bins, FP64 (oracle sample)",
-                   "histories_per_step": n_mean},
+        "config": {"workload": BOX_WORKLOAD, "histories_per_step_per_gpu": n_mean, "schedule": "history",
+                   "precision": "fp64", "sample": "a bounded sample of the workload per step, on the host cores"},
         "cpu_baseline": {"value": value, "unit": "histories/s", "cores": used, "kind": "oracle",
                          "sample": f"{n_mean} histories of the box L=10 workload per step"},
         "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -611,7 +612,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r64["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, cosine incidence, 200 bins",
+            "config": {"workload": BOX_WORKLOAD,
                        "histories_per_step_per_gpu": n, "schedule": "history", "precision": "fp64",
                        "l2": "flushed between steps (512 MB write)", "seed": seed},
             "clocks": clocks,
