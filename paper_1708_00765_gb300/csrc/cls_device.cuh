@@ -1211,7 +1211,9 @@ __global__ void __launch_bounds__(HistoryBounds<P, G, DIF>::threads, HistoryBoun
         // (measured 10% faster there, 1-5% slower on the single-geometry walks)
         if constexpr (G == 0) warp_count<P>(regions, rb, a.t.nbins_stride, out >= 0 && lreg < 2, lreg, s, out, lane);
         if (out >= 0) alive = false;
-        if (a.flush_every) {
+        // only FP32 regions flush early (their float partial sums stay short);
+        // the host sets no flush interval for FP64 regions
+        if (sizeof(P) == 4 && a.flush_every) {
             if (fed0 >= a.flush_every) {
                 __syncwarp();
                 flush_region<P, DIF>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
