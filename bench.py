@@ -45,7 +45,7 @@ BOX_WORKLOAD = "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, cosine inciden
 # roofline as FP64-equivalent TFLOP/s for context.  The kernel evaluates the
 # elementary functions in the integer pipes and is bound by issue and latency,
 # not by the FP64 pipe.
-FP64_WARP_INST_PER_EVENT = 76.4
+FP64_WARP_INST_PER_EVENT = 76.0
 FP32_WARP_INST_PER_EVENT = 21.2
 FP64_FLOP_PER_EVENT = 148.8
 # The diffusive workload's FP32 kernels (500 bins: no difference array).
@@ -57,7 +57,7 @@ BATCH_FP32_WARP_INST_PER_EVENT = 27.0
 BATCH_FP32_DRAM_BYTES_PER_LAUNCH = 13024256
 # DRAM bytes of that full-size FP64 launch (the same one-pass capture); None
 # whenever the kernel has changed since the capture.
-FP64_DRAM_BYTES_PER_LAUNCH = 750080
+FP64_DRAM_BYTES_PER_LAUNCH = 882688
 SM_COUNT = 152           # GB300
 DFMA_PER_SM_CLK = 2      # ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / 152 SMs
 ISSUE_PER_SM_CLK = 4     # one warp instruction per scheduler per clock, 4 schedulers
