@@ -174,8 +174,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ oracle timing
-def oracle_rate(params, seconds_target: float, cores: int, first: int = 0):
-    """Time the FP64 oracle on a bounded sample of the workload over `cores` processes."""
+def oracle_rate(params, seconds_target: float, cores: int, first: int = 0, detail: dict | None = None):
+    """Time the FP64 oracle on a bounded sample of the workload over `cores` processes.
+    `detail`, if given, receives the single-process pilot's rate, the events per
+    second of the sample and the time the full workload would take (extrapolated)."""
     import oracle
     case = oracle.Case(*params[:7], int(params[7]), int(params[8]))
     t0 = time.perf_counter()
@@ -186,6 +188,8 @@ def oracle_rate(params, seconds_target: float, cores: int, first: int = 0):
     t0 = time.perf_counter()
     raw = oracle.run_parallel(case, 1, first, n, workers=cores)
     dt = time.perf_counter() - t0
+    if detail is not None:
+        detail.update(single_process_histories_per_s=rate1, events_per_s=raw["n_events"] / dt)
     return n / dt, n, dt, raw["workers"]
 
 
@@ -197,8 +201,9 @@ def reference_arm(args, rank, world, pg):
     params = workloads.BOX_L10
     cores = os.cpu_count() or 1
     rates = []
+    detail = {}
     for i in range(args.warmup + args.steps):
-        r, n, dt, used = oracle_rate(params, 4.0, cores, first=i * 10_000_000)
+        r, n, dt, used = oracle_rate(params, 4.0, cores, first=i * 10_000_000, detail=detail)
         if i >= args.warmup:
             rates.append((r, n, dt))
     value = sum(r for r, _, _ in rates) / len(rates)
@@ -210,7 +215,9 @@ def reference_arm(args, rank, world, pg):
         "config": {"workload": BOX_WORKLOAD, "histories_per_step_per_gpu": n_mean, "schedule": "history",
                    "precision": "fp64", "sample": "a bounded sample of the workload per step, on the host cores"},
         "cpu_baseline": {"value": value, "unit": "histories/s", "cores": used, "kind": "oracle",
-                         "sample": f"{n_mean} histories of the box L=10 workload per step"},
+                         "sample": f"{n_mean} histories of the box L=10 workload per step",
+                         "events_per_s": detail["events_per_s"],
+                         "single_process_histories_per_s": detail["single_process_histories_per_s"]},
         "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -633,9 +640,13 @@ def main():
                 line[arm] = rx
                 line["fom_ratio_" + arm + "_over_fp64"] = rx["fom_total_flux"] / r64["fom_total_flux"]
         if not args.no_cpu_baseline and world == 1:
-            rate, ns, dt, used = oracle_rate(params, 10.0, os.cpu_count() or 1, first=10**12)
+            detail = {}
+            rate, ns, dt, used = oracle_rate(params, 10.0, os.cpu_count() or 1, first=10**12, detail=detail)
             line["cpu_baseline"] = {"value": rate, "unit": "histories/s", "cores": used, "kind": "oracle",
-                                    "sample": f"{ns} histories of the same workload ({dt:.1f} s)"}
+                                    "sample": f"{ns} histories of the same workload ({dt:.1f} s)",
+                                    "events_per_s": detail["events_per_s"],
+                                    "single_process_histories_per_s": detail["single_process_histories_per_s"],
+                                    "full_workload_s_extrapolated": n / rate}
         print(json.dumps(line), flush=True)
     barrier(pg)
     if pg is not None:
