@@ -337,6 +337,9 @@ def batch_workload(args, rank, world, pg):
             b = cls.Problem(cases, batch=True)
             b.set_option("precision", prec)
             tuned[prec] = b.autotune(max(4096, min(n // 16, 262_144)), seed=3, stream=stream)
+            # per-case schedules, kept only if a whole-batch pilot is faster with them
+            per_case = b.autotune_cases(65_536, seed=3, stream=stream)
+            tuned[prec]["event_schedule_cases"] = sum(1 for c in per_case if c == cls.CLS_SCHED_EVENT)
             dev = timed_runs(b, n, 1, args.steps, args.warmup, flush, torch, stream)
             arms[prec] = (max_over_ranks(pg, dev) / args.steps, [b.tallies(k) for k in range(len(cases))])
             b.close()

@@ -242,6 +242,36 @@ int cls_batch_tallies(cls_handle *h, int case_idx, cls_tallies_t *out);
 /* Number of cases of the handle (1 for cls_create handles). */
 int cls_num_cases(const cls_handle *h);
 
+/* Schedule of one case of a batch: CLS_SCHED_HISTORY, CLS_SCHED_EVENT, or
+ * CLS_SCHED_AUTO (the default: the handle's CLS_OPT_SCHEDULE).  A batch whose
+ * cases have different schedules runs as two persistent launches per
+ * cls_batch_run, one per schedule, each over its own cases (largest estimated
+ * cost first) and both captured in the batch's CUDA graph; the launch options
+ * (block, chunk, bank, events per pass) are the handle's.  Results do not
+ * depend on the schedule: both walk every history draw for draw.  Takes
+ * effect at the next run.  Errors: CLS_E_INVAL. */
+int cls_batch_set_case_schedule(cls_handle *h, int case_idx, int schedule);
+
+/* The schedule case `case_idx` runs under at the next run (its own, else the
+ * handle's; CLS_SCHED_AUTO while the handle's is still to be tuned).
+ * Errors: CLS_E_INVAL. */
+int cls_batch_get_case_schedule(const cls_handle *h, int case_idx, int *schedule);
+
+/* Autotune the schedule of every case: each case alone, on a temporary
+ * single-case twin with the handle's precision and launch options, runs
+ * n_pilot histories (history ids far above any a caller uses, Philox key
+ * `seed`) under the history and under the event schedule, timed with CUDA
+ * events on `stream`; the faster is the case's choice.  A case's preference
+ * alone need not carry over into the batch (a second launch adds its own
+ * tail), so the choices are kept (cls_batch_set_case_schedule) only if a
+ * pilot of the whole batch, n_pilot histories per case on a temporary twin,
+ * runs faster with them than with every case on the handle's schedule;
+ * otherwise every case follows the handle's schedule.  With the handle's
+ * schedule still CLS_SCHED_AUTO the choices are kept untested.  The handle's
+ * tallies are untouched.  Synchronous.
+ * Errors: CLS_E_INVAL, CLS_E_NOMEM, CLS_E_CUDA. */
+int cls_autotune_cases(cls_handle *h, uint64_t n_pilot, uint64_t seed, void *stream);
+
 /* ------------------------------------------------------ per-history outcomes */
 
 /* Outcome codes of cls_record_outcomes: how a history ended (paper Sec. 2:

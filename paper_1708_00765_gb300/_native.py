@@ -44,7 +44,8 @@ CLS_SCHED_EVENT = 2
 EXPORTED = ("cls_create", "cls_set_option", "cls_get_option", "cls_run", "cls_tallies", "cls_raw_tallies",
             "cls_reset", "cls_destroy", "cls_strerror", "cls_trace", "cls_batch_create", "cls_batch_run",
             "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_debug_math", "cls_run_noalloc", "cls_autotune", "cls_finalize_raw",
-            "cls_record_outcomes")
+            "cls_record_outcomes", "cls_batch_set_case_schedule", "cls_batch_get_case_schedule",
+            "cls_autotune_cases")
 
 CLS_NOALLOC_MAX_CASES = 64
 CLS_OUTCOME_REFLECTED = 0
@@ -119,6 +120,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "cls_autotune": ([H, u64, u64, H], i),
         "cls_finalize_raw": ([P(cls_raw_t), P(d), P(u64), d, P(cls_tallies_t)], i),
         "cls_record_outcomes": ([H, H, u64], i),
+        "cls_batch_set_case_schedule": ([H, i, i], i),
+        "cls_batch_get_case_schedule": ([H, i, P(i)], i),
+        "cls_autotune_cases": ([H, u64, u64, H], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -228,6 +232,21 @@ class Problem:
         """cls_autotune: returns the chosen schedule and launch shape."""
         _check(load().cls_autotune(self._h, n_pilot, seed, _stream_handle(stream)), "cls_autotune")
         return {k: self.get_option(k) for k in ("schedule", "block", "chunk", "events_per_pass")}
+
+    def set_case_schedule(self, case: int, schedule):
+        """cls_batch_set_case_schedule: "history", "event" or "auto" (follow the handle's)."""
+        v = VALUES.get(schedule, schedule) if isinstance(schedule, str) else schedule
+        _check(load().cls_batch_set_case_schedule(self._h, case, int(v)), "cls_batch_set_case_schedule")
+
+    def case_schedule(self, case: int) -> int:
+        out = ctypes.c_int()
+        _check(load().cls_batch_get_case_schedule(self._h, case, ctypes.byref(out)), "cls_batch_get_case_schedule")
+        return out.value
+
+    def autotune_cases(self, n_pilot: int, seed: int = 1, stream=None) -> list:
+        """cls_autotune_cases: returns every case's chosen schedule (CLS_SCHED_*)."""
+        _check(load().cls_autotune_cases(self._h, n_pilot, seed, _stream_handle(stream)), "cls_autotune_cases")
+        return [self.case_schedule(k) for k in range(self.params.shape[0])]
 
     def tallies(self, case: int = 0) -> dict:
         nb = self.nbins[case]

@@ -69,6 +69,10 @@ struct cls_handle {
     RunCase *d_runs = nullptr;
     uint8_t *outcome_codes = nullptr;  // caller's per-history outcome buffer (device), or null
     uint64_t outcome_cap = 0;
+    // batches: per-case schedule (CLS_SCHED_AUTO: the handle's CLS_OPT_SCHEDULE).
+    // Cases of different schedules run as two groups, one launch each, with
+    // their own slices of the work list and their own chunk counters.
+    std::vector<int> case_sched;
     cudaEvent_t runs_copied = nullptr;
     std::vector<int> order;  // case indices, largest estimated cost first
     std::vector<uint64_t> next_history;
@@ -86,7 +90,7 @@ struct cls_handle {
     cudaStream_t capture_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
-    uint64_t graph_total_chunks = 0;
+    uint64_t graph_total_chunks[2] = {0, 0};
     int graph_key[8] = {0};
 };
 
@@ -244,6 +248,7 @@ int create_common(const double *params, int ncases, bool batch, cls_handle **out
     h->geom = h->cases[0].d;
     for (const CaseParams &c : h->cases)
         if (c.d != h->geom) h->geom = 0;
+    h->case_sched.assign(ncases, CLS_SCHED_AUTO);
     h->order.resize(ncases);
     std::iota(h->order.begin(), h->order.end(), 0);
     std::stable_sort(h->order.begin(), h->order.end(),
@@ -252,7 +257,7 @@ int create_common(const double *params, int ncases, bool batch, cls_handle **out
     int rc = CLS_OK;
     if (cudaMalloc(&h->d_cases, ncases * sizeof(CaseParams)) != cudaSuccess ||
         cudaMalloc(&h->d_runs, runs_bytes(ncases)) != cudaSuccess ||
-        cudaMalloc(&h->d_chunk_counter, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&h->d_chunk_counter, 2 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&h->h_runs, runs_bytes(ncases)) != cudaSuccess) {
         rc = CLS_E_NOMEM;
     }
@@ -288,22 +293,45 @@ int region_bytes_for(const cls_handle *h) {
 // histories per region, which bounds the FP32 partial sums.
 constexpr int kFp32FlushHistories = 1024;
 
-// Fill the pinned work list for n histories per case and describe the launch.
-int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, LaunchArgs *a) {
+// Schedule of case k: its own, or the handle's.
+int case_schedule(const cls_handle *h, int k) {
+    const int cs = h->case_sched.empty() ? CLS_SCHED_AUTO : h->case_sched[k];
+    return cs != CLS_SCHED_AUTO ? cs : h->opt.schedule;
+}
+
+// One run: a launch per schedule group (one group unless a batch's cases
+// have different schedules).  Group g's cases sit in the work list at
+// runs[off[g] .. off[g] + nruns), largest estimated cost first, with chunk
+// numbers from 0 and chunk counter g.
+struct RunPlan {
+    int ngroups = 0;
+    int sched[2] = {0, 0};
+    LaunchArgs a[2];
+};
+
+// Fill the pinned work list for n histories per case and describe the launches.
+int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, RunPlan *plan) {
     // the previous run's copy of the pinned work list must have completed
     CLS_CUDA(cudaEventSynchronize(h->runs_copied));
     const int nc = (int)h->cases.size();
-    uint64_t chunk_begin = 0;
-    for (int i = 0; i < nc; ++i) {
-        const int k = h->order[i];
-        RunCase &r = h->h_runs[i];
-        r.first = h->next_history[k];
-        r.n = n;
-        r.batch_len = batch_len_for(n, h->nbatch);
-        r.chunk_begin = chunk_begin;
-        r.case_index = k;
-        r.pad = 0;
-        chunk_begin += (n + h->opt.chunk - 1) / h->opt.chunk;
+    const int order_of[2] = {h->opt.schedule, h->opt.schedule == CLS_SCHED_EVENT ? CLS_SCHED_HISTORY : CLS_SCHED_EVENT};
+    int idx = 0, off[2] = {0, 0}, cnt[2] = {0, 0};
+    uint64_t chunks[2] = {0, 0};
+    for (int g = 0; g < 2; ++g) {
+        off[g] = idx;
+        for (int i = 0; i < nc; ++i) {
+            const int k = h->order[i];
+            if (case_schedule(h, k) != order_of[g]) continue;
+            RunCase &r = h->h_runs[idx++];
+            r.first = h->next_history[k];
+            r.n = n;
+            r.batch_len = batch_len_for(n, h->nbatch);
+            r.chunk_begin = chunks[g];
+            r.case_index = k;
+            r.pad = 0;
+            chunks[g] += (n + h->opt.chunk - 1) / h->opt.chunk;
+            ++cnt[g];
+        }
     }
     OutcomeRecord *rec = outcome_record(h->h_runs, nc);
     *rec = OutcomeRecord{nullptr, 0, 0};
@@ -314,21 +342,30 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, LaunchArgs *a) {
         if (n > h->outcome_cap / (uint64_t)nc) return CLS_E_INVAL;
         *rec = OutcomeRecord{h->outcome_codes, h->next_history[0], n};
     }
-    std::memset(a, 0, sizeof(*a));
-    a->cases = h->d_cases;
-    a->runs = h->d_runs;
-    a->nruns = nc;
-    a->chunk = (uint32_t)h->opt.chunk;
-    a->total_chunks = chunk_begin;
-    a->chunk_counter = h->d_chunk_counter;
-    a->t = Tallies{h->d_flux, h->d_stats, h->d_counters, h->nbatch, h->nbins_stride};
-    a->seed = seed;
-    a->rk = make_round_keys(seed);
-    a->max_events = h->opt.max_events;
-    a->region_bytes = region_bytes_for(h);
-    a->dif = region_dif_for(h) ? 1 : 0;
-    a->flush_every = (h->opt.precision == CLS_PREC_FP32) ? kFp32FlushHistories : 0;
-    a->outcomes = outcome_record(h->d_runs, nc);
+    LaunchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.cases = h->d_cases;
+    a.chunk = (uint32_t)h->opt.chunk;
+    a.t = Tallies{h->d_flux, h->d_stats, h->d_counters, h->nbatch, h->nbins_stride};
+    a.seed = seed;
+    a.rk = make_round_keys(seed);
+    a.max_events = h->opt.max_events;
+    a.region_bytes = region_bytes_for(h);
+    a.dif = region_dif_for(h) ? 1 : 0;
+    a.flush_every = (h->opt.precision == CLS_PREC_FP32) ? kFp32FlushHistories : 0;
+    a.outcomes = outcome_record(h->d_runs, nc);
+    plan->ngroups = 0;
+    for (int g = 0; g < 2; ++g) {
+        if (cnt[g] == 0) continue;
+        LaunchArgs &ag = plan->a[plan->ngroups];
+        ag = a;
+        ag.runs = h->d_runs + off[g];
+        ag.nruns = cnt[g];
+        ag.total_chunks = chunks[g];
+        ag.chunk_counter = h->d_chunk_counter + plan->ngroups;
+        plan->sched[plan->ngroups] = order_of[g];
+        ++plan->ngroups;
+    }
     return CLS_OK;
 }
 
@@ -349,8 +386,8 @@ struct Shape {
     uint32_t bank_slots;  // event schedule: slots per block and buffer
 };
 
-int tracker_shape(cls_handle *h, int region_bytes, Shape *out) {
-    const bool event = h->opt.schedule == CLS_SCHED_EVENT;
+int tracker_shape(cls_handle *h, int region_bytes, int sched, Shape *out) {
+    const bool event = sched == CLS_SCHED_EVENT;
     const bool fp64 = h->opt.precision == CLS_PREC_FP64;
     // each warp owns two tally regions; wide meshes get fewer warps per block
     const size_t per_warp = 2 * (size_t)region_bytes;
@@ -379,8 +416,8 @@ int tracker_shape(cls_handle *h, int region_bytes, Shape *out) {
 
 // Event schedule: make sure the particle bank (grid warps x 2 buffers x
 // slots x fields x 16 B) is allocated.  Done before any graph capture.
-int ensure_bank(cls_handle *h, const Shape &sh) {
-    if (h->opt.schedule != CLS_SCHED_EVENT) return CLS_OK;
+int ensure_bank(cls_handle *h, int sched, const Shape &sh) {
+    if (sched != CLS_SCHED_EVENT) return CLS_OK;
     const size_t need = (size_t)sh.grid * (sh.block / 32) * 2 * sh.bank_slots *
                         (size_t)event_bank_fields(h->opt.precision) * 16;
     if (need <= h->bank_bytes) return CLS_OK;
@@ -396,10 +433,10 @@ int ensure_bank(cls_handle *h, const Shape &sh) {
     return CLS_OK;
 }
 
-int launch_tracker(cls_handle *h, LaunchArgs a, const Shape &sh, cudaStream_t s) {
+int launch_tracker(cls_handle *h, LaunchArgs a, int sched, const Shape &sh, cudaStream_t s) {
     cudaError_t e;
     const bool fp64 = h->opt.precision == CLS_PREC_FP64;
-    if (h->opt.schedule == CLS_SCHED_EVENT) {
+    if (sched == CLS_SCHED_EVENT) {
         a.bank = h->d_bank;
         a.bank_slots = sh.bank_slots;
         a.events_per_pass = (uint32_t)h->opt.events_per_pass;
@@ -790,19 +827,21 @@ int cls_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
         if (arc) return arc;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    LaunchArgs a;
-    int rc = prepare_run(h, n, seed, &a);
+    RunPlan plan;
+    int rc = prepare_run(h, n, seed, &plan);
     if (rc) return rc;
-    Shape sh;
-    rc = tracker_shape(h, a.region_bytes, &sh);
-    if (!rc) rc = ensure_bank(h, sh);
+    Shape sh[2];
+    for (int g = 0; g < plan.ngroups && !rc; ++g) {
+        rc = tracker_shape(h, plan.a[g].region_bytes, plan.sched[g], &sh[g]);
+        if (!rc) rc = ensure_bank(h, plan.sched[g], sh[g]);
+    }
     if (rc) return rc;
     rc = record_pair(h, s, true);
     if (rc) return rc;
     CLS_CUDA(cudaMemcpyAsync(h->d_runs, h->h_runs, runs_bytes(h->cases.size()), cudaMemcpyHostToDevice, s));
     CLS_CUDA(cudaEventRecord(h->runs_copied, s));
-    CLS_CUDA(cudaMemsetAsync(h->d_chunk_counter, 0, sizeof(unsigned long long), s));
-    rc = launch_tracker(h, a, sh, s);
+    CLS_CUDA(cudaMemsetAsync(h->d_chunk_counter, 0, 2 * sizeof(unsigned long long), s));
+    for (int g = 0; g < plan.ngroups && !rc; ++g) rc = launch_tracker(h, plan.a[g], plan.sched[g], sh[g], s);
     if (rc) return rc;
     rc = record_pair(h, s, false);
     if (rc) return rc;
@@ -820,24 +859,31 @@ int cls_batch_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
         if (arc) return arc;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    LaunchArgs a;
-    int rc = prepare_run(h, n, seed, &a);
+    RunPlan plan;
+    int rc = prepare_run(h, n, seed, &plan);
     if (rc) return rc;
-    // capture {counter reset, tracker} once per (launch shape, seed); later calls only
-    // refresh the work list (history ranges) before replaying the graph
+    // capture {counter reset, one tracker per schedule group} once per (launch
+    // shape, seed, grouping); later calls only refresh the work list (history
+    // ranges) before replaying the graph
     const int key[8] = {h->opt.precision, h->opt.schedule, h->opt.block, h->opt.chunk,
                         (int)h->opt.max_events, h->opt.blocks_per_sm, (int)(seed & 0x7fffffff), (int)(seed >> 31)};
-    if (h->graph_exec && (a.total_chunks != h->graph_total_chunks || std::memcmp(key, h->graph_key, sizeof(key))))
+    const uint64_t tc[2] = {plan.a[0].total_chunks, plan.ngroups > 1 ? plan.a[1].total_chunks : 0};
+    if (h->graph_exec && (tc[0] != h->graph_total_chunks[0] || tc[1] != h->graph_total_chunks[1] ||
+                          std::memcmp(key, h->graph_key, sizeof(key))))
         destroy_graph(h);
     if (!h->graph_exec) {
-        Shape sh;
-        rc = tracker_shape(h, a.region_bytes, &sh);
-        if (!rc) rc = ensure_bank(h, sh);
+        Shape sh[2];
+        for (int g = 0; g < plan.ngroups && !rc; ++g) {
+            rc = tracker_shape(h, plan.a[g].region_bytes, plan.sched[g], &sh[g]);
+            if (!rc) rc = ensure_bank(h, plan.sched[g], sh[g]);
+        }
         if (rc) return rc;
         if (!h->capture_stream) CLS_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
         CLS_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaMemsetAsync(h->d_chunk_counter, 0, sizeof(unsigned long long), h->capture_stream);
-        int lrc = (e == cudaSuccess) ? launch_tracker(h, a, sh, h->capture_stream) : CLS_E_CUDA;
+        cudaError_t e = cudaMemsetAsync(h->d_chunk_counter, 0, 2 * sizeof(unsigned long long), h->capture_stream);
+        int lrc = (e == cudaSuccess) ? CLS_OK : CLS_E_CUDA;
+        for (int g = 0; g < plan.ngroups && !lrc; ++g)
+            lrc = launch_tracker(h, plan.a[g], plan.sched[g], sh[g], h->capture_stream);
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
         if (lrc || e2 != cudaSuccess) {
@@ -850,7 +896,8 @@ int cls_batch_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
             destroy_graph(h);
             return CLS_E_CUDA;
         }
-        h->graph_total_chunks = a.total_chunks;
+        h->graph_total_chunks[0] = tc[0];
+        h->graph_total_chunks[1] = tc[1];
         std::memcpy(h->graph_key, key, sizeof(key));
     }
     rc = record_pair(h, s, true);
@@ -863,6 +910,94 @@ int cls_batch_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
     h->last_stream = s;
     account_run(h, n);
     return CLS_OK;
+}
+
+int cls_batch_set_case_schedule(cls_handle *h, int case_idx, int schedule) {
+    if (!h || case_idx < 0 || case_idx >= (int)h->cases.size()) return CLS_E_INVAL;
+    if (schedule != CLS_SCHED_AUTO && schedule != CLS_SCHED_HISTORY && schedule != CLS_SCHED_EVENT) return CLS_E_INVAL;
+    if (h->case_sched[case_idx] != schedule) {
+        h->case_sched[case_idx] = schedule;
+        destroy_graph(h);  // the grouping of the captured launches changes
+    }
+    return CLS_OK;
+}
+
+int cls_batch_get_case_schedule(const cls_handle *h, int case_idx, int *schedule) {
+    if (!h || !schedule || case_idx < 0 || case_idx >= (int)h->cases.size()) return CLS_E_INVAL;
+    *schedule = case_schedule(h, case_idx);
+    return CLS_OK;
+}
+
+int cls_autotune_cases(cls_handle *h, uint64_t n_pilot, uint64_t seed, void *stream) {
+    if (!h || n_pilot == 0 || n_pilot > (1ull << 32)) return CLS_E_INVAL;
+    CLS_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return CLS_E_CUDA;
+    }
+    const uint64_t base = 1ull << 61;  // pilot history ids, far from a caller's
+    const int nc = (int)h->cases.size();
+    std::vector<int> chosen(nc, CLS_SCHED_AUTO);
+    int rc = CLS_OK;
+    for (int k = 0; k < nc && !rc; ++k) {
+        cls_handle *t = nullptr;
+        rc = create_common(h->params.data() + 9 * (size_t)k, 1, false, &t);
+        if (rc) break;
+        t->opt = h->opt;
+        t->cases[0].case_id = h->cases[k].case_id;  // the case's own random numbers
+        rc = cudaMemcpy(t->d_cases, t->cases.data(), sizeof(CaseParams), cudaMemcpyHostToDevice) == cudaSuccess
+                 ? CLS_OK : CLS_E_CUDA;
+        float ms[2] = {0.f, 0.f};
+        const int scheds[2] = {CLS_SCHED_HISTORY, CLS_SCHED_EVENT};
+        for (int i = 0; i < 2 && !rc; ++i) {
+            t->opt.schedule = scheds[i];
+            for (int rep = 0; rep < 2 && !rc; ++rep) {
+                t->next_history[0] = base + (uint64_t)(2 * i + rep) * n_pilot;
+                if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) rc = CLS_E_CUDA;
+                if (!rc) rc = cls_run(t, rep ? n_pilot : std::max<uint64_t>(n_pilot / 4, 1), seed, stream);
+                if (!rc && rep == 1 && cudaEventRecord(e1, s) != cudaSuccess) rc = CLS_E_CUDA;
+            }
+            if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms[i], e0, e1) != cudaSuccess))
+                rc = CLS_E_CUDA;
+        }
+        cls_destroy(t);
+        if (!rc) chosen[k] = ms[1] < ms[0] ? CLS_SCHED_EVENT : CLS_SCHED_HISTORY;
+    }
+    // a case's preference alone need not carry over into the batch, where a
+    // second launch adds its own tail: keep the per-case grouping only if a
+    // pilot of the whole batch runs faster with it than with every case on
+    // the handle's schedule
+    bool mixed = false;
+    for (int k = 0; k < nc; ++k) mixed |= chosen[k] != h->opt.schedule;
+    float batch_ms[2] = {0.f, 0.f};
+    if (!rc && mixed && h->opt.schedule != CLS_SCHED_AUTO) {
+        cls_handle *t = nullptr;
+        rc = create_common(h->params.data(), nc, true, &t);
+        if (!rc) {
+            t->opt = h->opt;
+            for (int i = 0; i < 2 && !rc; ++i) {
+                for (int k = 0; k < nc; ++k) t->case_sched[k] = i ? chosen[k] : CLS_SCHED_AUTO;
+                destroy_graph(t);
+                for (int rep = 0; rep < 2 && !rc; ++rep) {
+                    for (auto &nh : t->next_history) nh = base + (uint64_t)(8 + 2 * i + rep) * n_pilot;
+                    if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) rc = CLS_E_CUDA;
+                    if (!rc) rc = cls_batch_run(t, rep ? n_pilot : std::max<uint64_t>(n_pilot / 4, 1), seed, stream);
+                    if (!rc && rep == 1 && cudaEventRecord(e1, s) != cudaSuccess) rc = CLS_E_CUDA;
+                }
+                if (!rc && (cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&batch_ms[i], e0, e1) != cudaSuccess))
+                    rc = CLS_E_CUDA;
+            }
+            cls_destroy(t);
+        }
+        if (!rc && !(batch_ms[1] < batch_ms[0])) mixed = false;
+    }
+    for (int k = 0; k < nc && !rc; ++k) rc = cls_batch_set_case_schedule(h, k, mixed ? chosen[k] : CLS_SCHED_AUTO);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 int cls_record_outcomes(cls_handle *h, uint8_t *d_codes, uint64_t capacity) {

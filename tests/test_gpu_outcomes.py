@@ -63,6 +63,23 @@ def test_batch_outcomes_match_oracle_after_graph_replay():
         assert np.array_equal(codes[k], ref), k
 
 
+def test_batch_outcomes_with_mixed_case_schedules():
+    params = workloads.batch_sweep(8, seed=7, nbins=20)
+    n = 800
+    prob = cls.Problem(params, batch=True)
+    prob.set_option("schedule", "history")
+    for k in (1, 2, 5):
+        prob.set_case_schedule(k, "event")
+    buf = torch.full((8 * n,), 255, dtype=torch.uint8, device="cuda")
+    prob.record_outcomes(buf.data_ptr(), buf.numel())
+    prob.run(n, 12)
+    torch.cuda.synchronize()
+    codes = buf.cpu().numpy().reshape(8, n)
+    prob.close()
+    for k in range(8):
+        assert np.array_equal(codes[k], oracle.outcomes(ocase(params[k]), 12, 0, n, case_id=k)), k
+
+
 def test_event_cap_is_recorded_as_capped():
     codes, _, raw = gpu_codes(workloads.BOX_L10, 2000, 3, max_events=4)
     assert set(np.unique(codes).tolist()) <= {0, 1, 2, 3}

@@ -292,6 +292,63 @@ def test_batch_cases_match_oracle_exactly():
     prob.close()
 
 
+def _batch_exact(prob, params, seed, runs):
+    """Every case's counts equal the oracle's over the given consecutive runs."""
+    for k in range(params.shape[0]):
+        raw_g = prob.raw_tallies(k)
+        first = 0
+        tot = {key: 0 for key in COUNT_KEYS}
+        sum_t = 0.0
+        for n in runs:
+            o = oracle.run(ocase(params[k]), seed, first, n, case_id=k)
+            for key in COUNT_KEYS:
+                tot[key] = max(tot[key], o[key]) if key == "max_events" else tot[key] + o[key]
+            sum_t += o["sum_t"]
+            first += n
+        for key in COUNT_KEYS:
+            assert raw_g[GPU_KEYS.get(key, key)] == tot[key], (k, key)
+        assert raw_g["sum_t"] == pytest.approx(sum_t, rel=RTOL)
+
+
+def test_batch_with_mixed_case_schedules_matches_oracle_exactly():
+    """Cases on the history and on the event schedule in one batch: two launches per
+    replay of the captured graph, every case bit-exact against the oracle."""
+    params = workloads.batch_sweep(12, seed=7, nbins=20)
+    prob = cls.Problem(params, batch=True)
+    prob.set_option("schedule", "history")
+    for k in range(0, 12, 2):
+        prob.set_case_schedule(k, "event")
+    assert [prob.case_schedule(k) for k in range(12)] == [cls.CLS_SCHED_EVENT, cls.CLS_SCHED_HISTORY] * 6
+    prob.run(2000, 9)
+    prob.run(1000, 9)  # graph replay with a new history range
+    _batch_exact(prob, params, 9, [2000, 1000])
+    prob.close()
+
+
+def test_batch_with_every_case_on_the_other_schedule():
+    params = workloads.batch_sweep(6, seed=7, nbins=20)
+    prob = cls.Problem(params, batch=True)
+    prob.set_option("schedule", "history")
+    for k in range(6):
+        prob.set_case_schedule(k, "event")
+    prob.run(1500, 4)
+    _batch_exact(prob, params, 4, [1500])
+    with pytest.raises(cls.ClsError):
+        prob.set_case_schedule(6, "event")
+    prob.close()
+
+
+def test_autotune_cases_keeps_results_exact():
+    params = workloads.batch_sweep(8, seed=7, nbins=20)
+    prob = cls.Problem(params, batch=True)
+    prob.set_option("schedule", "history")
+    chosen = prob.autotune_cases(4096, seed=3)
+    assert len(chosen) == 8 and set(chosen) <= {cls.CLS_SCHED_HISTORY, cls.CLS_SCHED_EVENT}
+    prob.run(1500, 6)
+    _batch_exact(prob, params, 6, [1500])
+    prob.close()
+
+
 def test_fp32_batch_within_combined_sigma_of_oracle_per_case():
     """FP32-tracking batch, case by case, against the FP64 oracle on an independent seed
     and a history-id subset: R, T, A and <phi> within 4.5 combined standard errors
