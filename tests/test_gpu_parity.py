@@ -338,6 +338,20 @@ def test_batch_with_every_case_on_the_other_schedule():
     prob.close()
 
 
+def test_autotune_cases_with_the_handle_schedule_still_automatic():
+    """With the handle's schedule still to be tuned, every case keeps its own choice;
+    the first run then tunes the handle's launch shape, and results stay exact."""
+    params = workloads.batch_sweep(6, seed=7, nbins=20)
+    prob = cls.Problem(params, batch=True)
+    prob.set_option("schedule", "auto")
+    chosen = prob.autotune_cases(4096, seed=3)
+    assert set(chosen) <= {cls.CLS_SCHED_HISTORY, cls.CLS_SCHED_EVENT}
+    prob.run(1200, 8)
+    assert [prob.case_schedule(k) for k in range(6)] == chosen
+    _batch_exact(prob, params, 8, [1200])
+    prob.close()
+
+
 def test_autotune_cases_keeps_results_exact():
     params = workloads.batch_sweep(8, seed=7, nbins=20)
     prob = cls.Problem(params, batch=True)
