@@ -69,7 +69,9 @@ extern "C" {
 #define CLS_OPT_PRECISION 1     /* CLS_PREC_FP64 (default) or CLS_PREC_FP32                 */
 #define CLS_OPT_SCHEDULE 2      /* CLS_SCHED_HISTORY (default), CLS_SCHED_EVENT, CLS_SCHED_AUTO */
 #define CLS_OPT_BLOCK 3         /* threads per block, multiple of 32 in [32, 256]; the FP64
-                                   history tracker uses at most 128 (its launch bounds)      */
+                                   history tracker uses at most 128 and the FP32 one for the
+                                   3D box on meshes up to 251 bins at most 224 (their launch
+                                   bounds)                                                   */
 #define CLS_OPT_CHUNK 4         /* histories a warp claims at once: 32, 64, ..., 1024       */
 #define CLS_OPT_NBATCH 5        /* statistics batches per run, 2..1024 (default 64)         */
 #define CLS_OPT_MAX_EVENTS 6    /* per-history event cap, 1..2^28 (default 1e8)             */

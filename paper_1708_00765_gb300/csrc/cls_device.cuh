@@ -1073,7 +1073,8 @@ __device__ __forceinline__ int find_run(const LaunchArgs &a, uint64_t ch) {
 // interior-bin difference array, 3 per SM (80 registers) without it, where the
 // 64-register build spilled about 200 bytes a thread (measured on a 500-bin
 // diffusive box: 33% faster at 3; the difference-array kernels are 3% slower
-// at 3).  FP64 blocks of at most kHistoryBlockFp64 = 128 threads, 5 per SM
+// at 3); the 3D box with the difference array takes 4 blocks of 224 threads
+// (history_threads_fp32).  FP64 blocks of at most kHistoryBlockFp64 = 128 threads, 5 per SM
 // (102 registers, 20 warps), 6 (85 registers, 24 warps) for the
 // one-dimensional walks (rod, slab, x-projected box), whose state fits: the
 // FP64 walk is latency-bound, and more resident warps hide its
@@ -1085,7 +1086,7 @@ struct HistoryBounds {
 };
 template <int G, bool DIF>
 struct HistoryBounds<float, G, DIF> {
-    static constexpr int threads = 256, blocks = DIF ? 4 : 3;
+    static constexpr int threads = history_threads_fp32(G, DIF), blocks = DIF ? 4 : 3;
 };
 
 template <typename P, int G, bool DIF = false>

@@ -393,7 +393,8 @@ int tracker_shape(cls_handle *h, int region_bytes, int sched, Shape *out) {
     const size_t per_warp = 2 * (size_t)region_bytes;
     const int fit_warps = (int)std::min<size_t>(kMaxSmemPerBlock / per_warp, 8);
     if (fit_warps < 1) return CLS_E_INVAL;
-    const int cap_warps = (!event && fp64) ? kHistoryBlockFp64 / 32 : 8;  // the FP64 history tracker's bound
+    // the history trackers' launch bounds
+    const int cap_warps = event ? 8 : fp64 ? kHistoryBlockFp64 / 32 : history_threads_fp32(h->geom, region_dif_for(h)) / 32;
     const int block = 32 * std::min(std::min(h->opt.block / 32, fit_warps), cap_warps);
     const size_t smem = (size_t)(block / 32) * per_warp;
     int bps = h->opt.blocks_per_sm;
