@@ -46,7 +46,7 @@ BOX_WORKLOAD = "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, cosine inciden
 # elementary functions in the integer pipes and is bound by issue and latency,
 # not by the FP64 pipe.
 FP64_WARP_INST_PER_EVENT = 76.0
-FP32_WARP_INST_PER_EVENT = 21.2
+FP32_WARP_INST_PER_EVENT = 19.7
 FP64_FLOP_PER_EVENT = 148.8
 # The diffusive workload's FP32 kernels (500 bins: no difference array).
 DIFFUSIVE_WARP_INST_PER_EVENT = {"history": 20.3, "event": 20.7}
