@@ -781,17 +781,21 @@ __device__ __forceinline__ double *region_stats(unsigned char *region, int nbs) 
     return reinterpret_cast<double *>(region + region_bins_bytes((int)sizeof(typename Real<P>::Bin), nbs));
 }
 
+// The history's track length t and t^2 into this lane's own copy of the
+// region's statistics (no atomics), in the region's precision: FP64 regions in
+// double; FP32 regions in float, as their bins (flushed to FP64 every few
+// hundred histories), so no conversion reaches the narrow FP64 pipe.
 template <typename P>
 __device__ __forceinline__ void finish_history(unsigned char *region, int nbs, const History<P> &s, int lane) {
-    const double t0 = (double)s.track0;
-    const double t1 = (double)s.track1;
-    const double t = t0 + t1;
     using B = typename Real<P>::Bin;
-    B *ls = region_lane_stats<P>(region, nbs) + lane;  // this lane's own copy: no atomics
-    ls[32 * S_T] += (B)t;
-    ls[32 * S_T2] += (B)(t * t);
-    ls[32 * S_TRACK0] += (B)t0;
-    ls[32 * S_TRACK1] += (B)t1;
+    const B t0 = (B)s.track0;
+    const B t1 = (B)s.track1;
+    const B t = t0 + t1;
+    B *ls = region_lane_stats<P>(region, nbs) + lane;
+    ls[32 * S_T] += t;
+    ls[32 * S_T2] += t * t;
+    ls[32 * S_TRACK0] += t0;
+    ls[32 * S_TRACK1] += t1;
 }
 
 // Outcome and event counters of the lanes whose history ended this step
