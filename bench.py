@@ -174,17 +174,19 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ oracle timing
-def oracle_rate(params, seconds_target: float, cores: int, first: int = 0, detail: dict | None = None):
-    """Time the FP64 oracle on a bounded sample of the workload over `cores` processes.
-    `detail`, if given, receives the single-process pilot's rate, the events per
-    second of the sample and the time the full workload would take (extrapolated)."""
+def oracle_rate(params, seconds_target: float, cores: int, first: int = 0, detail: dict | None = None,
+                n_fixed: int | None = None):
+    """Time the FP64 oracle on a bounded sample of the workload over `cores` processes
+    (n_fixed histories if given, else about seconds_target of work).  `detail`, if
+    given, receives the single-process pilot's rate and the events per second of the
+    sample."""
     import oracle
     case = oracle.Case(*params[:7], int(params[7]), int(params[8]))
     t0 = time.perf_counter()
     pilot = 2000
     oracle.run(case, 1, first, pilot)
     rate1 = pilot / (time.perf_counter() - t0)
-    n = max(cores * 2048, int(rate1 * cores * seconds_target))
+    n = n_fixed or max(cores * 2048, int(rate1 * cores * seconds_target))
     t0 = time.perf_counter()
     raw = oracle.run_parallel(case, 1, first, n, workers=cores)
     dt = time.perf_counter() - t0
@@ -203,7 +205,7 @@ def reference_arm(args, rank, world, pg):
     rates = []
     detail = {}
     for i in range(args.warmup + args.steps):
-        r, n, dt, used = oracle_rate(params, 4.0, cores, first=i * 10_000_000, detail=detail)
+        r, n, dt, used = oracle_rate(params, 4.0, cores, first=i * 10_000_000, detail=detail, n_fixed=args.histories)
         if i >= args.warmup:
             rates.append((r, n, dt))
     value = sum(r for r, _, _ in rates) / len(rates)
