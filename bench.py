@@ -48,6 +48,9 @@ BOX_WORKLOAD = "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, cosine inciden
 FP64_WARP_INST_PER_EVENT = 76.0
 FP32_WARP_INST_PER_EVENT = 19.4
 FP64_FLOP_PER_EVENT = 148.8
+# The FP64 box kernel's FP64 pipe busy fraction (ncu sm__pipe_fp64_cycles_active,
+# `--set full` of a 1e7-history launch): its second limit beside the issue rate.
+FP64_PIPE_ACTIVE = 0.60
 # The diffusive workload's FP32 kernels (500 bins: no difference array).
 DIFFUSIVE_WARP_INST_PER_EVENT = {"history": 20.2, "event": 20.7}
 # The batched sweep's FP32 kernel (history_kernel<float, 0, 1>, 256 cases x
@@ -608,7 +611,8 @@ def main():
                          "work": f"{FP64_WARP_INST_PER_EVENT} warp instructions/event x {r['events_per_launch']:.4g} events/launch",
                          "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} issue/clk x {clk_mhz} MHz (sampled)",
                          "fp64_equivalent_tflops": FP64_FLOP_PER_EVENT * ev_s / 1e12,
-                         "fp64_peak_tflops": SM_COUNT * DFMA_PER_SM_CLK * 2 * clk_mhz * 1e6 / 1e12}
+                         "fp64_peak_tflops": SM_COUNT * DFMA_PER_SM_CLK * 2 * clk_mhz * 1e6 / 1e12,
+                         "fp64_pipe_active_ncu": FP64_PIPE_ACTIVE}
     if "fp32" in results:
         r = results["fp32"]
         achieved = FP32_WARP_INST_PER_EVENT * r["events_per_launch"] / (r["launch_ms"] * 1e-3) / 1e12
