@@ -64,3 +64,24 @@ def test_workload_generator_is_deterministic():
     assert set(a[:, 7]) <= {1.0, 3.0} and set(a[:, 6]) <= {0.1, 1.0, 10.0}
     assert a[:, 0:2].min() >= 0.02 and a[:, 0:2].max() <= 10
     assert a[:, 2:4].min() >= 0.05 and a[:, 2:4].max() <= 10
+
+
+def test_binding_constants_equal_the_header():
+    """Every CLS_* value the Python binding uses is the one include/cls.h defines, and
+    every ctypes signature has the declared number of parameters."""
+    from paper_1708_00765_gb300 import _native
+    with open(os.path.join(ROOT, "include", "cls.h")) as f:
+        text = f.read()
+    defines = {m.group(1): int(m.group(2)) for m in
+               re.finditer(r"#define\s+(CLS_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text)}
+    bound = {k: v for k, v in vars(_native).items() if k.startswith("CLS_") and isinstance(v, int)}
+    assert len(bound) >= 30
+    for k, v in bound.items():
+        assert k in defines, k
+        assert defines[k] == v, k
+    code = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lib = _native.load()
+    for m in re.finditer(r"\b(cls_[a-z_]+)\s*\(([^)]*)\)\s*;", code):
+        params = [p for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+        fn = getattr(lib, m.group(1))
+        assert len(fn.argtypes) == len(params), m.group(1)
