@@ -35,9 +35,7 @@ BOX_WORKLOAD = "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, cosine inciden
 # Work per event of the benchmark workloads' kernels, for the issue-rate
 # roofline (152 SMs x 4 warp instructions per clock): warp instructions per
 # event counted by ncu (smsp__inst_executed.sum / events, one pass) on the
-# full-size launch of the current kernels (1e8 histories;
-# profiles/history_kernel_box_L10.md, profiles/history_kernel_batch_sweep.md,
-# profiles/event_kernel_diffusive.md),
+# full-size launch of the current kernels (1e8 histories; the sweep's 256 x 1e7),
 # updated with each capture of a changed kernel.  A small launch counts more
 # per event: its heavy-tailed last histories run in nearly empty warps.
 # FP64_FLOP_PER_EVENT: the same event's FP64 arithmetic evaluated directly in
