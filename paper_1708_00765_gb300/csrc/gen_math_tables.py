@@ -101,7 +101,8 @@ def two_pi_q60() -> int:
     return int((2 * pi() * Decimal(2) ** 60).to_integral_value())
 
 
-def main() -> None:
+def render() -> str:
+    """The text of cls_math_tables.h."""
     logs, ln2 = log_table()
     sc = sincos_table()
     M64 = (1 << 64) - 1
@@ -140,8 +141,12 @@ def main() -> None:
     for s_, c_ in sc:
         out.append(f"    {{{s_}ll, {c_}ll}},")
     out += ["};", "", "}  // namespace cls", ""]
+    return "\n".join(out)
+
+
+def main() -> None:
     with open(os.path.join(HERE, "cls_math_tables.h"), "w") as fh:
-        fh.write("\n".join(out))
+        fh.write(render())
 
 
 if __name__ == "__main__":

@@ -194,3 +194,13 @@ def test_sqrt_within_one_ulp(intmath):
         ref = Fraction(math.isqrt(x << 200), 2**100) / 2 ** (sc // 2)
         worst = max(worst, float(abs(Fraction(v) - ref) / Fraction(math.ulp(float(ref)))))
     assert worst <= 1.0, worst
+
+
+def test_committed_tables_are_the_generators():
+    """cls_math_tables.h is exactly what gen_math_tables.py computes in decimal arithmetic."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("gen_math_tables", os.path.join(CSRC, "gen_math_tables.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    with open(os.path.join(CSRC, "cls_math_tables.h")) as f:
+        assert f.read() == gen.render()
