@@ -141,8 +141,8 @@ typedef struct {
  *                    CLS_GEOM_BOX_X
  *   nbins            uniform flux bins along x, 1..4096
  * Selects the current CUDA device, allocates the device tallies (library-
- * owned, freed by cls_destroy) and zeroes them.  Flux tallies (cases x
- * statistics batches x bins) above 2^32 doubles are refused (CLS_E_NOMEM).
+ * owned, freed by cls_destroy; see cls_bind_workspace for caller-owned
+ * memory) and zeroes them.
  * Errors: CLS_E_INVAL, CLS_E_NOMEM, CLS_E_NODEVICE, CLS_E_CUDA. */
 int cls_create(double sigma0, double sigma1, double lambda0, double lambda1, double c0, double c1,
                double L, int d, int nbins, cls_handle **out);
@@ -323,8 +323,10 @@ int cls_debug_math(const uint64_t *k, int n, double *ln1m, double *sin2pi, doubl
 
 /* ------------------------------------------------- allocation-free run */
 
-/* Largest number of cases one cls_run_noalloc call takes. */
+/* Largest number of cases one cls_run_noalloc call takes, and its largest
+ * nbins_stride. */
 #define CLS_NOALLOC_MAX_CASES 64
+#define CLS_NOALLOC_MAX_STRIDE 4096
 
 /* cls_run_noalloc -- run the FP64 history-based tracker without allocating
  * any device memory.  The paper has no counterpart: this exists for callers
@@ -345,18 +347,24 @@ int cls_debug_math(const uint64_t *k, int n, double *ln1m, double *sin2pi, doubl
  *   d_counters [ncases][9] u64: reflected, transmitted, absorbed, collisions,
  *              interface crossings, lateral reflections, events, capped
  *              histories (all added), longest history in events (maximum).
- * nbatch is 1..1024, nbins_stride >= the largest nbins.  Results equal
- * cls_run's for the same seed and history range (default options).
+ * nbatch is 1..1024, nbins_stride is the largest nbins .. CLS_NOALLOC_MAX_STRIDE.
+ * Results equal cls_run's for the same seed and history range (default
+ * options; per-history event cap 1e8).  The call is asynchronous, so it cannot
+ * report capped histories as CLS_E_EVENT_LIMIT: they show in d_counters[k][7].
  *
- * Scratch (case parameters, work list, work counter; about 12 KB) lives in a
+ * Scratch (case parameters, work list, work counter; about 16 KB) lives in a
  * static device array that every GPU loading the library holds until the
  * process exits.  The first call on each device looks up that array's device
- * address (with the device current); make that first call before any stream
- * capture.  All calls share the array and each call rewrites it, so calls that
- * overlap on the GPU race and must be serialised by the caller (one stream).
- * Asynchronous on `stream`.
- * Errors: CLS_E_INVAL (NULL buffer, ncases or n out of range, invalid case,
- * nbins_stride too small), CLS_E_CUDA. */
+ * address (with the device current) and keeps it for the life of the process;
+ * make that first call before any stream capture, and do not call this entry
+ * point again after cudaDeviceReset.  Each call hands its cases and work list
+ * to a small set-up kernel as kernel arguments, which writes them into the
+ * array ahead of the tracker on `stream`; nothing is read from host memory
+ * after the call returns.  All calls share the array and each call rewrites
+ * it, so calls that overlap on the GPU race and must be serialised by the
+ * caller (one stream).  Asynchronous on `stream`.
+ * Errors: CLS_E_INVAL (NULL buffer, ncases, n, nbatch or nbins_stride out of
+ * range, invalid case), CLS_E_CUDA. */
 int cls_run_noalloc(const double *params, int ncases, uint64_t first, uint64_t n, uint64_t seed, int nbatch,
                     int nbins_stride, double *d_flux, double *d_stats, unsigned long long *d_counters,
                     void *stream);

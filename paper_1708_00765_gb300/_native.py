@@ -48,6 +48,7 @@ EXPORTED = ("cls_create", "cls_set_option", "cls_get_option", "cls_run", "cls_ta
             "cls_autotune_cases")
 
 CLS_NOALLOC_MAX_CASES = 64
+CLS_NOALLOC_MAX_STRIDE = 4096
 CLS_OUTCOME_REFLECTED = 0
 CLS_OUTCOME_TRANSMITTED = 1
 CLS_OUTCOME_ABSORBED = 2

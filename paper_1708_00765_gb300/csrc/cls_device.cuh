@@ -15,6 +15,7 @@
 // The collision draw is consumed even when Sigma_m = 0.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -33,6 +34,21 @@ __host__ cudaError_t occupancy_with_smem(int *blocks_per_sm, K kernel, int block
     const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, block, smem);
+}
+
+// The opt-in to 200 KB of dynamic shared memory, set once per device and
+// kernel (`done` holds one bit per device index below 64, set after a
+// successful call; two threads racing on it only repeat the call).
+template <typename K>
+__host__ cudaError_t ensure_smem_optin(K kernel, std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
 }
 
 // ------------------------------------------------- FP64 logarithm, sine/cosine
@@ -863,7 +879,7 @@ __device__ __forceinline__ void warp_count(unsigned char *regions, int rbytes, i
 // shuffle search over the warp's inclusive prefix sum of the interior counts.
 template <typename P>
 __device__ __forceinline__ void spread_interior(unsigned char *regions, int rbytes, int lreg, double *gflux,
-                                                uint32_t goff, int k0, P c, int ni, int lane) {
+                                                uint64_t goff, int k0, P c, int ni, int lane) {
     using B = typename Real<P>::Bin;
     int incl = ni;
 #pragma unroll
@@ -886,7 +902,7 @@ __device__ __forceinline__ void spread_interior(unsigned char *regions, int rbyt
         const int ob = __shfl_sync(CLS_FULL_MASK, base_bin, o);
         const P oc = __shfl_sync(CLS_FULL_MASK, c, o);
         const int oreg = __shfl_sync(CLS_FULL_MASK, lreg, o);
-        uint32_t ogoff = 0;
+        uint64_t ogoff = 0;
         if (any_global) ogoff = __shfl_sync(CLS_FULL_MASK, goff, o);
         if (t < total) {
             if (oreg < 2) {
@@ -913,7 +929,7 @@ __device__ __forceinline__ void spread_interior(unsigned char *regions, int rbyt
 // trackers).
 template <typename P, bool DIF = false>
 __device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes, int nbs, int lreg, double *gflux,
-                                             uint32_t goff, const Flight<P> &f, int lane) {
+                                             uint64_t goff, const Flight<P> &f, int lane) {
     using B = typename Real<P>::Bin;
     constexpr bool kDif = sizeof(B) == 4 && DIF;
     const bool has = f.k1 >= f.k0;
@@ -1198,7 +1214,8 @@ __global__ void __launch_bounds__(HistoryBounds<P, G, DIF>::threads, HistoryBoun
             resolve_direction<P, G>(s, a.cases[lcase], key);
             out = step<P, false, G, true>(s, a.cases[lcase], key, a.max_events, f, nullptr);
         }
-        const uint32_t goff = (lreg == 2) ? ((uint32_t)lcase * (uint32_t)a.t.nbatch + lbatch) * (uint32_t)a.t.nbins_stride : 0u;
+        const uint64_t goff =
+            (lreg == 2) ? ((uint64_t)lcase * (uint64_t)a.t.nbatch + lbatch) * (uint64_t)a.t.nbins_stride : 0ull;
         warp_deposit<P, DIF>(regions, rb, a.t.nbins_stride, lreg, a.t.flux, goff, f, lane);
         if (out >= 0) {
             record_outcome(a, lcase, s.h_lo, s.h_hi, out);

@@ -286,12 +286,12 @@ __global__ void __launch_bounds__(256, EventMinBlocks<P>::value) event_kernel(co
             // the particle's region, or 2 if that region has since changed key
             int reg = packed & 3;
             if (reg < 2 && (uint32_t)(packed >> 2) != gen[reg]) reg = 2;
-            uint32_t goff = 0;
+            uint64_t goff = 0;
             if (alive && reg == 2) {
                 const RunCase &rc = a.runs[run];
                 const uint64_t h = ((uint64_t)s.h_hi << 32) | s.h_lo;
-                const uint32_t batch = (uint32_t)((h - rc.first) / rc.batch_len);
-                goff = ((uint32_t)ci * (uint32_t)a.t.nbatch + batch) * (uint32_t)nbs;
+                const uint64_t batch = (h - rc.first) / rc.batch_len;
+                goff = ((uint64_t)ci * (uint64_t)a.t.nbatch + batch) * (uint64_t)nbs;
             }
             const uint32_t ev0 = alive ? s.events : 0u;
             s.n_coll = s.n_int = s.n_refl = 0;

@@ -6,12 +6,9 @@ namespace cls {
 
 template <int G, bool DIF>
 cudaError_t launch_history_gd(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(history_kernel<float, G, DIF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> optin{0};
+    const cudaError_t e = ensure_smem_optin(history_kernel<float, G, DIF>, optin);
+    if (e != cudaSuccess) return e;
     history_kernel<float, G, DIF><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }

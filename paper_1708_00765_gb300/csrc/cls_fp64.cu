@@ -8,12 +8,9 @@ namespace cls {
 
 template <int G>
 cudaError_t launch_history_g(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(history_kernel<double, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> optin{0};
+    const cudaError_t e = ensure_smem_optin(history_kernel<double, G>, optin);
+    if (e != cudaSuccess) return e;
     history_kernel<double, G><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }

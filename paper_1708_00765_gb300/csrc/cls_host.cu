@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/cls.h"
+#include "cls_case.h"
 #include "cls_internal.h"
 
 using namespace cls;
@@ -27,7 +28,6 @@ using namespace cls;
 namespace {
 
 constexpr int kBatchQuantum = 1024;   // statistics batches are multiples of this many histories
-constexpr int kMaxBins = 4096;
 constexpr int kMaxCases = 65536;
 constexpr uint32_t kMaxEventsLimit = 1u << 28;
 constexpr size_t kMaxSmemPerBlock = 200 * 1024;  // opt-in dynamic shared memory per block
@@ -104,73 +104,11 @@ int cuda_fail(cudaError_t e) { return e == cudaSuccess ? CLS_OK : CLS_E_CUDA; }
         if (_e != cudaSuccess) return CLS_E_CUDA;   \
     } while (0)
 
-bool finite(double v) { return std::isfinite(v); }
-
 // The run's work list: one RunCase per case, then the OutcomeRecord.
 size_t runs_bytes(size_t ncases) { return ncases * sizeof(RunCase) + sizeof(OutcomeRecord); }
 
 OutcomeRecord *outcome_record(RunCase *runs, size_t ncases) {
     return reinterpret_cast<OutcomeRecord *>(reinterpret_cast<unsigned char *>(runs) + ncases * sizeof(RunCase));
-}
-
-int validate(const double *p) {
-    const double s0 = p[0], s1 = p[1], l0 = p[2], l1 = p[3], c0 = p[4], c1 = p[5], L = p[6];
-    const double d = p[7], nb = p[8];
-    if (!(finite(s0) && s0 >= 0 && finite(s1) && s1 >= 0)) return CLS_E_INVAL;
-    if (!(finite(l0) && l0 > 0 && finite(l1) && l1 > 0)) return CLS_E_INVAL;
-    if (!(c0 >= 0 && c0 <= 1 && c1 >= 0 && c1 <= 1)) return CLS_E_INVAL;
-    if (!(finite(L) && L > 0)) return CLS_E_INVAL;
-    if (!(d == 1.0 || d == 2.0 || d == 3.0 || d == 11.0 || d == 13.0)) return CLS_E_INVAL;
-    if (!(nb >= 1 && nb <= kMaxBins && nb == std::floor(nb))) return CLS_E_INVAL;
-    return CLS_OK;
-}
-
-// Rough events-per-history estimate, used only to order cases largest first:
-// flights per unit path length times an estimate of the path length, which
-// grows with the number of scatterings ~ 1/(1 - c) and with the size L.
-double cost_estimate(const CaseParams &c) {
-    const double p0 = c.p0, p1 = 1.0 - c.p0;
-    const double sig = p0 * c.sigma[0] + p1 * c.sigma[1];
-    const double rate = sig + p0 / c.lambda[0] + p1 / c.lambda[1];
-    const double cbar = sig > 0 ? (p0 * c.c[0] * c.sigma[0] + p1 * c.c[1] * c.sigma[1]) / sig : 0.0;
-    const double tau = sig * c.L;
-    const double ncol = std::min(1.0 / std::max(1.0 - cbar, 1e-6), 1.0 + tau * tau);
-    const double path = std::min(c.L, 1.0 / std::max(sig, 1e-12)) * (1.0 + ncol * std::min(1.0, tau));
-    return 1.0 + rate * path;
-}
-
-CaseParams make_case(const double *p, uint32_t case_id) {
-    CaseParams c;
-    std::memset(&c, 0, sizeof(c));
-    for (int i = 0; i < 2; ++i) {
-        c.sigma[i] = p[i];
-        c.inv_sigma[i] = p[i] > 0 ? 1.0 / p[i] : 0.0;
-        c.lambda[i] = p[2 + i];
-        c.c[i] = p[4 + i];
-        c.sigma_f[i] = (float)p[i];
-        c.inv_sigma_f[i] = p[i] > 0 ? (float)(1.0 / p[i]) : 0.0f;
-        c.lambda_f[i] = (float)p[2 + i];
-        c.c_f[i] = (float)p[4 + i];
-    }
-    c.L = p[6];
-    c.d = (int32_t)p[7];
-    c.nbins = (int32_t)p[8];
-    c.p0 = c.lambda[0] / (c.lambda[0] + c.lambda[1]);
-    c.dx = c.L / c.nbins;
-    c.inv_dx = c.nbins / c.L;
-    c.L_f = (float)c.L;
-    c.p0_f = (float)c.p0;
-    c.dx_f = (float)c.dx;
-    c.inv_dx_f = (float)c.inv_dx;
-    c.case_id = case_id;
-    for (int i = 0; i < 2; ++i) {
-        c.thr_c53[i] = unit_threshold(c.c[i], 53);
-        c.thr_c24[i] = (uint32_t)unit_threshold((double)c.c_f[i], 24);
-    }
-    c.thr_p053 = unit_threshold(c.p0, 53);
-    c.thr_p024 = (uint32_t)unit_threshold((double)c.p0_f, 24);
-    c.cost = cost_estimate(c);
-    return c;
 }
 
 void free_tallies(cls_handle *h) {
@@ -185,7 +123,6 @@ void free_tallies(cls_handle *h) {
 int alloc_tallies(cls_handle *h) {
     const size_t nc = h->cases.size();
     const size_t nflux = nc * (size_t)h->nbatch * (size_t)h->nbins_stride;
-    if (nflux >= (1ull << 32)) return CLS_E_NOMEM;  // flux tallies are addressed with 32-bit offsets
     if (cudaMalloc(&h->d_flux, nflux * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->d_stats, nc * S_NUM * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->d_counters, nc * C_NUM * sizeof(unsigned long long)) != cudaSuccess) {
@@ -222,7 +159,7 @@ int create_common(const double *params, int ncases, bool batch, cls_handle **out
     if (!out || !params || ncases < 1 || ncases > kMaxCases) return CLS_E_INVAL;
     *out = nullptr;
     for (int k = 0; k < ncases; ++k) {
-        int rc = validate(params + 9 * (size_t)k);
+        int rc = validate_case(params + 9 * (size_t)k);
         if (rc) return rc;
     }
     int ndev = 0;

@@ -14,12 +14,14 @@
 //
 // Every call shares the one scratch array, which keeps the last call's
 // contents; each call rewrites the parameters and work list and clears the
-// chunk counter before its kernel starts.  Calls whose work overlaps on the
-// GPU (different streams, or another host thread) race on it.
+// chunk counter in a small set-up kernel before its tracker starts.  Calls
+// whose work overlaps on the GPU (different streams, or another host thread)
+// race on it.
 #include <cstring>
 #include <mutex>
 
 #include "../../include/cls.h"
+#include "cls_case.h"
 #include "cls_device.cuh"
 
 namespace {
@@ -33,8 +35,29 @@ struct NoallocScratch {
 };
 
 // The static scratch: every device that loads the library holds one copy of
-// it (about 12 KB) until the process exits.
+// it (about 16 KB) until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
+
+// One call's case parameters and work list, handed to the set-up kernel by
+// value: kernel arguments are copied when the launch is enqueued, so nothing
+// is read from host memory after this call returns (a stream-ordered copy
+// from a host buffer would have to keep that buffer alive until it runs).
+struct NoallocImage {
+    CaseParams cases[CLS_NOALLOC_MAX_CASES];
+    RunCase runs[CLS_NOALLOC_MAX_CASES];
+    int ncases;
+};
+static_assert(sizeof(NoallocImage) < 32000, "kernel arguments are limited to 32 KB");
+
+// Writes the call's cases and work list into the scratch and clears the work
+// counter; runs before the tracker on the same stream.
+__global__ void noalloc_setup(NoallocScratch *scratch, const NoallocImage img) {
+    for (int i = threadIdx.x; i < img.ncases; i += blockDim.x) {
+        scratch->cases[i] = img.cases[i];
+        scratch->runs[i] = img.runs[i];
+    }
+    if (threadIdx.x == 0) scratch->chunk_counter = 0ull;
+}
 
 constexpr int kMaxDevices = 64;
 NoallocScratch *g_scratch_ptr[kMaxDevices] = {nullptr};
@@ -65,14 +88,6 @@ int scratch_for_current_device(NoallocScratch **out, int *sm_count) {
     return CLS_OK;
 }
 
-bool valid_case(const double *p) {
-    const double s0 = p[0], s1 = p[1], l0 = p[2], l1 = p[3], c0 = p[4], c1 = p[5], L = p[6], d = p[7], nb = p[8];
-    auto fin = [](double v) { return v == v && v - v == 0.0; };
-    return fin(s0) && s0 >= 0 && fin(s1) && s1 >= 0 && fin(l0) && l0 > 0 && fin(l1) && l1 > 0 && c0 >= 0 &&
-           c0 <= 1 && c1 >= 0 && c1 <= 1 && fin(L) && L > 0 && (d == 1.0 || d == 2.0 || d == 3.0 || d == 11.0 || d == 13.0) && nb >= 1 && nb <= 4096 &&
-           nb == (double)(int)nb;
-}
-
 }  // namespace
 
 extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first, uint64_t n, uint64_t seed,
@@ -82,56 +97,29 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
     if (ncases < 1 || ncases > CLS_NOALLOC_MAX_CASES) return CLS_E_INVAL;
     if (n == 0 || n > (1ull << 62) || first > (1ull << 62)) return CLS_E_INVAL;
     if (nbatch < 1 || nbatch > 1024) return CLS_E_INVAL;
-    int nbins_max = 0;
+    if (nbins_stride < 1 || nbins_stride > CLS_NOALLOC_MAX_STRIDE) return CLS_E_INVAL;
     for (int k = 0; k < ncases; ++k) {
-        if (!valid_case(params + 9 * (size_t)k)) return CLS_E_INVAL;
-        nbins_max = nbins_max > (int)params[9 * k + 8] ? nbins_max : (int)params[9 * k + 8];
+        const double *p = params + 9 * (size_t)k;
+        if (validate_case(p) != CLS_OK || p[8] > nbins_stride) return CLS_E_INVAL;
     }
-    if (nbins_stride < nbins_max) return CLS_E_INVAL;
 
     NoallocScratch *scratch = nullptr;
     int sm_count = 0;
     int rc = scratch_for_current_device(&scratch, &sm_count);
     if (rc) return rc;
 
-    // host image of the parameters and work list (stack memory: no allocation)
-    NoallocScratch host;
-    std::memset(&host, 0, sizeof(host));
+    // this call's cases and work list (stack memory: no allocation), the same
+    // case set-up as cls_batch_create: case k draws with Philox counter word 3 = k
+    NoallocImage img;
+    std::memset(&img, 0, sizeof(img));
+    img.ncases = ncases;
     const uint64_t q = 1024ull * (uint64_t)nbatch;
     const uint64_t batch_len = 1024ull * ((n + q - 1) / q > 0 ? (n + q - 1) / q : 1);
     const int chunk = 256;
     uint64_t chunk_begin = 0;
     for (int k = 0; k < ncases; ++k) {
-        const double *p = params + 9 * (size_t)k;
-        CaseParams &c = host.cases[k];
-        for (int i = 0; i < 2; ++i) {
-            c.sigma[i] = p[i];
-            c.inv_sigma[i] = p[i] > 0 ? 1.0 / p[i] : 0.0;
-            c.lambda[i] = p[2 + i];
-            c.c[i] = p[4 + i];
-            c.sigma_f[i] = (float)p[i];
-            c.inv_sigma_f[i] = p[i] > 0 ? (float)(1.0 / p[i]) : 0.0f;
-            c.lambda_f[i] = (float)p[2 + i];
-            c.c_f[i] = (float)p[4 + i];
-        }
-        c.L = p[6];
-        c.d = (int32_t)p[7];
-        c.nbins = (int32_t)p[8];
-        c.p0 = c.lambda[0] / (c.lambda[0] + c.lambda[1]);
-        c.dx = c.L / c.nbins;
-        c.inv_dx = c.nbins / c.L;
-        c.L_f = (float)c.L;
-        c.p0_f = (float)c.p0;
-        c.dx_f = (float)c.dx;
-        c.inv_dx_f = (float)c.inv_dx;
-        c.case_id = (uint32_t)k;
-        for (int i = 0; i < 2; ++i) {
-            c.thr_c53[i] = unit_threshold(c.c[i], 53);
-            c.thr_c24[i] = (uint32_t)unit_threshold((double)c.c_f[i], 24);
-        }
-        c.thr_p053 = unit_threshold(c.p0, 53);
-        c.thr_p024 = (uint32_t)unit_threshold((double)c.p0_f, 24);
-        RunCase &r = host.runs[k];
+        img.cases[k] = make_case(params + 9 * (size_t)k, (uint32_t)k);
+        RunCase &r = img.runs[k];
         r.first = first;
         r.n = n;
         r.batch_len = batch_len;
@@ -139,16 +127,6 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
         r.case_index = k;
         chunk_begin += (n + chunk - 1) / chunk;
     }
-
-    cudaStream_t s = (cudaStream_t)stream;
-    // pageable source: the copy is staged before cudaMemcpyAsync returns, so the
-    // stack image may go out of scope afterwards
-    if (cudaMemcpyAsync(scratch->cases, host.cases, ncases * sizeof(CaseParams), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(scratch->runs, host.runs, ncases * sizeof(RunCase), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess ||
-        cudaMemsetAsync(&scratch->chunk_counter, 0, sizeof(unsigned long long), s) != cudaSuccess)
-        return CLS_E_CUDA;
 
     LaunchArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -176,6 +154,10 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, history_kernel<double, 0>, block, smem) != cudaSuccess)
         return CLS_E_CUDA;
     if (bps < 1) return CLS_E_INVAL;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    noalloc_setup<<<1, 64, 0, s>>>(scratch, img);
+    if (cudaGetLastError() != cudaSuccess) return CLS_E_CUDA;
     history_kernel<double, 0><<<sm_count * bps, block, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? CLS_OK : CLS_E_CUDA;
 }

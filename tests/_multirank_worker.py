@@ -24,7 +24,9 @@ def oracle_raw(case, seed, first, n):
             "track": r["track"], "flux": r["flux"], "batch_histories": bh}
 
 
-def run(rank, world, port, case_tuple, seed, n_total, drop_rank, out_q):
+def run(rank, world, port, case_tuple, seed, n_total, fault, out_q):
+    """`fault`: None, ("drop", r) -- rank r lost its shard -- or ("repeat", r) --
+    rank r walked its neighbour r - 1's range instead of its own."""
     import torch.distributed as dist
 
     import oracle
@@ -35,11 +37,14 @@ def run(rank, world, port, case_tuple, seed, n_total, drop_rank, out_q):
     try:
         case = oracle.Case(*case_tuple)
         first, n = shard.shard_range(rank, world, n_total)
-        if rank == drop_rank:
-            n = 0  # this rank lost its shard
+        if fault and fault[1] == rank:
+            if fault[0] == "drop":
+                n = 0  # this rank lost its shard
+            else:
+                first, n = shard.shard_range(rank - 1, world, n_total)  # walked its neighbour's ids
         raw = oracle_raw(case, seed, first, n)
         try:
-            merged = shard.allreduce_raw(raw, expected_histories=n_total)
+            merged = shard.allreduce_raw(raw, history_range=(first, n), expected_range=(0, n_total))
         except shard.CoverageError as e:
             out_q.put((rank, "coverage", str(e)))
             return

@@ -21,12 +21,12 @@ def free_port():
         return s.getsockname()[1]
 
 
-def launch(world, n_total, drop_rank=-1):
+def launch(world, n_total, fault=None):
     import _multirank_worker as w
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = free_port()
-    procs = [ctx.Process(target=w.run, args=(r, world, port, CASE, 7, n_total, drop_rank, q)) for r in range(world)]
+    procs = [ctx.Process(target=w.run, args=(r, world, port, CASE, 7, n_total, fault, q)) for r in range(world)]
     for p in procs:
         p.start()
     out = {}
@@ -69,8 +69,28 @@ def test_two_ranks_merge_equals_one_run():
 
 
 def test_lost_shard_is_detected():
-    out = launch(2, 4000, drop_rank=1)
+    out = launch(2, 4000, fault=("drop", 1))
     assert all(status == "coverage" for status, _ in out.values())
+
+
+def test_repeated_shard_is_detected():
+    """Rank 1 walks rank 0's ids instead of its own: the merged history count is right
+    (2 x 2000), but ids [0, 2000) were walked twice and [2000, 4000) never."""
+    out = launch(2, 4000, fault=("repeat", 1))
+    assert all(status == "coverage" for status, _ in out.values())
+    assert all("more than once" in payload for _, payload in out.values())
+
+
+def test_check_cover_on_the_host():
+    shard.check_cover([(0, 10), (10, 5), (15, 0)], (0, 15))
+    shard.check_cover([(100, 3), (103, 7)], (100, 10))
+    for ranges, exp in (([(0, 10), (5, 10)], (0, 15)),   # overlap
+                        ([(0, 10), (11, 4)], (0, 15)),   # gap
+                        ([(0, 10), (10, 10)], (0, 15)),  # beyond the end
+                        ([(1, 14)], (0, 15)),            # missing start
+                        ([(0, 10), (0, 10)], (0, 20))):  # the same range twice, right total
+        with pytest.raises(shard.CoverageError):
+            shard.check_cover(ranges, exp)
 
 
 def test_host_finalize_matches_oracle_finalize():

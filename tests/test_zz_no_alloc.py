@@ -19,6 +19,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
+import oracle  # noqa: E402
 import paper_1708_00765_gb300 as cls  # noqa: E402
 from paper_1708_00765_gb300 import _native, workloads  # noqa: E402
 
@@ -59,6 +60,14 @@ def test_noalloc_two_calls_match_cls_run():
             nb = int(cases[k, 8])
             np.testing.assert_allclose(f[k, :, :nb], raw["flux"], rtol=RTOL, atol=1e-15 * raw["flux"].max())
         ref.close()
+    # and against the oracle itself: the counts of every case over both ranges
+    for k in range(nc):
+        c = oracle.Case(*cases[k][:7], int(cases[k][7]), int(cases[k][8]))
+        parts = [oracle.run(c, 5, first, n, case_id=k) for first, n in ranges]
+        for j, key in enumerate(("nR", "nT", "nA", "n_coll", "n_int", "n_refl", "n_events", "n_capped")):
+            assert int(ct[k, j]) == sum(p[key] for p in parts), (k, key)
+        assert int(ct[k, 8]) == max(p["max_events"] for p in parts)
+        assert st[k, 0] == pytest.approx(sum(p["sum_t"] for p in parts), rel=RTOL)
 
 
 def test_noalloc_rejects_too_many_cases():
@@ -66,3 +75,11 @@ def test_noalloc_rejects_too_many_cases():
     buf = torch.zeros(16, dtype=torch.float64, device="cuda")
     rc = _native.run_noalloc(cases, 0, 100, 1, 4, 100, buf.data_ptr(), buf.data_ptr(), buf.data_ptr())
     assert rc == _native.CLS_E_INVAL
+
+
+def test_noalloc_rejects_a_stride_beyond_its_maximum():
+    cases = np.array([workloads.ROD_L10])
+    buf = torch.zeros(16, dtype=torch.float64, device="cuda")
+    for nbs in (99, _native.CLS_NOALLOC_MAX_STRIDE + 1):  # below the case's 100 bins; above the maximum
+        rc = _native.run_noalloc(cases, 0, 100, 1, 4, nbs, buf.data_ptr(), buf.data_ptr(), buf.data_ptr())
+        assert rc == _native.CLS_E_INVAL
