@@ -254,6 +254,25 @@ def run_many(cases, seed: int, first: int, n: int, *, case_ids=None, workers: in
         return pool.map(_run_case, args)
 
 
+def _run_seed(args):
+    case_t, seed, first, n, nbatch = args
+    return run(Case(*case_t), seed, first, n, nbatch=nbatch)
+
+
+def run_seeds(case: Case, seeds, first: int, n: int, *, nbatch: int = DEFAULT_NBATCH,
+              workers: int | None = None) -> list:
+    """run() of one case under several seeds (independent samples of the same
+    histories' law), one task per seed over a spawn-started process pool."""
+    import multiprocessing as mp
+    build()
+    args = [(astuple(case), int(s), first, n, nbatch) for s in seeds]
+    workers = min(workers or os.cpu_count() or 1, len(args))
+    if workers <= 1:
+        return [_run_seed(a) for a in args]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_run_seed, args, chunksize=max(1, len(args) // (4 * workers)))
+
+
 def trace(case: Case, seed: int, h: int, *, case_id: int = 0, max_events: int = DEFAULT_MAX_EVENTS,
           cap: int = 100_000):
     """Event-by-event trace of one history: array of rows

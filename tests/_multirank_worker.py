@@ -15,7 +15,12 @@ def oracle_raw(case, seed, first, n):
                 "n_events": 0, "n_capped": 0, "max_events": 0, "sum_t": 0.0, "sum_t2": 0.0, "track": (0.0, 0.0),
                 "flux": np.zeros((oracle.DEFAULT_NBATCH, case.nbins)),
                 "batch_histories": np.zeros(oracle.DEFAULT_NBATCH, dtype=np.uint64)}
-    r = oracle.run(case, seed, first, n)
+    return oracle_raw_from(oracle.run(case, seed, first, n), n)
+
+
+def oracle_raw_from(r, n):
+    """The library's raw-tally layout (cls_raw_t fields, flux[nbatch][nbins] and the
+    histories per batch) of an oracle run of n histories."""
     bl = r["batch_len"]
     bh = np.array([max(0, min(bl, n - b * bl)) for b in range(r["nbatch"])], dtype=np.uint64)
     return {"n_histories": r["n_histories"], "nR": r["nR"], "nT": r["nT"], "nA": r["nA"], "n_coll": r["n_coll"],
