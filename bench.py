@@ -1,12 +1,18 @@
 """Benchmark: CLS random walks on one GB300 (or N, as independent history shards).
 
-Workload (default): 3D box of side 10, Sigma = (0.1, 10), Lambda = (1, 0.1),
-c = 0.99, cosine-law incidence on x = 0, 200 flux bins, 1e8 histories per GPU
-per step, FP64, persistent history-based tracker.  One step = one pass of the
-whole walk (source, flights, events, track-length tallies) over 1e8 histories;
-`value` is histories/s over all ranks, device-timed with CUDA events.  The same
-workload also runs with FP32 tracking / FP64 tallies, and both arms report the
-figure of merit FOM = 1 / (sigma_rel(<phi>)^2 T).
+Default workload (the headline line): the batched sweep of 256 cases (seed 7:
+rods and 3D boxes, L in {0.1, 1, 10}, Sigma, Lambda log-uniform, c uniform;
+100 flux bins) at 1e8 histories per case per step.  One step = one pass of the
+whole walk (sources, flights, events, track-length tallies) over 2.56e10
+histories: FP32 tracking with FP64 tallies, every case in one persistent
+launch replayed from a CUDA graph.  `value` is histories/s over all ranks,
+device-timed with CUDA events.  Against it, the same cases walked in FP64 one
+launch per case (no graph, default launch shape): the figure of merit
+FOM_X = 1 / (sigma_rel(X)^2 T) per case for X in {<phi>, R, T, worst bin},
+the two arms' results in units of their combined standard error on
+independent seeds, and the fraction of histories whose outcome is identical
+on the same seed.  The same line carries the 3D box (L = 10, 1e8 histories
+per step) in FP64 and FP32.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank takes its own disjoint history range (weak scaling).
@@ -14,6 +20,7 @@ Under torchrun each rank takes its own disjoint history range (weak scaling).
 from __future__ import annotations
 
 import argparse
+import csv
 import json
 import math
 import os
@@ -30,39 +37,110 @@ sys.path.insert(0, ROOT)
 
 METRIC = "histories/s and FOM 1/(sigma^2 T) at equal sigma, FP32-batched vs FP64-plain on 1 GB300"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+SWEEP_CASES, SWEEP_SEED, SWEEP_BINS = 256, 7, 100
+SWEEP_HISTORIES = 100_000_000  # per case per step
+SWEEP_WORKLOAD = ("batched sweep: 256 cases (seed 7; d in {rod, 3D box}, L in {0.1, 1, 10}, Sigma and Lambda "
+                  "log-uniform, c uniform), 100 bins, FP32 tracking / FP64 tallies, one persistent launch "
+                  "replayed from a CUDA graph")
 BOX_WORKLOAD = "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, cosine incidence, 200 bins"
+SEED32, SEED64 = 1, 2   # the FP32 and FP64 arms draw from independent Philox keys
+E2E_STEPS = 3           # end-to-end steps through the C ABI (host copies in the timed region)
+ORACLE_HISTORIES = 1_000_000  # per case: the oracle's independent-seed check of the FP32 arm
 
-# Work per event of the benchmark workloads' kernels, for the issue-rate
-# roofline (152 SMs x 4 warp instructions per clock): warp instructions per
-# event counted by ncu (smsp__inst_executed.sum / events, one pass) on the
-# full-size launch of the current kernels (1e8 histories; the sweep's 256 x 1e7),
-# updated with each capture of a changed kernel.  A small launch counts more
-# per event: its heavy-tailed last histories run in nearly empty warps.
-# FP64_FLOP_PER_EVENT: the same event's FP64 arithmetic evaluated directly in
-# FP64 with FP64 elementary functions (ln, sin/cos, division, sqrt), counted by
-# ncu (DADD + DMUL + 2 DFMA) on that direct evaluation; reported beside the
-# roofline as FP64-equivalent TFLOP/s for context.  The kernel evaluates the
-# elementary functions in the integer pipes and is bound by issue and latency,
-# not by the FP64 pipe.
-FP64_WARP_INST_PER_EVENT = 76.0
-FP32_WARP_INST_PER_EVENT = 19.4
-FP64_FLOP_PER_EVENT = 148.8
-# The FP64 box kernel's FP64 pipe busy fraction (ncu sm__pipe_fp64_cycles_active,
-# `--set full` of a 1e7-history launch): its second limit beside the issue rate.
-FP64_PIPE_ACTIVE = 0.60
-# The diffusive workload's FP32 kernels (500 bins: no difference array).
-DIFFUSIVE_WARP_INST_PER_EVENT = {"history": 20.2, "event": 20.7}
-# The batched sweep's FP32 kernel (history_kernel<float, 0, 1>, 256 cases x
-# 1e7 histories in one launch, autotuned shape): warp instructions per event
-# and DRAM bytes of one full-size replay, the same one-pass ncu capture.
-BATCH_FP32_WARP_INST_PER_EVENT = 26.5
-BATCH_FP32_DRAM_BYTES_PER_LAUNCH = 13265664
-# DRAM bytes of that full-size FP64 launch (the same one-pass capture); None
-# whenever the kernel has changed since the capture.
-FP64_DRAM_BYTES_PER_LAUNCH = 882688
 SM_COUNT = 152           # GB300
-DFMA_PER_SM_CLK = 2      # ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / 152 SMs
 ISSUE_PER_SM_CLK = 4     # one warp instruction per scheduler per clock, 4 schedulers
+LANES = 32
+
+# ------------------------------------------------------ algorithmic work model
+# The work of Algorithm A per history, counted in thread operations (one
+# 32-bit integer or FP32 operation, one FP32 approximate function, one shared
+# atomic each), written from the algorithm -- not from the kernel -- and
+# computed from each run's own counters (histories, events, collisions,
+# absorptions, mean flight length):
+#   draws: the source's (rod 1, slab and x-projected box 2, extruded 4, box 5),
+#     two per event (collision and interface distances), one per collision
+#     (scatter or absorb), one per rod / slab scatter or two per 3D scatter;
+#   RNG: half a Philox4x32-10 block per draw (10 rounds of two 32x32->64
+#     multiplies -- 4 operations -- and 4 XORs: 80 per block) plus 2 to form u;
+#   per event: the two distances (2 logarithms at 2 operations, 2 scalings),
+#     a boundary distance per tracked axis (3), the event select (5), the move
+#     (1 per axis), the bin coordinates of the flight's ends (4), its end-bin
+#     partials (2), one add per bin it touches (1 + E|omega_x| flight / dx),
+#     and bookkeeping (2);
+#   per collision the scatter test (1); per 3D scatter a new direction (mu,
+#     sin theta, sin/cos phi, the three components and reciprocals: 8 + axes),
+#     1 for the rod, 2 for the slab; per history the source (box 14, extruded
+#     12, slab 3, rod 1) and the history-end statistics (6).
+# Peak: every lane of every scheduler issuing one operation per clock,
+# 152 SMs x 4 x 32 lanes x the sampled SM clock.
+PHILOX_BLOCK_OPS = 80
+UNIFORM_OPS = 2
+# geometry -> (tracked axes, source draws, source ops, scatter draws, scatter ops, E|omega_x|)
+GEOM_MODEL = {1: (1, 1, 1, 1, 1, 1.0), 2: (2, 4, 12, 2, 10, 0.5), 3: (3, 5, 14, 2, 11, 0.5),
+              11: (1, 2, 3, 1, 2, 0.5), 13: (1, 2, 3, 1, 2, 0.5)}
+
+
+def model_draws(geom: int, t: dict) -> float:
+    """Random numbers Algorithm A draws for the histories of tallies `t` (suite I source)."""
+    _, src_draws, _, sc_draws, _, _ = GEOM_MODEL[geom]
+    return src_draws * t["n_histories"] + 2 * t["n_events"] + t["n_coll"] + sc_draws * (t["n_coll"] - t["nA"])
+
+
+def algorithmic_ops(params, t: dict) -> float:
+    """Thread operations of Algorithm A for the histories of tallies `t` of case `params`."""
+    geom, L, nbins = int(params[7]), float(params[6]), int(params[8])
+    axes, _, src_ops, _, sc_ops, wx = GEOM_MODEL[geom]
+    N, ev, nc, na = t["n_histories"], t["n_events"], t["n_coll"], t["nA"]
+    if ev == 0:
+        return 0.0
+    flight = t["total_flux"] * N / ev
+    bins_touched = min(float(nbins), 1.0 + wx * flight / (L / nbins))
+    per_event = 6 + 3 * axes + 5 + axes + 4 + 2 + bins_touched + 2
+    return ((PHILOX_BLOCK_OPS / 2 + UNIFORM_OPS) * model_draws(geom, t) + per_event * ev + nc
+            + sc_ops * (nc - na) + (src_ops + 6) * N)
+
+
+def peak_ops(clk_mhz: float) -> float:
+    return SM_COUNT * ISSUE_PER_SM_CLK * LANES * clk_mhz * 1e6
+
+
+# --------------------------------------------- ncu counts of the current kernels
+KERNEL_COUNTS = os.path.join(ROOT, "profiles", "kernel_counts.csv")
+
+
+def kernel_counts(kernel: str, workload: str):
+    """Warp instructions and DRAM bytes of one full-size launch, from the committed
+    ncu summary of the current kernels (None when it holds no row for them)."""
+    if not os.path.exists(KERNEL_COUNTS):
+        return None
+    with open(KERNEL_COUNTS) as f:
+        for row in csv.DictReader(line for line in f if not line.startswith("#")):
+            if row["kernel"] == kernel and row["workload"] == workload:
+                return {k: float(row[k]) for k in ("events", "warp_inst", "dram_read", "dram_write", "duration_ms")}
+    return None
+
+
+def roofline(kernel, workload, ops_per_launch, launch_s, events_per_launch, clk_mhz, n_full: bool):
+    """The bench's roofline object: algorithmic thread operations per launch over the
+    launch's CUDA-event duration, against the issue peak; beside it, the kernel's own
+    instruction count (ncu) as issue-slot occupancy, and its DRAM traffic."""
+    achieved = ops_per_launch / launch_s
+    peak = peak_ops(clk_mhz)
+    out = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tthread-op/s",
+           "frac": achieved / peak, "traffic": None, "kernel": kernel,
+           "work": f"{ops_per_launch / events_per_launch:.1f} algorithmic thread operations/event x "
+                   f"{events_per_launch:.4g} events/launch",
+           "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} schedulers x {LANES} lanes x {clk_mhz} MHz (sampled)",
+           "issue": None}
+    kc = kernel_counts(kernel, workload)
+    if kc is not None and n_full:
+        per_event = kc["warp_inst"] / kc["events"]
+        issue_peak = SM_COUNT * ISSUE_PER_SM_CLK * clk_mhz * 1e6
+        out["traffic"] = kc["dram_read"] + kc["dram_write"]
+        out["issue"] = {"warp_inst_per_event": per_event,
+                        "frac": per_event * events_per_launch / launch_s / issue_peak,
+                        "source": os.path.relpath(KERNEL_COUNTS, ROOT)}
+    return out
 
 
 def parse():
@@ -71,16 +149,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--histories", type=int, default=None, help="override histories per step (tests only)")
-    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-tracking arm")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 arm (profiling only)")
+    ap.add_argument("--histories", type=int, default=None,
+                    help="histories per step (per case for the sweep); tests and profiling only")
+    ap.add_argument("--workload", default="default", choices=["default", "sweep", "box", "diffusive", "suite"],
+                    help="default: the sweep's headline line plus the box arms; sweep / box: one of them alone; "
+                         "diffusive: L=100 box, c=0.999, history vs event schedule; suite: the paper's 54 "
+                         "benchmark configurations (Tables 3-8), FP64")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 arms (profiling only)")
+    ap.add_argument("--no-fp32", action="store_true", help="box: skip the FP32 arm")
     ap.add_argument("--no-projected", action="store_true",
-                    help="skip the arms that walk the box by its x-marginal (geometry 13)")
+                    help="box: skip the arms that walk the box by its x-marginal (geometry 13)")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle's check of the FP32 sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="box", choices=["box", "diffusive", "batch", "suite"],
-                    help="box: L=10 box (default, the headline line); diffusive: L=100 box, c=0.999, "
-                         "history vs event schedule; batch: 256-case sweep, FP64 plain vs FP32 batched; "
-                         "suite: the paper's 54 benchmark configurations (Tables 3-8), FP64")
+    ap.add_argument("--oracle-histories", type=int, default=ORACLE_HISTORIES)
     return ap.parse_args()
 
 
@@ -91,12 +172,9 @@ def dist_setup():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
-        import torch.distributed as dist
-        backend = "nccl"
         import torch
-        if not torch.cuda.is_available():
-            backend = "gloo"
-        dist.init_process_group(backend=backend)
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
         pg = dist
     return rank, world, local, pg
 
@@ -175,117 +253,495 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
+def merge_clocks(samplers):
+    """One clocks record over several sampled regions: the median of their medians,
+    the union of their throttle reasons."""
+    s = [x.summary() for x in samplers if x.summary().get("sm_mhz")]
+    if not s:
+        return samplers[0].summary()
+    return {"sm_mhz": statistics.median(x["sm_mhz"] for x in s), "sm_max_mhz": s[0]["sm_max_mhz"],
+            "reasons": sorted({r for x in s for r in x["reasons"]}), "samples": sum(x["samples"] for x in s),
+            "power_w_max": max(x["power_w_max"] for x in s)}
+
+
 # ------------------------------------------------------------ oracle timing
-def oracle_rate(params, seconds_target: float, cores: int, first: int = 0, detail: dict | None = None,
-                n_fixed: int | None = None):
-    """Time the FP64 oracle on a bounded sample of the workload over `cores` processes
-    (n_fixed histories if given, else about seconds_target of work).  `detail`, if
-    given, receives the single-process pilot's rate and the events per second of the
-    sample."""
+def sweep_cases():
+    from paper_1708_00765_gb300 import workloads
+    return workloads.batch_sweep(SWEEP_CASES, seed=SWEEP_SEED, nbins=SWEEP_BINS)
+
+
+def oracle_cases(cases):
     import oracle
-    case = oracle.Case(*params[:7], int(params[7]), int(params[8]))
+    return [oracle.Case(*c[:7], int(c[7]), int(c[8])) for c in cases]
+
+
+def oracle_pool(cores):
+    """The oracle's process pool: spawn-started, before this process touches the GPU."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    return mp.get_context("spawn").Pool(cores)
+
+
+def oracle_sweep(pool, cases, seed, first, n):
+    """Oracle runs of histories [first, first + n) of every case (case k with Philox
+    counter word 3 = k), one task per case; returns an AsyncResult of raw tallies."""
+    import oracle
+    from dataclasses import astuple
+    args = [(astuple(c), seed, first, n, k) for k, c in enumerate(oracle_cases(cases))]
+    order = sorted(range(len(args)), key=lambda k: -cases[k][6] * (1 + cases[k][4] + cases[k][5]))
+    res = pool.map_async(oracle._run_case, [args[k] for k in order], chunksize=1)
+    return res, order
+
+
+def oracle_sweep_rate(pool, cases, cores, n_per_case=None, seconds_target=12.0, first=10**12):
+    """Histories/s of the FP64 oracle on a bounded sample of the sweep: the first
+    n_per_case ids of every case (sized from a pilot for about seconds_target of work
+    when not given), over the spawn pool of `cores` processes."""
+    if n_per_case is None:
+        t0 = time.perf_counter()
+        res, _ = oracle_sweep(pool, cases, SEED64, first, 200)
+        res.get()
+        pilot = time.perf_counter() - t0
+        n_per_case = int(min(1_000_000, max(200, 200 * seconds_target / max(pilot, 1e-3))))
     t0 = time.perf_counter()
-    pilot = 2000
-    oracle.run(case, 1, first, pilot)
-    rate1 = pilot / (time.perf_counter() - t0)
-    n = n_fixed or max(cores * 2048, int(rate1 * cores * seconds_target))
-    t0 = time.perf_counter()
-    raw = oracle.run_parallel(case, 1, first, n, workers=cores)
+    res, _ = oracle_sweep(pool, cases, SEED64, first + 10**9, n_per_case)
+    raws = res.get()
     dt = time.perf_counter() - t0
-    if detail is not None:
-        detail.update(single_process_histories_per_s=rate1, events_per_s=raw["n_events"] / dt)
-    return n / dt, n, dt, raw["workers"]
+    n = len(cases) * n_per_case
+    return {"value": n / dt, "n_per_case": n_per_case, "seconds": dt, "cores": cores,
+            "events_per_s": sum(r["n_events"] for r in raws) / dt}
 
 
 def reference_arm(args, rank, world, pg):
-    from paper_1708_00765_gb300 import workloads
+    """The base contract's reference arm for this tier: the FP64 oracle, as it stands,
+    on the host cores, each step a bounded sample of the headline workload."""
     if rank != 0:
         barrier(pg)
         return
-    params = workloads.BOX_L10
+    cases = sweep_cases()
     cores = os.cpu_count() or 1
+    pool = oracle_pool(cores)
+    n_case = args.histories
     rates = []
-    detail = {}
     for i in range(args.warmup + args.steps):
-        r, n, dt, used = oracle_rate(params, 4.0, cores, first=i * 10_000_000, detail=detail, n_fixed=args.histories)
+        r = oracle_sweep_rate(pool, cases, cores, n_per_case=n_case, seconds_target=4.0, first=i * 10**10)
+        n_case = r["n_per_case"]  # the first step's size, for all steps
         if i >= args.warmup:
-            rates.append((r, n, dt))
-    value = sum(r for r, _, _ in rates) / len(rates)
-    n_mean = int(sum(n for _, n, _ in rates) / len(rates))
+            rates.append(r)
+    pool.close()
+    pool.join()
+    value = sum(r["value"] for r in rates) / len(rates)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(d for _, _, d in rates) / len(rates),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(r["seconds"] for r in rates) / len(rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": BOX_WORKLOAD, "histories_per_step_per_gpu": n_mean, "schedule": "history",
-                   "precision": "fp64", "sample": "a bounded sample of the workload per step, on the host cores"},
-        "cpu_baseline": {"value": value, "unit": "histories/s", "cores": used, "kind": "oracle",
-                         "sample": f"{n_mean} histories of the box L=10 workload per step",
-                         "events_per_s": detail["events_per_s"],
-                         "single_process_histories_per_s": detail["single_process_histories_per_s"]},
+        "config": {"workload": SWEEP_WORKLOAD, "cases": SWEEP_CASES, "histories_per_case_per_step": n_case,
+                   "sample": "a bounded sample of the workload per step (the first ids of every case), "
+                             "walked by the FP64 oracle on the host cores"},
+        "cpu_baseline": {"value": value, "unit": "histories/s", "cores": rates[0]["cores"], "kind": "oracle",
+                         "sample": f"{n_case} histories of each of the {SWEEP_CASES} sweep cases per step",
+                         "events_per_s": sum(r["events_per_s"] for r in rates) / len(rates)},
         "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     barrier(pg)
 
 
-# ------------------------------------------------------------------ our arm
-def timed_runs(prob, n, seed, steps, warmup, flush, torch, stream, first_base=0):
-    """Device seconds of `steps` runs of n histories after `warmup` untimed ones."""
+# ------------------------------------------------------------------ helpers
+def stats_of(v):
+    v = sorted(float(x) for x in v)
+    if not v:
+        return None
+    return {"median": v[len(v) // 2], "min": v[0], "max": v[-1], "cases": len(v)}
+
+
+def rel_sigma(value, sigma):
+    return sigma / abs(value) if value != 0 and sigma > 0 else None
+
+
+def worst_bin_rel_sigma(t):
+    phi, sd = np.asarray(t["flux"]), np.asarray(t["flux_sigma"])
+    ok = (phi > 0) & (sd > 0)
+    return float(np.max(sd[ok] / phi[ok])) if ok.any() else None
+
+
+FOM_KEYS = (("total_flux", "sigma_total_flux"), ("R", "sigma_R"), ("T", "sigma_T"))
+
+
+def fom_ratios(tal32, tal64, t32, t64):
+    """Per case FOM_X(FP32 batched) / FOM_X(FP64 plain), FOM = 1 / (sigma_rel^2 T),
+    for X in {<phi>, R, T, worst-bin phi}.  sigma^2 scales as 1/N, so the ratio at
+    equal N is the ratio at equal sigma: the FP64 time to reach the FP32 arm's sigma
+    over the FP32 time.  T is each arm's whole-sweep time."""
+    out = {}
+    for key, skey in FOM_KEYS + (("worst_bin", None),):
+        r = []
+        for a, b in zip(tal32, tal64):
+            if key == "worst_bin":
+                s32, s64 = worst_bin_rel_sigma(a), worst_bin_rel_sigma(b)
+            else:
+                s32, s64 = rel_sigma(a[key], a[skey]), rel_sigma(b[key], b[skey])
+            if s32 and s64:
+                r.append((s64 * s64 * t64) / (s32 * s32 * t32))
+        out[key] = stats_of(r)
+    return out
+
+
+def z_scores(tal_a, tal_b, keys=("R", "T", "A", "total_flux")):
+    """(a - b) / sqrt(sigma_a^2 + sigma_b^2) per case and observable (paper Eq. combined_var);
+    counts that are exactly equal with zero error give no z-score."""
+    zs = []
+    for a, b in zip(tal_a, tal_b):
+        for k in keys:
+            comb = math.hypot(a["sigma_" + k], b["sigma_" + k])
+            if comb > 0:
+                zs.append((a[k] - b[k]) / comb)
+    zs = np.array(zs)
+    return {"max_abs": float(np.max(np.abs(zs))), "rms": float(np.sqrt(np.mean(zs * zs))),
+            "above_4": int(np.sum(np.abs(zs) > 4)), "n": int(zs.size)}
+
+
+def oracle_tallies(raw, case):
+    import oracle
+    return oracle.finalize(raw, case)
+
+
+def timed_pass(run, steps, warmup, flush, torch, stream, before_timed=None):
+    """CUDA-event times (s) of `steps` calls of run() after `warmup` untimed ones, L2
+    flushed before each; before_timed() runs once between the two phases."""
     times = []
     for i in range(warmup + steps):
         flush.zero_()
         if i == warmup:
-            prob.reset()
-            if first_base:
-                prob.set_option("first_history", first_base)
+            if before_timed:
+                before_timed()
+            torch.cuda.synchronize()
         start = torch.cuda.Event(enable_timing=True)
         stop = torch.cuda.Event(enable_timing=True)
         start.record(stream)
-        prob.run(n, seed, stream=stream)
+        run()
         stop.record(stream)
         if i >= warmup:
             times.append((start, stop))
     torch.cuda.synchronize()
-    return sum(a.elapsed_time(b) for a, b in times) * 1e-3
+    return [a.elapsed_time(b) * 1e-3 for a, b in times]
 
 
-def diffusive_workload(args, rank, world, pg):
+# ---------------------------------------------------------------- the sweep
+def sweep_arms(args, rank, world, pg, local, pool):
+    """The 256-case sweep: FP32 batched + graph (timed, steps x n per case), end to end
+    through the C ABI, FP64 plain (one launch per case, one pass of n per case), the
+    identical-outcome records and the oracle's independent check."""
+    import torch
+    import paper_1708_00765_gb300 as cls
+    cases = sweep_cases()
+    nc = len(cases)
+    n = args.histories or SWEEP_HISTORIES
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    # the oracle's independent check of the FP32 arm starts first and overlaps the GPU work
+    oracle_job = None
+    if pool is not None and rank == 0 and not args.no_oracle:
+        oracle_job = oracle_sweep(pool, cases, SEED64, 0, args.oracle_histories)
+
+    # ---- FP32 batched: every case in one persistent launch, replayed from a graph
+    b32 = cls.Problem(cases, batch=True)
+    b32.set_option("precision", "fp32")
+    tuned = b32.autotune(max(4096, min(n // 16, 262_144)), seed=3, stream=stream)
+    base = rank * (args.warmup + args.steps + E2E_STEPS) * n
+    if base:
+        b32.set_option("first_history", base)
+
+    def reset32():
+        b32.reset()
+        b32.set_option("first_history", base + args.warmup * n)
+
+    barrier(pg)
+    s32 = ClockSampler(local)
+    with s32:
+        times = timed_pass(lambda: b32.run(n, SEED32, stream=stream), args.steps, args.warmup, flush, torch, stream,
+                           before_timed=reset32)
+        barrier(pg)
+    t32 = max_over_ranks(pg, sum(times))
+    tal32 = [b32.tallies(k) for k in range(nc)]
+    # end to end through the C ABI: each step's run (its work list copied from pinned
+    # host memory) and every case's tallies (device-to-host copy, FP64 normalisation)
+    barrier(pg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(E2E_STEPS):
+        b32.run(n, SEED32, stream=stream)
+        for k in range(nc):
+            b32.tallies(k)
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+    b32.close()
+    events32 = sum(t["n_events"] for t in tal32) / args.steps
+    ops32 = sum(algorithmic_ops(c, t) for c, t in zip(cases, tal32)) / args.steps
+    out["fp32_batched"] = {
+        "histories_per_s": world * nc * n * args.steps / t32, "ms_per_step": 1e3 * t32 / args.steps,
+        "events_per_s": world * events32 * args.steps / t32,
+        "collisions_per_s": world * sum(t["n_coll"] for t in tal32) / t32,
+        "events_per_history": events32 / (nc * n), "autotuned": tuned,
+        "launch_ms": [1e3 * x for x in times], "ops_per_step": ops32, "events_per_step": events32}
+    out["e2e"] = {"value": world * nc * n * E2E_STEPS / e2e_s, "unit": "histories/s", "steps": E2E_STEPS,
+                  "h2d_bytes_per_step": nc * 40 + 24,
+                  "d2h_bytes_per_step": nc * (64 * SWEEP_BINS * 8 + 4 * 8 + 9 * 8)}
+
+    if not args.no_fp64:
+        # ---- FP64 plain: one handle and one launch per case, default launch shape, no graph
+        plain = [cls.Problem(c) for c in cases]
+        for p in plain:
+            p.run(20_000, 99, stream=stream)  # warm-up (module load, first launch)
+            p.reset()
+            if rank:
+                p.set_option("first_history", rank * n)
+        torch.cuda.synchronize()
+        barrier(pg)
+        s64 = ClockSampler(local)
+        with s64:
+            flush.zero_()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in plain]
+            for p, (a, b) in zip(plain, ev):
+                a.record(stream)
+                p.run(n, SEED64, stream=stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            barrier(pg)
+        t64 = max_over_ranks(pg, ev[0][0].elapsed_time(ev[-1][1]) * 1e-3)
+        tal64 = [p.tallies() for p in plain]
+        for p in plain:
+            p.close()
+        events64 = sum(t["n_events"] for t in tal64)
+        ops64 = sum(algorithmic_ops(c, t) for c, t in zip(cases, tal64))
+        out["fp64_plain"] = {"histories_per_s": world * nc * n / t64, "s_per_pass": t64,
+                             "events_per_s": world * events64 / t64, "ops_per_pass": ops64,
+                             "events_per_pass": events64}
+        out["clocks64"] = s64
+        out["fom"] = fom_ratios(tal32, tal64, t32, t64)
+        out["z_fp32_vs_fp64"] = z_scores(tal32, tal64)
+        # ---- identical outcomes: both precisions walk ids [0, n) of every case on the FP64
+        # arm's seed once more, untimed, recording each history's outcome on the device
+        codes = {}
+        for prec in ("fp32", "fp64"):
+            b = cls.Problem(cases, batch=True)  # default launch shape: results do not depend on it
+            b.set_option("precision", prec)
+            codes[prec] = torch.empty(nc * n, dtype=torch.uint8, device="cuda")
+            b.record_outcomes(codes[prec].data_ptr(), codes[prec].numel())
+            b.set_option("first_history", rank * n)
+            b.run(n, SEED64, stream=stream)
+            torch.cuda.synchronize()
+            b.close()
+        same = np.array([int((codes["fp32"][k * n:(k + 1) * n] == codes["fp64"][k * n:(k + 1) * n]).sum())
+                         for k in range(nc)]) / n
+        del codes
+        torch.cuda.empty_cache()
+        out["identical_outcomes"] = {"median": float(np.median(same)), "min": float(same.min()),
+                                     "overall": float(same.mean()), "histories_per_case": n, "seed": SEED64}
+    out["clocks32"] = s32
+    if oracle_job is not None:
+        res, order = oracle_job
+        raws = res.get()
+        ocs = oracle_cases(cases)
+        tal_o = [None] * nc
+        for k, raw in zip(order, raws):
+            tal_o[k] = oracle_tallies(raw, ocs[k])
+        # oracle results carry the library's key names for the z-scores
+        out["z_fp32_vs_oracle"] = z_scores(tal32, tal_o)
+        out["z_fp32_vs_oracle"]["oracle_histories_per_case"] = args.oracle_histories
+    out["tal32"] = tal32
+    return out
+
+
+# ------------------------------------------------------------------ the box
+def box_arms(args, rank, world, pg, local):
+    """The 3D box of side 10 (1e8 histories per step) in FP64 and FP32, plus the same
+    box walked by its x-marginal (geometry 13)."""
+    import torch
+    import paper_1708_00765_gb300 as cls
+    from paper_1708_00765_gb300 import workloads
+    n = args.histories or workloads.BOX_L10_HISTORIES
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    arms = ([] if args.no_fp64 else ["fp64"]) + ([] if args.no_fp32 else ["fp32"])
+    if not args.no_projected and not (args.no_fp64 or args.no_fp32):
+        arms += ["fp64_x", "fp32_x"]
+    results = {}
+    samplers = []
+    for arm in arms:
+        params = workloads.BOX_L10_X if arm.endswith("_x") else workloads.BOX_L10
+        prob = cls.Problem(params)
+        prob.set_option("precision", arm[:4])
+        base = rank * (args.warmup + args.steps) * n
+
+        def reset():
+            prob.reset()
+            prob.set_option("first_history", base + args.warmup * n)
+
+        if base:
+            prob.set_option("first_history", base)
+        barrier(pg)
+        sampler = ClockSampler(local)
+        with sampler:
+            times = timed_pass(lambda: prob.run(n, 1, stream=stream), args.steps, args.warmup, flush, torch, stream,
+                               before_timed=reset)
+            barrier(pg)
+        samplers.append(sampler)
+        tal = prob.tallies()
+        prob.close()
+        dev = max_over_ranks(pg, sum(times))
+        rel = tal["sigma_total_flux"] / tal["total_flux"]
+        ops = algorithmic_ops(params, tal) / args.steps
+        ev = tal["n_events"] / args.steps
+        results[arm] = {
+            "histories_per_s": world * args.steps * n / dev, "ms_per_step": 1e3 * dev / args.steps,
+            "events_per_s": world * tal["n_events"] / dev, "collisions_per_s": world * tal["n_coll"] / dev,
+            "events_per_history": tal["n_events"] / tal["n_histories"],
+            "R": tal["R"], "T": tal["T"], "A": tal["A"], "total_flux": tal["total_flux"],
+            "sigma_total_flux": tal["sigma_total_flux"],
+            "fom_total_flux": 1.0 / (rel * rel * dev / world) if rel > 0 else None,
+            "ops_per_launch": ops, "events_per_launch": ev, "launch_s": dev / args.steps}
+    clk = merge_clocks(samplers) if samplers else None
+    clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    full = n == workloads.BOX_L10_HISTORIES
+    names = {"fp64": ("history_kernel<double, 3>", "box"), "fp32": ("history_kernel<float, 3>", "box"),
+             "fp64_x": ("history_kernel<double, 13>", "box_x"), "fp32_x": ("history_kernel<float, 13>", "box_x")}
+    for arm, r in results.items():
+        k, w = names[arm]
+        r["roofline"] = roofline(k, w, r["ops_per_launch"], r["launch_s"], r["events_per_launch"], clk_mhz, full)
+    if "fp64" in results:
+        for arm in ("fp32", "fp64_x", "fp32_x"):
+            if arm in results and results[arm]["fom_total_flux"]:
+                results["fom_ratio_" + arm + "_over_fp64"] = results[arm]["fom_total_flux"] / results["fp64"]["fom_total_flux"]
+    results["clocks"] = clk
+    results["workload"] = BOX_WORKLOAD
+    results["histories_per_step"] = n
+    return results
+
+
+# ------------------------------------------------------------- headline line
+def headline(args, rank, world, pg, local):
+    import torch
+    import paper_1708_00765_gb300 as cls
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the walk never runs on the CPU)")
+    cores = os.cpu_count() or 1
+    # the oracle's pool is spawn-started before this process first touches the GPU
+    pool = oracle_pool(cores) if rank == 0 and (not args.no_oracle or (world == 1 and not args.no_cpu_baseline)) \
+        else None
+    torch.cuda.set_device(local)
+    cls.load(build_if_missing=True)
+    n = args.histories or SWEEP_HISTORIES
+    sw = sweep_arms(args, rank, world, pg, local, pool)
+    box = box_arms(args, rank, world, pg, local) if args.workload == "default" else None
+    if rank != 0:
+        if pool is not None:
+            pool.close()
+        return
+    cases = sweep_cases()
+    clk = merge_clocks([sw["clocks32"]] + ([sw["clocks64"]] if "clocks64" in sw else []))
+    clk_mhz = clk.get("sm_mhz") or 2070.0
+    f32 = sw["fp32_batched"]
+    full = n == SWEEP_HISTORIES
+    line = {
+        "metric": METRIC, "value": f32["histories_per_s"], "unit": "histories/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": f32["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": SWEEP_WORKLOAD, "cases": len(cases), "histories_per_case_per_step": n,
+                   "bins": SWEEP_BINS, "fp32_seed": SEED32, "fp64_seed": SEED64,
+                   "l2": "flushed between steps (512 MB write)"},
+        "clocks": clk,
+        "e2e": sw["e2e"],
+        "gpu_launches": args.steps,
+        "roofline": roofline("history_kernel<float, 0>", "sweep", f32["ops_per_step"],
+                             f32["ms_per_step"] * 1e-3, f32["events_per_step"], clk_mhz, full),
+        "fp32_batched": {k: v for k, v in f32.items() if k not in ("ops_per_step",)},
+    }
+    if "fp64_plain" in sw:
+        p64 = sw["fp64_plain"]
+        line["fp64_plain"] = {
+            "histories_per_s": p64["histories_per_s"], "s_per_pass": p64["s_per_pass"],
+            "events_per_s": p64["events_per_s"], "launches": len(cases),
+            "roofline": roofline("history_kernel<double, 1|3>", "sweep_plain", p64["ops_per_pass"], p64["s_per_pass"],
+                                 p64["events_per_pass"], clk_mhz, False)}
+        line["fom_fp32_batched_over_fp64_plain"] = dict(sw["fom"], note=(
+            "per case, FOM = 1/(sigma_rel^2 T) with T the arm's whole-sweep time; equal N is equal sigma "
+            "(sigma^2 ~ 1/N), so this is also T64/T32 at equal sigma"))
+        line["z_fp32_vs_fp64"] = dict(sw["z_fp32_vs_fp64"], note="independent Philox keys (seeds 1 and 2); "
+                                                                  "R, T, A, <phi> of every case")
+        line["identical_outcomes"] = sw["identical_outcomes"]
+    if "z_fp32_vs_oracle" in sw:
+        line["z_fp32_vs_oracle"] = dict(sw["z_fp32_vs_oracle"], note="FP64 oracle, independent seed, first ids "
+                                                                      "of every case")
+    if box is not None:
+        line["box_L10"] = box
+    if world == 1 and not args.no_cpu_baseline and pool is not None:
+        cb = oracle_sweep_rate(pool, cases, cores)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": "histories/s", "cores": cb["cores"], "kind": "oracle",
+                                "sample": f"{cb['n_per_case']} histories of each of the {len(cases)} sweep cases "
+                                          f"({cb['seconds']:.1f} s)",
+                                "events_per_s": cb["events_per_s"],
+                                "full_workload_s_extrapolated": len(cases) * n / cb["value"]}
+    if pool is not None:
+        pool.close()
+        pool.join()
+    print(json.dumps(line), flush=True)
+
+
+def box_only(args, rank, world, pg, local):
+    import torch
+    import paper_1708_00765_gb300 as cls
+    torch.cuda.set_device(local)
+    cls.load(build_if_missing=True)
+    box = box_arms(args, rank, world, pg, local)
+    if rank == 0:
+        print(json.dumps({"workload": BOX_WORKLOAD, **{k: v for k, v in box.items()}}), flush=True)
+
+
+# -------------------------------------------------------------- diffusive box
+def diffusive_workload(args, rank, world, pg, local):
     """L=100 box, c=0.999, 500 bins, FP32 tracking: history vs event schedule."""
     import torch
     import paper_1708_00765_gb300 as cls
     from paper_1708_00765_gb300 import workloads
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(local)
+    cls.load(build_if_missing=True)
     params = workloads.BOX_DIFFUSIVE
     n = args.histories or workloads.BOX_DIFFUSIVE_HISTORIES
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     out = {}
-    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler = ClockSampler(local)
     with sampler:
         for sched in ("history", "event"):
             prob = cls.Problem(params)
             prob.set_option("precision", "fp32")
             prob.set_option("schedule", sched)
-            dev = timed_runs(prob, n, 1, args.steps, args.warmup, flush, torch, stream,
-                             first_base=rank * (args.warmup + args.steps) * n)
+            base = rank * (args.warmup + args.steps) * n
+
+            def reset():
+                prob.reset()
+                prob.set_option("first_history", base + args.warmup * n)
+
+            times = timed_pass(lambda: prob.run(n, 1, stream=stream), args.steps, args.warmup, flush, torch, stream,
+                               before_timed=reset)
             tal = prob.tallies()
-            dev = max_over_ranks(pg, dev)
+            dev = max_over_ranks(pg, sum(times))
             rel = tal["sigma_total_flux"] / tal["total_flux"]
             out[sched] = {"histories_per_s": world * args.steps * n / dev, "ms_per_step": 1e3 * dev / args.steps,
                           "events_per_s": world * tal["n_events"] / dev,
                           "events_per_history": tal["n_events"] / tal["n_histories"],
                           "max_events": tal["max_events"], "R": tal["R"], "total_flux": tal["total_flux"],
-                          "fom_total_flux": 1.0 / (rel * rel * dev / world)}
+                          "fom_total_flux": 1.0 / (rel * rel * dev / world),
+                          "ops_per_launch": algorithmic_ops(params, tal) / args.steps,
+                          "events_per_launch": tal["n_events"] / args.steps, "launch_s": dev / args.steps}
             prob.close()
     clk_mhz = sampler.summary().get("sm_mhz") or 2070.0
-    peak = SM_COUNT * ISSUE_PER_SM_CLK * clk_mhz * 1e6 / 1e12
+    full = n == workloads.BOX_DIFFUSIVE_HISTORIES
     for sched, r in out.items():
-        ev_s = r["events_per_s"] / world
-        achieved = DIFFUSIVE_WARP_INST_PER_EVENT[sched] * ev_s / 1e12
-        r["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
-                         "frac": achieved / peak, "kernel": f"{sched}_kernel<float, 3, 0>",
-                         "work": f"{DIFFUSIVE_WARP_INST_PER_EVENT[sched]} warp instructions/event",
-                         "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} issue/clk x {clk_mhz} MHz"}
+        r["roofline"] = roofline(f"{sched}_kernel<float, 3>", "diffusive", r["ops_per_launch"], r["launch_s"],
+                                 r["events_per_launch"], clk_mhz, full)
     if rank == 0:
         h = out["history"]
         print(json.dumps({
@@ -298,130 +754,8 @@ def diffusive_workload(args, rank, world, pg):
             "event_over_history": out["event"]["histories_per_s"] / h["histories_per_s"]}), flush=True)
 
 
-def batch_workload(args, rank, world, pg):
-    """256-case sweep at 1e7 histories per case: FP64 plain (one launch per case, no
-    graph, default launch shape) vs FP32 and FP64 batched (all cases in one
-    persistent launch replayed from a CUDA graph, launch shape and schedule chosen
-    by the autotuner), equal N per case."""
-    import torch
-    import paper_1708_00765_gb300 as cls
-    from paper_1708_00765_gb300 import workloads
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    cases = workloads.batch_sweep(256, seed=7, nbins=100)
-    n = args.histories or 10_000_000
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-    t64 = t64b = None
-    tal64 = []
-    same = None
-    with sampler:
-        # FP64 plain: one handle and one launch per case
-        plain = [] if args.no_fp64 else [cls.Problem(c) for c in cases]
-        for p in plain:
-            p.run(min(n, 20_000), 1, stream=stream)  # warm-up
-            p.reset()
-        torch.cuda.synchronize()
-        if plain:
-            flush.zero_()
-            start = torch.cuda.Event(enable_timing=True)
-            stop = torch.cuda.Event(enable_timing=True)
-            start.record(stream)
-            for p in plain:
-                p.run(n, 1, stream=stream)
-            stop.record(stream)
-            torch.cuda.synchronize()
-            t64 = max_over_ranks(pg, start.elapsed_time(stop) * 1e-3)
-            tal64 = [p.tallies() for p in plain]
-            for p in plain:
-                p.close()
-        arms = {}
-        tuned = {}
-        for prec in ("fp32",) if args.no_fp64 else ("fp32", "fp64"):
-            b = cls.Problem(cases, batch=True)
-            b.set_option("precision", prec)
-            tuned[prec] = b.autotune(max(4096, min(n // 16, 262_144)), seed=3, stream=stream)
-            # per-case schedules, kept only if a whole-batch pilot is faster with them
-            # (profiling runs skip them: their pilots would precede the captured launch)
-            if not args.no_fp64:
-                per_case = b.autotune_cases(65_536, seed=3, stream=stream)
-                tuned[prec]["event_schedule_cases"] = sum(1 for c in per_case if c == cls.CLS_SCHED_EVENT)
-            dev = timed_runs(b, n, 1, args.steps, args.warmup, flush, torch, stream)
-            arms[prec] = (max_over_ranks(pg, dev) / args.steps, [b.tallies(k) for k in range(len(cases))])
-            b.close()
-        # identical outcomes: both precisions walk the same histories (seed 11,
-        # ids 0..n-1 of every case) once more, untimed, recording each history's
-        # outcome (reflected / transmitted / absorbed / capped) on the device
-        codes = {}
-        for prec in () if args.no_fp64 else ("fp32", "fp64"):
-            b = cls.Problem(cases, batch=True)
-            b.set_option("precision", prec)
-            b.autotune(max(4096, min(n // 16, 262_144)), seed=3, stream=stream)  # cached: the choice above
-            codes[prec] = torch.empty(len(cases) * n, dtype=torch.uint8, device="cuda")
-            b.record_outcomes(codes[prec].data_ptr(), codes[prec].numel())
-            b.run(n, 11, stream=stream)
-            torch.cuda.synchronize()
-            b.close()
-        if codes:
-            same = (codes["fp32"] == codes["fp64"]).view(len(cases), n).sum(1, dtype=torch.int64).cpu().numpy() / n
-        del codes
-    t32, tal32 = arms["fp32"]
-    events32 = sum(t["n_events"] for t in tal32) / args.steps  # per replay (tallies of the timed steps)
-    clk_mhz = sampler.summary().get("sm_mhz") or 2070.0
-    peak = SM_COUNT * ISSUE_PER_SM_CLK * clk_mhz * 1e6 / 1e12
-    roofline = None
-    if BATCH_FP32_WARP_INST_PER_EVENT is not None:
-        achieved = BATCH_FP32_WARP_INST_PER_EVENT * events32 / t32 / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
-                    "frac": achieved / peak,
-                    "traffic": BATCH_FP32_DRAM_BYTES_PER_LAUNCH if n == 10_000_000 else None,
-                    "kernel": "history_kernel<float, 0, 1>",
-                    "work": f"{BATCH_FP32_WARP_INST_PER_EVENT} warp instructions/event x {events32:.4g} events/replay",
-                    "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} issue/clk x {clk_mhz} MHz (sampled)"}
-    if rank == 0 and args.no_fp64:
-        print(json.dumps({"profiling": "FP32 batched arm only", "fp32_batched": {
-            "histories_per_s": world * len(cases) * n / t32, "s_per_replay": t32, "events_per_replay": events32,
-            "autotuned": tuned["fp32"]}, "roofline": roofline, "clocks": sampler.summary()}), flush=True)
-        return
-    if rank == 0:
-        t64b, tal64b = arms["fp64"]
-        ratios = []
-        zs = []
-        for a, b in zip(tal64, tal32):
-            s64 = a["sigma_total_flux"]
-            s32 = b["sigma_total_flux"]
-            if s64 > 0 and s32 > 0:
-                # FOM = 1 / (sigma^2 T), sigma and T of the same histories: the
-                # batched tallies hold the timed steps' histories (steps x n)
-                ratios.append((s64 * s64 * t64) / (s32 * s32 * t32 * args.steps))
-                zs.append((b["total_flux"] - a["total_flux"]) / math.hypot(s64, s32))
-        ratios.sort()
-        events64 = sum(a["n_events"] for a in tal64)
-        print(json.dumps({
-            "metric": METRIC, "value": world * len(cases) * n / t32, "unit": "histories/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t32, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batched sweep, 256 cases (seed 7), 100 bins", "histories_per_case": n,
-                       "l2": "flushed between steps"},
-            "clocks": sampler.summary(),
-            "fp32_batched": {"histories_per_s": world * len(cases) * n / t32, "s_per_replay": t32,
-                             "events_per_replay": events32, "autotuned": tuned["fp32"]},
-            "roofline": roofline,
-            "fp64_batched": {"histories_per_s": world * len(cases) * n / t64b, "s_per_replay": t64b,
-                             "autotuned": tuned["fp64"]},
-            "fp64_plain": {"histories_per_s": world * len(cases) * n / t64, "s_total": t64,
-                           "events_per_s": events64 / t64},
-            "fom_ratio_fp32_batched_over_fp64_plain": {"median": ratios[len(ratios) // 2], "min": ratios[0],
-                                                       "max": ratios[-1], "cases": len(ratios)},
-            "fp32_vs_fp64_z": {"max_abs": max(abs(z) for z in zs), "rms": math.sqrt(sum(z * z for z in zs) / len(zs)),
-                               "note": "same seed: correlated draws, so this z is conservative"},
-            "fp32_fp64_identical_outcomes": {"median": float(sorted(same)[len(same) // 2]), "min": float(same.min()),
-                                             "max": float(same.max()), "overall": float(same.mean()),
-                                             "histories_per_case": n, "seed": 11},
-        }), flush=True)
-
-
-def suite_workload(args, rank, world, pg):
+# ------------------------------------------------------------- paper's suite
+def suite_workload(args, rank, world, pg, local):
     """The paper's benchmark suite (Tables 1-2 materials; d = 1 slab, 2 extruded,
     3 box; suites I and II): each configuration walked in FP64 on the GPU, timed with
     CUDA events, next to the paper's published CPU rate 1e9 / t_tot (another machine:
@@ -429,7 +763,8 @@ def suite_workload(args, rank, world, pg):
     import torch
     from fractions import Fraction
     import paper_1708_00765_gb300 as cls
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(local)
+    cls.load(build_if_missing=True)
     n = args.histories or 100_000_000
     stream = torch.cuda.current_stream()
     here = os.path.join(ROOT, "tests", "golden")
@@ -442,7 +777,7 @@ def suite_workload(args, rank, world, pg):
     out = []
     tot_t = 0.0
     tot_h = 0
-    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler = ClockSampler(local)
     with sampler:
         for suite, r in rows:
             sig = [float(Fraction(v)) for v in mats[r["case"][0]]["sigma"]]
@@ -506,159 +841,13 @@ def main():
     rank, world, local, pg = dist_setup()
     if args.impl == "reference":
         reference_arm(args, rank, world, pg)
-        return
-    if args.workload != "box":
-        import paper_1708_00765_gb300 as cls
-        cls.load(build_if_missing=True)
-        {"diffusive": diffusive_workload, "batch": batch_workload, "suite": suite_workload}[args.workload](
-            args, rank, world, pg)
+    elif args.workload in ("default", "sweep"):
+        headline(args, rank, world, pg, local)
         barrier(pg)
-        return
-    import torch
-    import paper_1708_00765_gb300 as cls
-    from paper_1708_00765_gb300 import workloads
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA device (the walk never runs on the CPU)")
-    torch.cuda.set_device(local)
-    cls.load(build_if_missing=True)
-    params = workloads.BOX_L10
-    n = args.histories or workloads.BOX_L10_HISTORIES
-    seed = 1
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    results = {}
-    arms = ([] if args.no_fp64 else ["fp64"]) + ([] if args.no_fp32 else ["fp32"])
-    if not args.no_projected and not (args.no_fp64 or args.no_fp32):
-        arms += ["fp64_x", "fp32_x"]
-    clocks = None
-    for arm in arms:
-        prob = cls.Problem(workloads.BOX_L10_X if arm.endswith("_x") else params)
-        prob.set_option("precision", arm[:4])
-        # rank r walks its own history ids: warm-up runs come first, the timed runs follow
-        base = rank * (args.warmup + args.steps) * n
-        if base:
-            prob.set_option("first_history", base)
+    else:
+        {"box": box_only, "diffusive": diffusive_workload, "suite": suite_workload}[args.workload](
+            args, rank, world, pg, local)
         barrier(pg)
-        torch.cuda.synchronize()
-        sampler = ClockSampler(local)
-        with sampler:
-            times = []
-            for i in range(args.warmup + args.steps):
-                flush.zero_()
-                if i == args.warmup:
-                    prob.reset()
-                    if base:
-                        prob.set_option("first_history", base + args.warmup * n)
-                    torch.cuda.synchronize()
-                    barrier(pg)
-                start = torch.cuda.Event(enable_timing=True)
-                stop = torch.cuda.Event(enable_timing=True)
-                start.record(stream)
-                prob.run(n, seed, stream=stream)
-                stop.record(stream)
-                if i >= args.warmup:
-                    times.append((start, stop))
-            torch.cuda.synchronize()
-            barrier(pg)
-        dev_s = sum(a.elapsed_time(b) for a, b in times) * 1e-3
-        if arm == "fp64":
-            clocks = sampler.summary()
-        else:
-            sampler.summary()
-        tal = prob.tallies()
-        dev_max = max_over_ranks(pg, dev_s)
-        hist = world * args.steps * n
-        rel = tal["sigma_total_flux"] / tal["total_flux"]
-        results[arm] = {
-            "histories_per_s": hist / dev_max,
-            "ms_per_step": 1e3 * dev_max / args.steps,
-            "events_per_s": world * tal["n_events"] / dev_max,
-            "collisions_per_s": world * tal["n_coll"] / dev_max,
-            "events_per_history": tal["n_events"] / tal["n_histories"],
-            "R": tal["R"], "T": tal["T"], "A": tal["A"], "total_flux": tal["total_flux"],
-            "sigma_total_flux": tal["sigma_total_flux"],
-            "fom_total_flux": 1.0 / (rel * rel * dev_max / world) if rel > 0 else None,
-            "launch_ms": 1e3 * dev_s / args.steps,
-            "events_per_launch": tal["n_events"] / args.steps,
-        }
-        # end to end through the C ABI: host-side run + tallies (D2H + FP64 normalisation) per step
-        if arm == "fp64":
-            e2e_steps = max(1, args.steps)
-            barrier(pg)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(e2e_steps):
-                prob.run(n, seed, stream=stream)
-                prob.tallies()
-            e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
-            nbatch = prob.get_option("nbatch")
-            results["e2e"] = {"value": world * e2e_steps * n / e2e_s, "unit": "histories/s",
-                              "h2d_bytes_per_step": 48,
-                              "d2h_bytes_per_step": nbatch * int(params[8]) * 8 + 4 * 8 + 9 * 8}
-        prob.close()
-
-    clk_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    if "fp64" in results:
-        r = results["fp64"]
-        ev_s = r["events_per_launch"] / (r["launch_ms"] * 1e-3)
-        achieved = FP64_WARP_INST_PER_EVENT * ev_s / 1e12
-        peak = SM_COUNT * ISSUE_PER_SM_CLK * clk_mhz * 1e6 / 1e12
-        r["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
-                         "frac": achieved / peak, "traffic": FP64_DRAM_BYTES_PER_LAUNCH,
-                         "kernel": "history_kernel<double>",
-                         "work": f"{FP64_WARP_INST_PER_EVENT} warp instructions/event x {r['events_per_launch']:.4g} events/launch",
-                         "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} issue/clk x {clk_mhz} MHz (sampled)",
-                         "fp64_equivalent_tflops": FP64_FLOP_PER_EVENT * ev_s / 1e12,
-                         "fp64_peak_tflops": SM_COUNT * DFMA_PER_SM_CLK * 2 * clk_mhz * 1e6 / 1e12,
-                         "fp64_pipe_active_ncu": FP64_PIPE_ACTIVE}
-    if "fp32" in results:
-        r = results["fp32"]
-        achieved = FP32_WARP_INST_PER_EVENT * r["events_per_launch"] / (r["launch_ms"] * 1e-3) / 1e12
-        peak = SM_COUNT * ISSUE_PER_SM_CLK * clk_mhz * 1e6 / 1e12
-        r["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
-                         "frac": achieved / peak, "kernel": "history_kernel<float>",
-                         "work": f"{FP32_WARP_INST_PER_EVENT} warp instructions/event",
-                         "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} issue/clk x {clk_mhz} MHz"}
-    if rank == 0 and "fp64" not in results:
-        print(json.dumps({"profiling_only": True, **results}), flush=True)
-    elif rank == 0:
-        r64 = results["fp64"]
-        line = {
-            "metric": METRIC, "value": r64["histories_per_s"], "unit": "histories/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r64["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": BOX_WORKLOAD,
-                       "histories_per_step_per_gpu": n, "schedule": "history", "precision": "fp64",
-                       "l2": "flushed between steps (512 MB write)", "seed": seed},
-            "clocks": clocks,
-            "e2e": results["e2e"],
-            "gpu_launches": args.steps,
-            "roofline": r64["roofline"],
-            "fp64": r64,
-        }
-        if "fp32" in results:
-            r32 = results["fp32"]
-            line["fp32"] = r32
-            if r32["fom_total_flux"] and r64["fom_total_flux"]:
-                line["fom_ratio_fp32_over_fp64"] = r32["fom_total_flux"] / r64["fom_total_flux"]
-        for arm in ("fp64_x", "fp32_x"):
-            if arm in results:
-                rx = dict(results[arm])
-                rx["note"] = "same box walked by its x-marginal (geometry 13): same law, fewer draws"
-                line[arm] = rx
-                line["fom_ratio_" + arm + "_over_fp64"] = rx["fom_total_flux"] / r64["fom_total_flux"]
-        if not args.no_cpu_baseline and world == 1:
-            detail = {}
-            rate, ns, dt, used = oracle_rate(params, 10.0, os.cpu_count() or 1, first=10**12, detail=detail)
-            line["cpu_baseline"] = {"value": rate, "unit": "histories/s", "cores": used, "kind": "oracle",
-                                    "sample": f"{ns} histories of the same workload ({dt:.1f} s)",
-                                    "events_per_s": detail["events_per_s"],
-                                    "single_process_histories_per_s": detail["single_process_histories_per_s"],
-                                    "full_workload_s_extrapolated": n / rate}
-        print(json.dumps(line), flush=True)
-    barrier(pg)
     if pg is not None:
         pg.destroy_process_group()
 

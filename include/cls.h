@@ -155,9 +155,13 @@ int cls_set_option(cls_handle *h, int key, int64_t value);
  * value used by the last run).  Errors: CLS_E_INVAL. */
 int cls_get_option(const cls_handle *h, int key, int64_t *value);
 
-/* Enqueue histories [next, next + n_histories) on `stream` and add them to the
- * tallies; next starts at 0 and advances by n_histories, so a sequence of runs
- * equals one long run (checkpoint / resume).  History h draws its random
+/* Walk histories [next, next + n_histories) of CLS Algorithm A (paper Sec. 4:
+ * source, then per event the collision and interface distances drawn afresh,
+ * the boundary distance, and the smallest of the three deciding between
+ * leakage or reflection, scattering or absorption, and a material switch) on
+ * `stream`, and add their track-length and current estimators (paper Sec. 2)
+ * to the tallies; next starts at 0 and advances by n_histories, so a sequence
+ * of runs equals one long run (checkpoint / resume).  History h draws its random
  * numbers from Philox4x32-10 with key `seed` and counter (j/2, h, case), so a
  * run is fully determined by (seed, first history, n).  Asynchronous; the
  * caller must keep the handle alive until the stream has finished.
@@ -166,7 +170,11 @@ int cls_run(cls_handle *h, uint64_t n_histories, uint64_t seed, void *stream);
 
 /* Synchronise with the last run's stream, copy the tallies to the host and
  * normalise them in FP64 into *out (out->flux / out->flux_sigma, if not NULL,
- * receive nbins values).  Errors: CLS_E_STATE (no history run yet),
+ * receive nbins values): the paper's observables (Sec. 2) R = J(x=0),
+ * T = J(x=L), the total flux <phi> and the flux profile phi(x) per unit
+ * incident current, with the standard errors the paper quotes but does not
+ * define (Sec. 5): per-history Bernoulli errors for R, T, A, the per-history
+ * error of <phi>, batch means for phi(x).  Errors: CLS_E_STATE (no history run yet),
  * CLS_E_CUDA, CLS_E_EVENT_LIMIT (out is filled; some histories were capped). */
 int cls_tallies(cls_handle *h, cls_tallies_t *out);
 
@@ -190,6 +198,37 @@ int cls_finalize_raw(const cls_raw_t *raw, const double *flux_batches, const uin
 
 /* Zero the tallies and restart history numbering at 0 (synchronous). */
 int cls_reset(cls_handle *h);
+
+/* ------------------------------------------------ caller-owned device memory */
+/* The paper has no counterpart: these let a caller that manages device memory
+ * itself (a framework's caching allocator, e.g. a PyTorch tensor) hold the
+ * handle's device buffers.
+ *
+ * cls_workspace_bytes: the bytes of device memory the handle needs for its
+ * current cases and options -- flux tallies [cases][nbatch][nbins_stride]
+ * doubles, statistics, counters, the case table, the work list, the work
+ * counters and, when the handle's schedule (or a case's) is the event schedule
+ * or still automatic, the event tracker's particle bank for the current launch
+ * shape (for an automatic schedule, the larger of the autotuner's event
+ * candidates).  Errors: CLS_E_INVAL, CLS_E_CUDA. */
+int cls_workspace_bytes(cls_handle *h, size_t *bytes);
+
+/* cls_bind_workspace: move every device buffer of the handle into the
+ * caller's device memory d_workspace of `bytes` bytes (256-byte aligned, on
+ * the handle's device, at least cls_workspace_bytes): the library frees its
+ * own buffers, copies the case table into the workspace and zeroes the
+ * tallies there (synchronous).  Bytes beyond the other buffers serve as the
+ * event bank, so a larger workspace allows a larger bank.  The caller owns the
+ * memory and must keep it allocated, and untouched, until the handle is
+ * destroyed or unbound; later runs use it and allocate no device memory
+ * (cls_trace and the autotuner's pilot handles still allocate their own).  An
+ * option change whose buffers no longer fit fails with CLS_E_NOMEM (nbatch at
+ * cls_set_option, a larger event bank at the next run); query again and bind
+ * a larger workspace.  d_workspace = NULL returns the handle to library-owned
+ * buffers.  Only before the first run or after cls_reset.
+ * Errors: CLS_E_INVAL (misaligned, not device memory of the handle's device,
+ * too small), CLS_E_STATE (the tallies hold results), CLS_E_NOMEM, CLS_E_CUDA. */
+int cls_bind_workspace(cls_handle *h, void *d_workspace, size_t bytes);
 
 /* Free all device and host resources of the handle (synchronises first). */
 void cls_destroy(cls_handle *h);

@@ -45,7 +45,7 @@ EXPORTED = ("cls_create", "cls_set_option", "cls_get_option", "cls_run", "cls_ta
             "cls_reset", "cls_destroy", "cls_strerror", "cls_trace", "cls_batch_create", "cls_batch_run",
             "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_debug_math", "cls_run_noalloc", "cls_autotune", "cls_finalize_raw",
             "cls_record_outcomes", "cls_batch_set_case_schedule", "cls_batch_get_case_schedule",
-            "cls_autotune_cases")
+            "cls_autotune_cases", "cls_workspace_bytes", "cls_bind_workspace")
 
 CLS_NOALLOC_MAX_CASES = 64
 CLS_NOALLOC_MAX_STRIDE = 4096
@@ -124,6 +124,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "cls_batch_set_case_schedule": ([H, i, i], i),
         "cls_batch_get_case_schedule": ([H, i, P(i)], i),
         "cls_autotune_cases": ([H, u64, u64, H], i),
+        "cls_workspace_bytes": ([H, P(ctypes.c_size_t)], i),
+        "cls_bind_workspace": ([H, H, ctypes.c_size_t], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -248,6 +250,17 @@ class Problem:
         """cls_autotune_cases: returns every case's chosen schedule (CLS_SCHED_*)."""
         _check(load().cls_autotune_cases(self._h, n_pilot, seed, _stream_handle(stream)), "cls_autotune_cases")
         return [self.case_schedule(k) for k in range(self.params.shape[0])]
+
+    def workspace_bytes(self) -> int:
+        """cls_workspace_bytes: device bytes the handle needs for its current options."""
+        out = ctypes.c_size_t()
+        _check(load().cls_workspace_bytes(self._h, ctypes.byref(out)), "cls_workspace_bytes")
+        return out.value
+
+    def bind_workspace(self, d_ptr: int, nbytes: int):
+        """cls_bind_workspace: hold the handle's device buffers in caller-owned device
+        memory at address d_ptr (e.g. a torch tensor's data_ptr()); 0 unbinds."""
+        _check(load().cls_bind_workspace(self._h, d_ptr or None, nbytes if d_ptr else 0), "cls_bind_workspace")
 
     def tallies(self, case: int = 0) -> dict:
         nb = self.nbins[case]

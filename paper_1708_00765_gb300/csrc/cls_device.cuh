@@ -118,7 +118,6 @@ struct Real;
 // like the numbers they encode; the FP64 pipe is left to the arithmetic.
 template <>
 struct Real<double> {
-    using Bin = double;
     static __device__ __forceinline__ unsigned long long k53(uint32_t hi, uint32_t lo) {
         return (((unsigned long long)hi << 32) | (unsigned long long)lo) >> 11;
     }
@@ -253,12 +252,11 @@ struct Real<double> {
     }
 };
 
-// FP32 tracking: position, direction and distances in float; shared-memory
-// tally bins in float, flushed into the FP64 global tallies every few hundred
-// histories; per-history sums convert to FP64 when the history ends.
+// FP32 tracking: position, direction and distances in float; the flights'
+// deposits are summed exactly in a fixed-point difference array and the
+// per-history statistics in FP64 (the tally regions below).
 template <>
 struct Real<float> {
-    using Bin = float;
     // the same draw truncated to its top 24 bits: u = k 2^-24
     static __device__ __forceinline__ float uniform(uint32_t hi, uint32_t) { return (float)(hi >> 8) * 0x1p-24f; }
     static __device__ __forceinline__ float two_u_minus_one(uint32_t hi, uint32_t lo) { return 2.0f * uniform(hi, lo) - 1.0f; }
@@ -765,18 +763,22 @@ __device__ __forceinline__ int step(History<P> &s, const CaseParams &cp, const R
 
 // ------------------------------------------------------- tally regions
 // A warp-private shared-memory region (layout: region_bytes() in
-// cls_internal.h): bins of Real<P>::Bin, FP64 statistics, u64 counters.
-// The difference array of an FP32 region's interior-bin deposits: 64-bit
-// fixed point with 32 fraction bits, added with native integer atomics (no
-// retry loop when a warp's flights share an entry, as on thin slabs) and
-// prefix-summed exactly at the flush.
+// cls_internal.h): the bins, FP64 statistics, u64 counters and the lanes' own
+// FP64 copies of the per-history statistics.  The FP64 walk's bins are
+// doubles; the FP32 walk's are a fixed-point difference array (u64 with 32
+// fraction bits), added with native integer atomics -- no retry loop when a
+// warp's flights share an entry, as on thin slabs -- and prefix-summed exactly
+// at the flush.
 template <typename P>
-__device__ __forceinline__ unsigned long long *region_dif(unsigned char *region, int nbs) {
-    return reinterpret_cast<unsigned long long *>(region + region_dif_offset((int)sizeof(typename Real<P>::Bin), nbs));
+constexpr bool kFixedBins = sizeof(P) == 4;
+
+__device__ __forceinline__ unsigned long long *region_fixed(unsigned char *region) {
+    return reinterpret_cast<unsigned long long *>(region);
 }
 
-// round(c 2^32) for 0 <= c < 2^30, from the float's bit pattern (a float has
-// 24 significant bits, so c >= 2^-8 converts exactly)
+// round(c 2^32) for 0 <= c < 2^31, from the float's bit pattern (a float has
+// 24 significant bits, so c >= 2^-8 converts exactly; smaller values round to
+// the nearest multiple of 2^-32)
 __device__ __forceinline__ unsigned long long fixed32(float c) {
     const uint32_t b = __float_as_uint(c);
     const int e = (int)(b >> 23) - 127;  // c = m 2^(e - 23)
@@ -787,27 +789,24 @@ __device__ __forceinline__ unsigned long long fixed32(float c) {
 }
 
 template <typename P>
-__device__ __forceinline__ typename Real<P>::Bin *region_lane_stats(unsigned char *region, int nbs) {
-    using B = typename Real<P>::Bin;
-    return reinterpret_cast<B *>(region + region_lane_stats_offset((int)sizeof(B), nbs));
+__device__ __forceinline__ double *region_lane_stats(unsigned char *region, int nbs) {
+    return reinterpret_cast<double *>(region + region_lane_stats_offset(kFixedBins<P>, nbs));
 }
 
 template <typename P>
 __device__ __forceinline__ double *region_stats(unsigned char *region, int nbs) {
-    return reinterpret_cast<double *>(region + region_bins_bytes((int)sizeof(typename Real<P>::Bin), nbs));
+    return reinterpret_cast<double *>(region + region_bins_bytes(kFixedBins<P>, nbs));
 }
 
-// The history's track length t and t^2 into this lane's own copy of the
-// region's statistics (no atomics), in the region's precision: FP64 regions in
-// double; FP32 regions in float, as their bins (flushed to FP64 every few
-// hundred histories), so no conversion reaches the narrow FP64 pipe.
+// The history's track length t and t^2 into this lane's own FP64 copy of the
+// region's statistics (no atomics).  The FP32 walk's per-history sums are
+// floats; they are widened here, once per history.
 template <typename P>
 __device__ __forceinline__ void finish_history(unsigned char *region, int nbs, const History<P> &s, int lane) {
-    using B = typename Real<P>::Bin;
-    const B t0 = (B)s.track0;
-    const B t1 = (B)s.track1;
-    const B t = t0 + t1;
-    B *ls = region_lane_stats<P>(region, nbs) + lane;
+    const double t0 = (double)s.track0;
+    const double t1 = (double)s.track1;
+    const double t = t0 + t1;
+    double *ls = region_lane_stats<P>(region, nbs) + lane;
     ls[32 * S_T] += t;
     ls[32 * S_T2] += t * t;
     ls[32 * S_TRACK0] += t0;
@@ -877,10 +876,12 @@ __device__ __forceinline__ void warp_count(unsigned char *regions, int rbytes, i
 // The interior bins of all lanes' flights, spread evenly over the 32 lanes:
 // lane t of each round scores interior task base + t, found by a 5-step
 // shuffle search over the warp's inclusive prefix sum of the interior counts.
+// Lanes with lreg < 2 score into their FP64 region (FP64 walk only: the FP32
+// walk's region lanes take the difference array and bring no tasks here);
+// lanes with lreg == 2 into the FP64 global bins.
 template <typename P>
 __device__ __forceinline__ void spread_interior(unsigned char *regions, int rbytes, int lreg, double *gflux,
                                                 uint64_t goff, int k0, P c, int ni, int lane) {
-    using B = typename Real<P>::Bin;
     int incl = ni;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -905,9 +906,9 @@ __device__ __forceinline__ void spread_interior(unsigned char *regions, int rbyt
         uint64_t ogoff = 0;
         if (any_global) ogoff = __shfl_sync(CLS_FULL_MASK, goff, o);
         if (t < total) {
-            if (oreg < 2) {
-                B *bins = reinterpret_cast<B *>(regions + oreg * rbytes);
-                atomicAdd(&bins[ob + t], (B)oc);
+            if (!kFixedBins<P> && oreg < 2) {
+                double *bins = reinterpret_cast<double *>(regions + oreg * rbytes);
+                atomicAdd(&bins[ob + t], (double)oc);
             } else {
                 atomicAdd(&gflux[ogoff + ob + t], (double)oc);
             }
@@ -915,36 +916,50 @@ __device__ __forceinline__ void spread_interior(unsigned char *regions, int rbyt
     }
 }
 
-// Score the warp's flights.  Each lane adds its two end bins.  Interior bins
-// (c each, k0 < k < k1): in an FP32 region with a difference array (DIF), two
-// entries of that fixed-point array (c at k0 + 1, -c at k1), whose prefix sum
-// the flush adds;
-// otherwise the interior bins of all lanes' flights are spread evenly over the
-// 32 lanes (warp prefix sum of the interior counts, and a 5-step shuffle
-// search for the lane that owns each interior bin), so long flights do not
-// serialise the warp.  FP64 regions score each interior bin exactly: a
-// difference array's prefix sums would cancel between near and far bins.
+// Score the warp's flights.
+//   FP32 walk, region lanes: the flight's bins are a0 in k0, c in each interior
+//   bin k0 < k < k1 and a1 in k1, each rounded once to 32 fraction bits (q0,
+//   qc, q1); as a difference array D (bin k = D[0] + ... + D[k]) that is
+//   D[k0] += q0, D[k0+1] += qc - q0, D[k1] += q1 - qc, D[k1+1] -= q1 -- two
+//   integer atomics for a flight inside one bin, three when it spans two, four
+//   otherwise -- and the flush's prefix sum returns exactly the rounded
+//   deposits, whatever the order of the atomics.
+//   FP64 walk: each lane adds its two end bins, and the interior bins of all
+//   lanes' flights are spread evenly over the 32 lanes (spread_interior), so
+//   long flights do not serialise the warp; each interior bin is added
+//   exactly (a difference array's prefix sums would cancel between near and
+//   far bins, and FP64 parity holds to 1e-12 per bin).
 // A lane with lreg == 2 scores straight into the FP64 global bins at
 // gflux + goff, those of its (case, batch) (see the region eviction in the
 // trackers).
-template <typename P, bool DIF = false>
+template <typename P>
 __device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes, int nbs, int lreg, double *gflux,
                                              uint64_t goff, const Flight<P> &f, int lane) {
-    using B = typename Real<P>::Bin;
-    constexpr bool kDif = sizeof(B) == 4 && DIF;
     const bool has = f.k1 >= f.k0;
     if (has) {
         if (lreg < 2) {
-            B *bins = reinterpret_cast<B *>(regions + lreg * rbytes);
-            atomicAdd(&bins[f.k0], (B)f.a0);
-            if (f.k1 > f.k0) atomicAdd(&bins[f.k1], (B)f.a1);
-            if constexpr (kDif) {
-                if (f.k1 > f.k0 + 1) {
-                    unsigned long long *dif = region_dif<P>(regions + lreg * rbytes, nbs);
-                    const unsigned long long q = fixed32((float)f.c);
-                    atomicAdd(&dif[f.k0 + 1], q);
-                    atomicAdd(&dif[f.k1], 0ull - q);  // modulo 2^64: exact
+            if constexpr (kFixedBins<P>) {
+                unsigned long long *D = region_fixed(regions + lreg * rbytes);
+                const unsigned long long q0 = fixed32((float)f.a0);
+                if (f.k1 == f.k0) {
+                    atomicAdd(&D[f.k0], q0);
+                    atomicAdd(&D[f.k0 + 1], 0ull - q0);  // modulo 2^64: exact
+                } else {
+                    const unsigned long long q1 = fixed32((float)f.a1);
+                    const unsigned long long qc = (f.k1 > f.k0 + 1) ? fixed32((float)f.c) : 0ull;
+                    atomicAdd(&D[f.k0], q0);
+                    if (f.k1 > f.k0 + 1) {
+                        atomicAdd(&D[f.k0 + 1], qc - q0);
+                        atomicAdd(&D[f.k1], q1 - qc);
+                    } else {
+                        atomicAdd(&D[f.k1], q1 - q0);
+                    }
+                    atomicAdd(&D[f.k1 + 1], 0ull - q1);
                 }
+            } else {
+                double *bins = reinterpret_cast<double *>(regions + lreg * rbytes);
+                atomicAdd(&bins[f.k0], (double)f.a0);
+                if (f.k1 > f.k0) atomicAdd(&bins[f.k1], (double)f.a1);
             }
         } else {
             double *gbins = gflux + goff;
@@ -952,7 +967,7 @@ __device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes,
             if (f.k1 > f.k0) atomicAdd(&gbins[f.k1], (double)f.a1);
         }
     }
-    const int ni = (has && !(kDif && lreg < 2)) ? max(f.k1 - f.k0 - 1, 0) : 0;
+    const int ni = (has && !(kFixedBins<P> && lreg < 2)) ? max(f.k1 - f.k0 - 1, 0) : 0;
     if (!__any_sync(CLS_FULL_MASK, ni > 0)) return;  // one vote instead of the scan when no lane has any
     spread_interior<P>(regions, rbytes, lreg, gflux, goff, f.k0, f.c, ni, lane);
 }
@@ -998,50 +1013,46 @@ __device__ __forceinline__ void finish_history_global(const LaunchArgs &a, int c
 
 // Flush a warp region into the global tally block of (case, batch): one global
 // FP64 atomic per non-zero bin, statistic and counter; the region is zeroed.
-template <typename P, bool DIF = false>
+template <typename P>
 __device__ __forceinline__ void flush_region(unsigned char *region, const LaunchArgs &a, int case_index,
                                              uint32_t batch, int lane) {
-    using B = typename Real<P>::Bin;
     const int nbs = a.t.nbins_stride;
     const int nb = a.cases[case_index].nbins;
-    B *bins = reinterpret_cast<B *>(region);
     double *g = a.t.flux + ((size_t)case_index * a.t.nbatch + batch) * (size_t)nbs;
-    if constexpr (DIF && sizeof(B) == 4) {
-        // bins plus the exact prefix sum of the fixed-point difference array, 32 bins at a time
-        unsigned long long *dif = region_dif<P>(region, nbs);
+    if constexpr (kFixedBins<P>) {
+        // the exact prefix sum of the fixed-point difference array, 32 bins at a
+        // time; its entry nb (past the last bin) sums to zero and is cleared
+        unsigned long long *D = region_fixed(region);
         unsigned long long carry = 0ull;
-        for (int base = 0; base < nb; base += 32) {
+        for (int base = 0; base <= nb; base += 32) {
             const int k = base + lane;
-            unsigned long long d = (k < nb) ? dif[k] : 0ull;
+            unsigned long long d = (k <= nb) ? D[k] : 0ull;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned long long v = __shfl_up_sync(CLS_FULL_MASK, d, o);
                 if (lane >= o) d += v;
             }
-            const long long interior = (long long)(carry + d);  // >= 0 up to rounding of the last bit
+            const long long q = (long long)(carry + d);  // the bin's deposits, 2^-32 units
             carry += __shfl_sync(CLS_FULL_MASK, d, 31);
-            if (k < nb) {
-                const double v = (double)bins[k] + (double)interior * 0x1p-32;
-                if (__double_as_longlong(v) != 0) atomicAdd(&g[k], v);
-                bins[k] = B(0);
-                dif[k] = 0ull;
-            }
+            if (k < nb && q != 0) atomicAdd(&g[k], (double)q * 0x1p-32);
+            if (k <= nb) D[k] = 0ull;
         }
     } else {
+        double *bins = reinterpret_cast<double *>(region);
         for (int k = lane; k < nb; k += 32) {
-            const B v = bins[k];
-            if (v != B(0)) {
-                atomicAdd(&g[k], (double)v);
-                bins[k] = B(0);
+            const double v = bins[k];
+            if (v != 0.0) {
+                atomicAdd(&g[k], v);
+                bins[k] = 0.0;
             }
         }
     }
     // the lanes' own copies of the per-history statistics, summed over the warp
-    B *ls = region_lane_stats<P>(region, nbs);
+    double *ls = region_lane_stats<P>(region, nbs);
 #pragma unroll
     for (int q = 0; q < S_NUM; ++q) {
-        double v = (double)ls[32 * q + lane];
-        ls[32 * q + lane] = B(0);
+        double v = ls[32 * q + lane];
+        ls[32 * q + lane] = 0.0;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(CLS_FULL_MASK, v, o);
         if (lane == 0 && __double_as_longlong(v) != 0) atomicAdd(&a.t.stats[(size_t)case_index * S_NUM + q], v);
@@ -1089,28 +1100,25 @@ __device__ __forceinline__ int find_run(const LaunchArgs &a, uint64_t ch) {
 // older region is flushed and re-keyed, and its remaining histories score
 // straight into the FP64 global tallies: the warp never waits for a straggler
 // of a heavy-tailed history-length distribution.
-// Launch bounds: FP32 blocks of 256 threads, 4 per SM (64 registers) with the
-// interior-bin difference array, 3 per SM (80 registers) without it, where the
-// 64-register build spilled about 200 bytes a thread (measured on a 500-bin
-// diffusive box: 33% faster at 3; the difference-array kernels are 3% slower
-// at 3); the 3D box with the difference array takes 4 blocks of 224 threads
-// (history_threads_fp32).  FP64 blocks of at most kHistoryBlockFp64 = 128 threads, 5 per SM
-// (102 registers, 20 warps), 6 (85 registers, 24 warps) for the
-// one-dimensional walks (rod, slab, x-projected box), whose state fits: the
-// FP64 walk is latency-bound, and more resident warps hide its
+// Launch bounds: FP32 blocks of 256 threads, 4 per SM (64 registers); the 3D
+// box takes 4 blocks of 224 threads (history_threads_fp32: 72 registers hold
+// its state without spills).  FP64 blocks of at most kHistoryBlockFp64 = 128
+// threads, 5 per SM (102 registers, 20 warps), 6 (85 registers, 24 warps) for
+// the one-dimensional walks (rod, slab, x-projected box), whose state fits:
+// the FP64 walk is latency-bound, and more resident warps hide its
 // integer-arithmetic and shared-memory latencies (measured: 5% faster for the
 // x-projected box at 6, no gain for the 3D box, which would spill).
-template <typename P, int G, bool DIF>
+template <typename P, int G>
 struct HistoryBounds {
     static constexpr int threads = kHistoryBlockFp64, blocks = (G == 1 || G == 11 || G == 13) ? 6 : 5;
 };
-template <int G, bool DIF>
-struct HistoryBounds<float, G, DIF> {
-    static constexpr int threads = history_threads_fp32(G, DIF), blocks = DIF ? 4 : 3;
+template <int G>
+struct HistoryBounds<float, G> {
+    static constexpr int threads = history_threads_fp32(G), blocks = 4;
 };
 
-template <typename P, int G, bool DIF = false>
-__global__ void __launch_bounds__(HistoryBounds<P, G, DIF>::threads, HistoryBounds<P, G, DIF>::blocks) history_kernel(const LaunchArgs a) {
+template <typename P, int G>
+__global__ void __launch_bounds__(HistoryBounds<P, G>::threads, HistoryBounds<P, G>::blocks) history_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -1169,7 +1177,7 @@ __global__ void __launch_bounds__(HistoryBounds<P, G, DIF>::threads, HistoryBoun
                     const int old_run = r ? key_run1 : key_run0;
                     const uint32_t old_batch = r ? key_batch1 : key_batch0;
                     if (old_run >= 0) {
-                        flush_region<P, DIF>(regions + r * rb, a, a.runs[old_run].case_index, old_batch, lane);
+                        flush_region<P>(regions + r * rb, a, a.runs[old_run].case_index, old_batch, lane);
                         // lanes still walking a history of the old key go on in global memory
                         if (alive && lreg == r) lreg = 2;
                     }
@@ -1216,7 +1224,7 @@ __global__ void __launch_bounds__(HistoryBounds<P, G, DIF>::threads, HistoryBoun
         }
         const uint64_t goff =
             (lreg == 2) ? ((uint64_t)lcase * (uint64_t)a.t.nbatch + lbatch) * (uint64_t)a.t.nbins_stride : 0ull;
-        warp_deposit<P, DIF>(regions, rb, a.t.nbins_stride, lreg, a.t.flux, goff, f, lane);
+        warp_deposit<P>(regions, rb, a.t.nbins_stride, lreg, a.t.flux, goff, f, lane);
         if (out >= 0) {
             record_outcome(a, lcase, s.h_lo, s.h_hi, out);
             if (lreg < 2) {
@@ -1238,19 +1246,19 @@ __global__ void __launch_bounds__(HistoryBounds<P, G, DIF>::threads, HistoryBoun
         if (sizeof(P) == 4 && a.flush_every) {
             if (fed0 >= a.flush_every) {
                 __syncwarp();
-                flush_region<P, DIF>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
+                flush_region<P>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
                 fed0 = 0;
             }
             if (fed1 >= a.flush_every) {
                 __syncwarp();
-                flush_region<P, DIF>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
+                flush_region<P>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
                 fed1 = 0;
             }
         }
     }
     __syncwarp();
-    if (key_run0 >= 0) flush_region<P, DIF>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
-    if (key_run1 >= 0) flush_region<P, DIF>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
+    if (key_run0 >= 0) flush_region<P>(regions, a, a.runs[key_run0].case_index, key_batch0, lane);
+    if (key_run1 >= 0) flush_region<P>(regions + rb, a, a.runs[key_run1].case_index, key_batch1, lane);
 }
 
 // ------------------------------------------------------------ trace kernel

@@ -166,7 +166,7 @@ struct EventMinBlocks {
     static constexpr int value = 2;
 };
 
-template <typename P, int G, bool DIF = false>
+template <typename P, int G>
 __global__ void __launch_bounds__(256, EventMinBlocks<P>::value) event_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256, EventMinBlocks<P>::value) event_kernel(co
                         break;
                     }
                     if (key_run[r] >= 0) {
-                        flush_region<P, DIF>(regions + r * rb, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
+                        flush_region<P>(regions + r * rb, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
                         gen[r] += 1;  // its banked particles now score into global memory
                         live[r] = 0;
                     }
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256, EventMinBlocks<P>::value) event_kernel(co
                 f.k0 = 0;
                 f.k1 = -1;
                 if (alive) o = step<P, false, G>(s, a.cases[ci], key, a.max_events, f, nullptr);
-                warp_deposit<P, DIF>(regions, rb, nbs, reg, a.t.flux, goff, f, lane);
+                warp_deposit<P>(regions, rb, nbs, reg, a.t.flux, goff, f, lane);
                 if (o >= 0) {
                     record_outcome(a, ci, s.h_lo, s.h_hi, o);
                     if (reg < 2) finish_event_history<P>(regions + reg * rb, nbs, s, o);
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(256, EventMinBlocks<P>::value) event_kernel(co
         if (a.flush_every) {
             for (int r = 0; r < 2; ++r) {
                 if (fed[r] >= a.flush_every && key_run[r] >= 0) {
-                    flush_region<P, DIF>(regions + r * rb, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
+                    flush_region<P>(regions + r * rb, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
                     fed[r] = 0;
                 }
             }
@@ -364,25 +364,15 @@ __global__ void __launch_bounds__(256, EventMinBlocks<P>::value) event_kernel(co
     }
     __syncwarp();
     for (int r = 0; r < 2; ++r)
-        if (key_run[r] >= 0) flush_region<P, DIF>(regions + r * rb, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
+        if (key_run[r] >= 0) flush_region<P>(regions + r * rb, a, a.runs[key_run[r]].case_index, key_batch[r], lane);
 }
 
 template <typename P, int G>
 cudaError_t launch_event_g(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
-    if constexpr (sizeof(P) == 4) {
-        if (a.dif) {
-            const cudaError_t e =
-                cudaFuncSetAttribute(event_kernel<P, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            if (e != cudaSuccess) return e;
-            event_kernel<P, G, true><<<grid, block, smem, st>>>(a);
-            return cudaGetLastError();
-        }
-    }
-    {
-        const cudaError_t e = cudaFuncSetAttribute(event_kernel<P, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        event_kernel<P, G, false><<<grid, block, smem, st>>>(a);
-    }
+    static std::atomic<unsigned long long> optin{0};
+    const cudaError_t e = ensure_smem_optin(event_kernel<P, G>, optin);
+    if (e != cudaSuccess) return e;
+    event_kernel<P, G><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -399,22 +389,19 @@ cudaError_t launch_event_impl(const LaunchArgs &a, int grid, int block, size_t s
 }
 
 template <typename P, int G>
-cudaError_t occupancy_event_g(int block, size_t smem, int *blocks_per_sm, bool dif) {
-    if constexpr (sizeof(P) == 4) {
-        if (dif) return occupancy_with_smem(blocks_per_sm, event_kernel<P, G, true>, block, smem);
-    }
-    return occupancy_with_smem(blocks_per_sm, event_kernel<P, G, false>, block, smem);
+cudaError_t occupancy_event_g(int block, size_t smem, int *blocks_per_sm) {
+    return occupancy_with_smem(blocks_per_sm, event_kernel<P, G>, block, smem);
 }
 
 template <typename P>
-cudaError_t occupancy_event_impl(int block, size_t smem, int *blocks_per_sm, int geom, bool dif) {
+cudaError_t occupancy_event_impl(int block, size_t smem, int *blocks_per_sm, int geom) {
     switch (geom) {
-    case 1: return occupancy_event_g<P, 1>(block, smem, blocks_per_sm, dif);
-    case 2: return occupancy_event_g<P, 2>(block, smem, blocks_per_sm, dif);
-    case 3: return occupancy_event_g<P, 3>(block, smem, blocks_per_sm, dif);
-    case 11: return occupancy_event_g<P, 11>(block, smem, blocks_per_sm, dif);
-    case 13: return occupancy_event_g<P, 13>(block, smem, blocks_per_sm, dif);
-    default: return occupancy_event_g<P, 0>(block, smem, blocks_per_sm, dif);
+    case 1: return occupancy_event_g<P, 1>(block, smem, blocks_per_sm);
+    case 2: return occupancy_event_g<P, 2>(block, smem, blocks_per_sm);
+    case 3: return occupancy_event_g<P, 3>(block, smem, blocks_per_sm);
+    case 11: return occupancy_event_g<P, 11>(block, smem, blocks_per_sm);
+    case 13: return occupancy_event_g<P, 13>(block, smem, blocks_per_sm);
+    default: return occupancy_event_g<P, 0>(block, smem, blocks_per_sm);
     }
 }
 

@@ -4,25 +4,13 @@
 
 namespace cls {
 
-template <int G, bool DIF>
-cudaError_t launch_history_gd(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-    static std::atomic<unsigned long long> optin{0};
-    const cudaError_t e = ensure_smem_optin(history_kernel<float, G, DIF>, optin);
-    if (e != cudaSuccess) return e;
-    history_kernel<float, G, DIF><<<grid, block, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-// with or without the interior-bin difference array (LaunchArgs::dif)
 template <int G>
 cudaError_t launch_history_g(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-    return a.dif ? launch_history_gd<G, true>(a, grid, block, smem, s) : launch_history_gd<G, false>(a, grid, block, smem, s);
-}
-
-template <int G>
-cudaError_t occupancy_history_g(int block, size_t smem, int *blocks_per_sm, bool dif) {
-    return dif ? occupancy_with_smem(blocks_per_sm, history_kernel<float, G, true>, block, smem)
-               : occupancy_with_smem(blocks_per_sm, history_kernel<float, G, false>, block, smem);
+    static std::atomic<unsigned long long> optin{0};
+    const cudaError_t e = ensure_smem_optin(history_kernel<float, G>, optin);
+    if (e != cudaSuccess) return e;
+    history_kernel<float, G><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 // One instantiation per geometry (compile-time branches) plus the mixed one.
@@ -46,19 +34,19 @@ cudaError_t launch_trace_fp32(const TraceArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm, int geom, bool dif) {
+cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm, int geom) {
     switch (geom) {
-    case 1: return occupancy_history_g<1>(block, smem, blocks_per_sm, dif);
-    case 2: return occupancy_history_g<2>(block, smem, blocks_per_sm, dif);
-    case 3: return occupancy_history_g<3>(block, smem, blocks_per_sm, dif);
-    case 11: return occupancy_history_g<11>(block, smem, blocks_per_sm, dif);
-    case 13: return occupancy_history_g<13>(block, smem, blocks_per_sm, dif);
-    default: return occupancy_history_g<0>(block, smem, blocks_per_sm, dif);
+    case 1: return occupancy_with_smem(blocks_per_sm, history_kernel<float, 1>, block, smem);
+    case 2: return occupancy_with_smem(blocks_per_sm, history_kernel<float, 2>, block, smem);
+    case 3: return occupancy_with_smem(blocks_per_sm, history_kernel<float, 3>, block, smem);
+    case 11: return occupancy_with_smem(blocks_per_sm, history_kernel<float, 11>, block, smem);
+    case 13: return occupancy_with_smem(blocks_per_sm, history_kernel<float, 13>, block, smem);
+    default: return occupancy_with_smem(blocks_per_sm, history_kernel<float, 0>, block, smem);
     }
 }
 
-cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm, int geom, bool dif) {
-    return occupancy_event_impl<float>(block, smem, blocks_per_sm, geom, dif);
+cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm, int geom) {
+    return occupancy_event_impl<float>(block, smem, blocks_per_sm, geom);
 }
 
 }  // namespace cls

@@ -52,7 +52,7 @@ int event_bank_fields(int precision) {
 }
 
 cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm, int geom) {
-    return occupancy_event_impl<double>(block, smem, blocks_per_sm, geom, false);
+    return occupancy_event_impl<double>(block, smem, blocks_per_sm, geom);
 }
 
 }  // namespace cls

@@ -81,6 +81,11 @@ struct cls_handle {
     // event-schedule bank
     void *d_bank = nullptr;
     size_t bank_bytes = 0;
+    // caller-owned device workspace (cls_bind_workspace) holding every device
+    // buffer above, or null: the library's own allocations
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t ws_bank_off = 0;
     // timing / sync
     cudaStream_t last_stream = nullptr;
     bool ran = false;
@@ -112,15 +117,63 @@ OutcomeRecord *outcome_record(RunCase *runs, size_t ncases) {
 }
 
 void free_tallies(cls_handle *h) {
-    cudaFree(h->d_flux);
-    cudaFree(h->d_stats);
-    cudaFree(h->d_counters);
+    if (!h->ws) {
+        cudaFree(h->d_flux);
+        cudaFree(h->d_stats);
+        cudaFree(h->d_counters);
+    }
     h->d_flux = nullptr;
     h->d_stats = nullptr;
     h->d_counters = nullptr;
 }
 
+// The library's own device buffers (none while a caller's workspace is bound).
+void free_device(cls_handle *h) {
+    free_tallies(h);
+    if (!h->ws) {
+        cudaFree(h->d_cases);
+        cudaFree(h->d_runs);
+        cudaFree(h->d_chunk_counter);
+        cudaFree(h->d_bank);
+    }
+    h->d_cases = nullptr;
+    h->d_runs = nullptr;
+    h->d_chunk_counter = nullptr;
+    h->d_bank = nullptr;
+    h->bank_bytes = 0;
+}
+
+// Byte offsets of the device buffers in a caller's workspace, each 256-byte
+// aligned: flux [cases][nbatch][nbins_stride] doubles, statistics, counters,
+// the case table, the work list, the two work counters, then the event bank.
+struct DevLayout {
+    size_t flux, stats, counters, cases, runs, chunk, bank, total;
+};
+
+DevLayout dev_layout(const cls_handle *h, size_t bank) {
+    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t nc = h->cases.size();
+    DevLayout L;
+    size_t o = 0;
+    L.flux = o;
+    o = up(o + nc * (size_t)h->nbatch * (size_t)h->nbins_stride * sizeof(double));
+    L.stats = o;
+    o = up(o + nc * S_NUM * sizeof(double));
+    L.counters = o;
+    o = up(o + nc * C_NUM * sizeof(unsigned long long));
+    L.cases = o;
+    o = up(o + nc * sizeof(CaseParams));
+    L.runs = o;
+    o = up(o + runs_bytes(nc));
+    L.chunk = o;
+    o = up(o + 2 * sizeof(unsigned long long));
+    L.bank = o;
+    L.total = up(o + bank);
+    return L;
+}
+
 int alloc_tallies(cls_handle *h) {
+    if (h->ws) return CLS_E_STATE;  // a bound workspace is re-carved, not reallocated
     const size_t nc = h->cases.size();
     const size_t nflux = nc * (size_t)h->nbatch * (size_t)h->nbins_stride;
     if (cudaMalloc(&h->d_flux, nflux * sizeof(double)) != cudaSuccess ||
@@ -217,17 +270,12 @@ uint64_t batch_len_for(uint64_t n, int nbatch) {
     return (uint64_t)kBatchQuantum * std::max<uint64_t>(1, (n + q - 1) / q);
 }
 
-bool region_dif_for(const cls_handle *h) {
-    return h->opt.precision == CLS_PREC_FP32 && fp32_region_dif(h->nbins_stride);
-}
-
 int region_bytes_for(const cls_handle *h) {
-    const int bin = (h->opt.precision == CLS_PREC_FP64) ? 8 : 4;
-    return region_bytes(bin, h->nbins_stride, region_dif_for(h));
+    return region_bytes(h->opt.precision == CLS_PREC_FP32, h->nbins_stride);
 }
 
-// FP32 tally bins are flushed into the FP64 global tallies after this many
-// histories per region, which bounds the FP32 partial sums.
+// FP32 regions are flushed into the FP64 global tallies after this many
+// histories, which keeps each bin's fixed-point sum far below its 2^31 range.
 constexpr int kFp32FlushHistories = 1024;
 
 // Schedule of case k: its own, or the handle's.
@@ -288,7 +336,6 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, RunPlan *plan) {
     a.rk = make_round_keys(seed);
     a.max_events = h->opt.max_events;
     a.region_bytes = region_bytes_for(h);
-    a.dif = region_dif_for(h) ? 1 : 0;
     a.flush_every = (h->opt.precision == CLS_PREC_FP32) ? kFp32FlushHistories : 0;
     a.outcomes = outcome_record(h->d_runs, nc);
     plan->ngroups = 0;
@@ -331,16 +378,15 @@ int tracker_shape(cls_handle *h, int region_bytes, int sched, Shape *out) {
     const int fit_warps = (int)std::min<size_t>(kMaxSmemPerBlock / per_warp, 8);
     if (fit_warps < 1) return CLS_E_INVAL;
     // the history trackers' launch bounds
-    const int cap_warps = event ? 8 : fp64 ? kHistoryBlockFp64 / 32 : history_threads_fp32(h->geom, region_dif_for(h)) / 32;
+    const int cap_warps = event ? 8 : fp64 ? kHistoryBlockFp64 / 32 : history_threads_fp32(h->geom) / 32;
     const int block = 32 * std::min(std::min(h->opt.block / 32, fit_warps), cap_warps);
     const size_t smem = (size_t)(block / 32) * per_warp;
     int bps = h->opt.blocks_per_sm;
     if (bps <= 0) {
         const int g = h->geom;
-        const bool dif = region_dif_for(h);
-        cudaError_t e = event ? (fp64 ? occupancy_event_fp64(block, smem, &bps, g) : occupancy_event_fp32(block, smem, &bps, g, dif))
+        cudaError_t e = event ? (fp64 ? occupancy_event_fp64(block, smem, &bps, g) : occupancy_event_fp32(block, smem, &bps, g))
                               : (fp64 ? occupancy_history_fp64(block, smem, &bps, g)
-                                      : occupancy_history_fp32(block, smem, &bps, g, dif));
+                                      : occupancy_history_fp32(block, smem, &bps, g));
         if (e != cudaSuccess) return CLS_E_CUDA;
         if (bps < 1) return CLS_E_INVAL;  // the block does not fit on an SM
     }
@@ -358,6 +404,13 @@ int ensure_bank(cls_handle *h, int sched, const Shape &sh) {
     if (sched != CLS_SCHED_EVENT) return CLS_OK;
     const size_t need = (size_t)sh.grid * (sh.block / 32) * 2 * sh.bank_slots *
                         (size_t)event_bank_fields(h->opt.precision) * 16;
+    if (h->ws) {
+        // the bank takes the bound workspace's bytes after its other buffers
+        if (need > h->ws_bytes - h->ws_bank_off) return CLS_E_NOMEM;
+        h->d_bank = h->ws + h->ws_bank_off;
+        h->bank_bytes = h->ws_bytes - h->ws_bank_off;
+        return CLS_OK;
+    }
     if (need <= h->bank_bytes) return CLS_OK;
     CLS_CUDA(cudaDeviceSynchronize());
     cudaFree(h->d_bank);
@@ -369,6 +422,50 @@ int ensure_bank(cls_handle *h, int sched, const Shape &sh) {
     }
     h->bank_bytes = need;
     return CLS_OK;
+}
+
+// Bytes of event bank the handle's current options need: none unless the
+// handle's schedule (or a case's) is the event schedule or still automatic;
+// for an automatic schedule, the larger of the autotuner's event candidates.
+int bank_need(cls_handle *h, size_t *need) {
+    *need = 0;
+    bool event = h->opt.schedule == CLS_SCHED_EVENT || h->opt.schedule == CLS_SCHED_AUTO;
+    for (size_t k = 0; k < h->cases.size(); ++k) event |= case_schedule(h, (int)k) == CLS_SCHED_EVENT;
+    if (!event) return CLS_OK;
+    const Options saved = h->opt;
+    const int saved_bps = h->used_blocks_per_sm;
+    int rc = CLS_OK;
+    for (int block : {h->opt.block, 128, 256}) {
+        if (block != saved.block && saved.schedule != CLS_SCHED_AUTO) continue;
+        h->opt.block = block;
+        Shape sh;
+        rc = tracker_shape(h, region_bytes_for(h), CLS_SCHED_EVENT, &sh);
+        if (rc) break;
+        *need = std::max(*need, (size_t)sh.grid * (sh.block / 32) * 2 * sh.bank_slots *
+                                    (size_t)event_bank_fields(h->opt.precision) * 16);
+    }
+    h->opt = saved;
+    h->used_blocks_per_sm = saved_bps;
+    return rc;
+}
+
+// Point every device buffer into the bound workspace (layout dev_layout), copy
+// the case table there and zero the tallies.  Synchronous.
+int carve_workspace(cls_handle *h, size_t bank) {
+    const DevLayout L = dev_layout(h, bank);
+    if (L.total > h->ws_bytes) return CLS_E_NOMEM;
+    h->d_flux = reinterpret_cast<double *>(h->ws + L.flux);
+    h->d_stats = reinterpret_cast<double *>(h->ws + L.stats);
+    h->d_counters = reinterpret_cast<unsigned long long *>(h->ws + L.counters);
+    h->d_cases = reinterpret_cast<CaseParams *>(h->ws + L.cases);
+    h->d_runs = reinterpret_cast<RunCase *>(h->ws + L.runs);
+    h->d_chunk_counter = reinterpret_cast<unsigned long long *>(h->ws + L.chunk);
+    h->ws_bank_off = L.bank;
+    h->d_bank = nullptr;
+    h->bank_bytes = 0;
+    destroy_graph(h);  // the captured launches name the old buffers
+    CLS_CUDA(cudaMemcpy(h->d_cases, h->cases.data(), h->cases.size() * sizeof(CaseParams), cudaMemcpyHostToDevice));
+    return zero_tallies(h);
 }
 
 int launch_tracker(cls_handle *h, LaunchArgs a, int sched, const Shape &sh, cudaStream_t s) {
@@ -693,13 +790,29 @@ int cls_set_option(cls_handle *h, int key, int64_t v) {
             // changes the tally layout: only allowed before the first run
             if (h->ran) return CLS_E_STATE;
             CLS_CUDA(cudaSetDevice(h->device));
-            free_tallies(h);
-            h->nbatch = (int)v;
-            o.nbatch = (int)v;
-            int rc = alloc_tallies(h);
-            if (rc) return rc;
-            rc = zero_tallies(h);
-            if (rc) return rc;
+            if (h->ws) {
+                // re-carve the bound workspace, if the new layout fits it
+                const int old = h->nbatch;
+                size_t bank = 0;
+                h->nbatch = (int)v;
+                int rc = bank_need(h, &bank);
+                if (!rc && dev_layout(h, bank).total > h->ws_bytes) rc = CLS_E_NOMEM;
+                if (rc) {
+                    h->nbatch = old;
+                    return rc;
+                }
+                o.nbatch = (int)v;
+                rc = carve_workspace(h, bank);
+                if (rc) return rc;
+            } else {
+                free_tallies(h);
+                h->nbatch = (int)v;
+                o.nbatch = (int)v;
+                int rc = alloc_tallies(h);
+                if (rc) return rc;
+                rc = zero_tallies(h);
+                if (rc) return rc;
+            }
         }
         break;
     case CLS_OPT_MAX_EVENTS:
@@ -991,14 +1104,64 @@ void cls_destroy(cls_handle *h) {
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (cudaEvent_t e : h->ev_pairs) cudaEventDestroy(e);
     if (h->runs_copied) cudaEventDestroy(h->runs_copied);
-    free_tallies(h);
-    cudaFree(h->d_cases);
-    cudaFree(h->d_runs);
-    cudaFree(h->d_chunk_counter);
-    cudaFree(h->d_bank);
+    free_device(h);
     if (h->h_runs) cudaFreeHost(h->h_runs);
     cudaGetLastError();
     delete h;
+}
+
+int cls_workspace_bytes(cls_handle *h, size_t *bytes) {
+    if (!h || !bytes) return CLS_E_INVAL;
+    CLS_CUDA(cudaSetDevice(h->device));
+    size_t bank = 0;
+    const int rc = bank_need(h, &bank);
+    if (rc) return rc;
+    *bytes = dev_layout(h, bank).total;
+    return CLS_OK;
+}
+
+int cls_bind_workspace(cls_handle *h, void *d_workspace, size_t bytes) {
+    if (!h) return CLS_E_INVAL;
+    if (h->ran) return CLS_E_STATE;  // the tallies hold results: cls_reset first
+    CLS_CUDA(cudaSetDevice(h->device));
+    if (!d_workspace) {
+        if (!h->ws) return CLS_OK;
+        // back to the library's own buffers
+        CLS_CUDA(cudaDeviceSynchronize());
+        free_device(h);
+        h->ws = nullptr;
+        h->ws_bytes = h->ws_bank_off = 0;
+        destroy_graph(h);
+        int rc = CLS_OK;
+        if (cudaMalloc(&h->d_cases, h->cases.size() * sizeof(CaseParams)) != cudaSuccess ||
+            cudaMalloc(&h->d_runs, runs_bytes(h->cases.size())) != cudaSuccess ||
+            cudaMalloc(&h->d_chunk_counter, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            rc = CLS_E_NOMEM;
+        }
+        if (!rc) rc = alloc_tallies(h);
+        if (!rc && cudaMemcpy(h->d_cases, h->cases.data(), h->cases.size() * sizeof(CaseParams),
+                              cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = CLS_E_CUDA;
+        if (!rc) rc = zero_tallies(h);
+        return rc;
+    }
+    if (reinterpret_cast<uintptr_t>(d_workspace) & 255u) return CLS_E_INVAL;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, d_workspace) != cudaSuccess) {
+        cudaGetLastError();
+        return CLS_E_INVAL;
+    }
+    if (attr.type != cudaMemoryTypeDevice || attr.device != h->device) return CLS_E_INVAL;
+    size_t bank = 0;
+    int rc = bank_need(h, &bank);
+    if (rc) return rc;
+    if (bytes < dev_layout(h, bank).total) return CLS_E_INVAL;
+    CLS_CUDA(cudaDeviceSynchronize());  // no launch of this handle still uses the old buffers
+    free_device(h);
+    h->ws = static_cast<unsigned char *>(d_workspace);
+    h->ws_bytes = bytes;
+    return carve_workspace(h, bank);
 }
 
 const char *cls_strerror(int code) {

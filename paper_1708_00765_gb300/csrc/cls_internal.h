@@ -110,7 +110,6 @@ struct LaunchArgs {
     uint32_t max_events;
     int region_bytes;     // bytes per warp tally region (see region_bytes())
     int flush_every;      // flush a region after this many histories were fed into it (0: never)
-    int dif;              // FP32 regions carry the difference array of interior-bin deposits
     const OutcomeRecord *outcomes;  // per-history outcome record, or nullptr (never recorded)
     // event schedule only
     void *bank;            // grid warps x 2 buffers x bank_slots particles (SoA)
@@ -130,30 +129,24 @@ struct TraceArgs {
     int *n_rows;
 };
 
-// A warp tally region: nbins_stride bins of the precision's tally type (FP64
-// for the FP64 walk, FP32 for FP32 tracking), padded to 8 bytes, then S_NUM
-// FP64 statistics and C_NUM u64 counters; padded to 16 bytes.
-__host__ __device__ inline int region_bins_bytes(int bin_size, int nbins_stride) { return (nbins_stride * bin_size + 7) & ~7; }
-// After the statistics and counters, each lane's own copy of the per-history
-// statistics (S_NUM x 32 values of the bin type, statistic-major), which a
-// lane updates without atomics when its history ends; the flush sums them
-// over the warp in FP64.
-__host__ __device__ inline int region_lane_stats_offset(int bin_size, int nbins_stride) {
-    return region_bins_bytes(bin_size, nbins_stride) + 8 * (S_NUM + C_NUM);
+// A warp tally region: the bins, then S_NUM FP64 statistics and C_NUM u64
+// counters, then each lane's own copy of the per-history statistics (S_NUM x
+// 32 doubles, statistic-major), which a lane updates without atomics when its
+// history ends and the flush sums over the warp; padded to 16 bytes.
+//   FP64 walk: nbins_stride FP64 bins, each flight scored bin by bin.
+//   FP32 walk: nbins_stride + 1 entries of a fixed-point difference array
+//     (u64, 32 fraction bits): a flight adds its end-bin partials and its
+//     interior-bin length with at most four integer atomics, and the flush
+//     takes the exact prefix sum, so the FP32 walk's deposits are summed
+//     without rounding (FP64 is used from the flush on).
+__host__ __device__ inline int region_bins_bytes(bool fixed, int nbins_stride) {
+    return 8 * (nbins_stride + (fixed ? 1 : 0));
 }
-// An FP32 region may then add a difference array of the interior-bin deposits
-// (64-bit fixed point): a flight adds c at its first interior bin and -c after
-// its last, and the flush takes the prefix sum.
-__host__ __device__ inline int region_dif_offset(int bin_size, int nbins_stride) {
-    return (region_lane_stats_offset(bin_size, nbins_stride) + bin_size * 32 * S_NUM + 7) & ~7;
+__host__ __device__ inline int region_lane_stats_offset(bool fixed, int nbins_stride) {
+    return region_bins_bytes(fixed, nbins_stride) + 8 * (S_NUM + C_NUM);
 }
-__host__ __device__ inline int region_bytes(int bin_size, int nbins_stride, bool dif = false) {
-    return (region_dif_offset(bin_size, nbins_stride) + (dif ? 8 * nbins_stride : 0) + 15) & ~15;
-}
-// FP32 regions carry the difference array while 64 of them (32 warps of two)
-// still fit an SM's shared memory, so that it costs no occupancy.
-__host__ __device__ inline bool fp32_region_dif(int nbins_stride) {
-    return 64 * region_bytes(4, nbins_stride, true) <= 227 * 1024;
+__host__ __device__ inline int region_bytes(bool fixed, int nbins_stride) {
+    return (region_lane_stats_offset(fixed, nbins_stride) + 8 * 32 * S_NUM + 15) & ~15;
 }
 
 // Largest block of the FP64 history tracker (its launch bounds allow 5 such
@@ -161,10 +154,10 @@ __host__ __device__ inline bool fp32_region_dif(int nbins_stride) {
 constexpr int kHistoryBlockFp64 = 128;
 
 // Threads per block the FP32 history tracker is built for (its launch bound,
-// and the host's cap on CLS_OPT_BLOCK): 224 for the 3D box with the
-// interior-bin difference array, whose 72 registers then hold its state
-// without spills (3.6% faster than 256 threads at 64 registers), else 256.
-constexpr int history_threads_fp32(int geom, bool dif) { return (geom == 3 && dif) ? 224 : 256; }
+// and the host's cap on CLS_OPT_BLOCK): 224 for the 3D box, whose 72
+// registers then hold its state without spills (3.6% faster than 256 threads
+// at 64 registers), else 256.
+constexpr int history_threads_fp32(int geom) { return geom == 3 ? 224 : 256; }
 
 // ceil(v 2^bits) for v in [0, 1], exact (scaling by a power of two is exact).
 inline unsigned long long unit_threshold(double v, int bits) {
@@ -182,9 +175,9 @@ cudaError_t launch_event_fp32(const LaunchArgs &a, int grid, int block, size_t s
 cudaError_t launch_trace_fp64(const TraceArgs &a, cudaStream_t s);
 cudaError_t launch_trace_fp32(const TraceArgs &a, cudaStream_t s);
 cudaError_t occupancy_history_fp64(int block, size_t smem, int *blocks_per_sm, int geom);
-cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm, int geom, bool dif);
+cudaError_t occupancy_history_fp32(int block, size_t smem, int *blocks_per_sm, int geom);
 cudaError_t occupancy_event_fp64(int block, size_t smem, int *blocks_per_sm, int geom);
-cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm, int geom, bool dif);
+cudaError_t occupancy_event_fp32(int block, size_t smem, int *blocks_per_sm, int geom);
 int event_bank_fields(int precision); // 16-byte SoA fields per particle (0 = FP64)
 
 }  // namespace cls

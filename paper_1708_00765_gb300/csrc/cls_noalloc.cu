@@ -140,8 +140,7 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
     a.seed = seed;
     a.rk = make_round_keys(seed);
     a.max_events = 100000000u;
-    a.region_bytes = region_bytes((int)sizeof(double), nbins_stride);
-    a.dif = 0;
+    a.region_bytes = region_bytes(false, nbins_stride);
     a.flush_every = 0;
 
     const size_t per_warp = 2 * (size_t)a.region_bytes;

@@ -10,14 +10,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "3", "--histories", "4096"], capture_output=True, text=True, timeout=600,
+                          "--warmup", "3", "--histories", "64"], capture_output=True, text=True, timeout=600,
                          cwd=ROOT, check=True).stdout
     lines = [l for l in out.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "histories/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
-    assert d["config"]["workload"].startswith("box L=10") and d["config"]["histories_per_step_per_gpu"] == 4096
+    assert d["config"]["workload"].startswith("batched sweep: 256 cases")
+    assert d["config"]["cases"] == 256 and d["config"]["histories_per_case_per_step"] == 64
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["events_per_s"] > 0
     assert d["e2e"] == {"value": d["value"], "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -116,13 +116,14 @@ def test_record_too_small_is_refused_and_null_stops_recording():
 
 @pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10])
 def test_fp32_outcomes_mostly_identical_to_fp64(params):
-    """FP32 tracking draws the same variates truncated to 24 bits: most histories end
-    the same way as in FP64; the counts of each outcome stay within 4 standard errors."""
+    """FP32 tracking draws the same variates truncated to 24 bits: all but about one
+    history in 10^6 end the same way as in FP64; the counts of each outcome stay
+    within 4 standard errors."""
     n = 100_000
     c64, _, _ = gpu_codes(params, n, 21)
     c32, _, _ = gpu_codes(params, n, 21, precision="fp32")
     same = float(np.mean(c64 == c32))
-    assert same > 0.8
+    assert same >= 0.9999  # measured: about one history in 10^6 ends differently
     for code in (0, 1, 2):
         p = float(np.mean(c64 == code))
         sd = max(np.sqrt(2 * p * (1 - p) / n), 1.0 / n)

@@ -257,16 +257,93 @@ def test_fp32_statistically_equal(params, kind):
         a = p32.trace(21, h)
         b = p64.trace(21, h)
         same += int(a[-1, 0]) == int(b[-1, 0])
-    assert same / 200 > 0.8
+    assert same >= 199  # measured: about one history in 10^6 ends differently
+
+
+def _host_bins_of_fp32_flights(rows, L, nbins, source_x=0.0):
+    """Score the flights of one FP32 trace on the host in FP64, by the rules of the
+    track-length estimator (paper Sec. 2; the flight's x-extent clipped to [0, L]
+    over |omega_x|, a flight inside one bin scores its length, omega_x = 0 scores
+    in the bin of its start).  Row i holds the position and direction after event
+    i, so flight i starts at row i - 1 (the source for i = 0) and moves along the
+    direction of row i - 1; the first flight's omega_x is its x-extent over its
+    length.  Returns (bins, per-material track)."""
+    f32 = np.float32
+    dx, inv_dx, Lf = f32(L / nbins), f32(nbins / L), f32(L)
+    bins = np.zeros(nbins)
+    track = [0.0, 0.0]
+    x0 = f32(source_x)
+    for i in range(rows.shape[0]):
+        ev, l, x1, m_after = int(rows[i, 0]), float(rows[i, 9]), f32(rows[i, 2]), int(rows[i, 8])
+        if ev == 6:
+            break
+        m = 1 - m_after if ev == 5 else m_after
+        track[m] += l
+        wx = float(rows[i - 1, 5]) if i > 0 else ((float(x1) - float(x0)) / l if l > 0 else 0.0)
+        if l > 0:
+            # bin coordinates in float, as the walk computes them: the bin a flight
+            # end falls in is a decision, taken in the walk's precision
+            lo, hi = max(min(x0, x1), f32(0)), min(max(x0, x1), Lf)
+            if wx == 0.0:
+                bins[min(int(f32(lo * inv_dx)), nbins - 1)] += l
+            else:
+                ulo, uhi = f32(lo * inv_dx), f32(hi * inv_dx)
+                k0, k1 = min(int(ulo), nbins - 1), min(int(uhi), nbins - 1)
+                if k0 == k1:
+                    bins[k0] += l
+                else:
+                    c = float(dx) / abs(wx)
+                    bins[k0] += (1.0 - float(f32(ulo - f32(k0)))) * c
+                    bins[k1] += float(f32(uhi - f32(k1))) * c
+                    bins[k0 + 1:k1] += c
+        x0 = x1
+    return bins, track
+
+
+@pytest.mark.parametrize("params", [workloads.BOX_L10, workloads.ROD_L10, workloads.suite_case("2c", d=11, nbins=50),
+                                    (1.0, 10.0, 0.5, 0.2, 0.99, 0.99, 10.0, 3, 500)])
+def test_fp32_tallies_are_an_fp64_sum_of_the_fp32_flights(params):
+    """FP32 tracking keeps its tallies in FP64 and exact fixed point: each history's
+    flights are summed in float along the walk and widened once, every bin deposit
+    is added exactly (32 fraction bits) and flushed into FP64.  Replayed from the FP32
+    traces of the same histories -- the flights exactly as the walk made them, summed
+    and binned on the host in FP64 -- the run's total track, its square sum and
+    per-material tracks agree within 1e-6 relative (far below 0.01 standard
+    errors), and every flux bin within 1e-4 of its FP64 binning (the walk's
+    approximate reciprocal of omega_x against the host's division; a deposit that
+    landed in the wrong bin, or a fixed-point entry lost, would be off by O(1))."""
+    n = 3000
+    prob = cls.Problem(params)
+    prob.set_option("precision", "fp32")
+    prob.run(n, 7)
+    raw = prob.raw_tallies()
+    tal = prob.tallies()
+    L, nb = float(params[6]), int(params[8])
+    t = np.zeros(n)
+    bins = np.zeros(nb)
+    track = np.zeros(2)
+    for h in range(n):
+        rows = prob.trace(7, h, cap=50_000)
+        assert rows.shape[0] < 50_000
+        t[h] = math.fsum(rows[:, 9])
+        b, tr = _host_bins_of_fp32_flights(rows, L, nb)
+        bins += b
+        track += tr
+    prob.close()
+    sigma_sum = n * tal["sigma_total_flux"]
+    assert abs(raw["sum_t"] - t.sum()) <= 1e-6 * t.sum()
+    assert abs(raw["sum_t"] - t.sum()) <= 0.01 * sigma_sum
+    assert raw["sum_t2"] == pytest.approx(float((t * t).sum()), rel=2e-6)
+    np.testing.assert_allclose(raw["track"], track, rtol=1e-6)
+    np.testing.assert_allclose(raw["flux"].sum(0), bins, rtol=1e-4, atol=1e-6 * bins.max())
 
 
 @pytest.mark.parametrize("schedule", ["history", "event"])
 @pytest.mark.parametrize("nbins", [7, 200, 2000])
 def test_fp32_flux_bins_add_up_to_the_track(schedule, nbins):
-    """FP32 tallies: the bins -- FP32 end-bin partials plus the prefix-summed FP64
-    difference array of the interior bins -- add up to the histories' total track
-    length, also on meshes whose tally regions need more than 48 KB of shared
-    memory per block."""
+    """FP32 tallies: the bins -- the exact prefix sums of the fixed-point difference
+    array -- add up to the histories' total track length, also on meshes whose tally
+    regions need more than 48 KB of shared memory per block."""
     params = (1.0, 10.0, 0.5, 0.2, 0.99, 0.99, 10.0, 3, nbins)
     _, t = gpu_raw(params, 20_000, 5, precision="fp32", schedule=schedule)
     dx = params[6] / nbins
