@@ -294,20 +294,27 @@ def oracle_sweep(pool, cases, seed, first, n):
     return res, order
 
 
-def oracle_sweep_rate(pool, cases, cores, n_per_case=None, seconds_target=12.0, first=10**12):
+def oracle_sweep_rate(pool, cases, cores, n_per_case=None, seconds_target=15.0, first=10**12):
     """Histories/s of the FP64 oracle on a bounded sample of the sweep: the first
     n_per_case ids of every case (sized from a pilot for about seconds_target of work
     when not given), over the spawn pool of `cores` processes."""
     if n_per_case is None:
+        pilot_n = 5000
         t0 = time.perf_counter()
-        res, _ = oracle_sweep(pool, cases, SEED64, first, 200)
+        res, _ = oracle_sweep(pool, cases, SEED64, first, pilot_n)
         res.get()
         pilot = time.perf_counter() - t0
-        n_per_case = int(min(1_000_000, max(200, 200 * seconds_target / max(pilot, 1e-3))))
-    t0 = time.perf_counter()
-    res, _ = oracle_sweep(pool, cases, SEED64, first + 10**9, n_per_case)
-    raws = res.get()
-    dt = time.perf_counter() - t0
+        n_per_case = int(min(5_000_000, max(pilot_n, pilot_n * seconds_target / max(pilot, 1e-3))))
+    sized = n_per_case is not None and seconds_target is None
+    for attempt in range(3):
+        t0 = time.perf_counter()
+        res, _ = oracle_sweep(pool, cases, SEED64, first + (attempt + 1) * 10**9, n_per_case)
+        raws = res.get()
+        dt = time.perf_counter() - t0
+        # the pilot's time is mostly fixed costs: grow the sample until it takes about the target
+        if sized or dt >= 0.5 * seconds_target or n_per_case >= 5_000_000:
+            break
+        n_per_case = int(min(5_000_000, n_per_case * seconds_target / max(dt, 1e-3)))
     n = len(cases) * n_per_case
     return {"value": n / dt, "n_per_case": n_per_case, "seconds": dt, "cores": cores,
             "events_per_s": sum(r["n_events"] for r in raws) / dt}
@@ -325,7 +332,8 @@ def reference_arm(args, rank, world, pg):
     n_case = args.histories
     rates = []
     for i in range(args.warmup + args.steps):
-        r = oracle_sweep_rate(pool, cases, cores, n_per_case=n_case, seconds_target=4.0, first=i * 10**10)
+        r = oracle_sweep_rate(pool, cases, cores, n_per_case=n_case, seconds_target=None if n_case else 4.0,
+                              first=i * 10**10)
         n_case = r["n_per_case"]  # the first step's size, for all steps
         if i >= args.warmup:
             rates.append(r)

@@ -69,9 +69,9 @@ extern "C" {
 #define CLS_OPT_PRECISION 1     /* CLS_PREC_FP64 (default) or CLS_PREC_FP32                 */
 #define CLS_OPT_SCHEDULE 2      /* CLS_SCHED_HISTORY (default), CLS_SCHED_EVENT, CLS_SCHED_AUTO */
 #define CLS_OPT_BLOCK 3         /* threads per block, multiple of 32 in [32, 256]; the FP64
-                                   history tracker uses at most 128 and the FP32 one for the
-                                   3D box on meshes up to 251 bins at most 224 (their launch
-                                   bounds)                                                   */
+                                   history tracker and the event tracker use at most 128, the
+                                   FP32 history tracker for the 3D box at most 224 (their
+                                   launch bounds)                                            */
 #define CLS_OPT_CHUNK 4         /* histories a warp claims at once: 32, 64, ..., 1024       */
 #define CLS_OPT_NBATCH 5        /* statistics batches per run, 2..1024 (default 64)         */
 #define CLS_OPT_MAX_EVENTS 6    /* per-history event cap, 1..2^28 (default 1e8)             */
@@ -83,6 +83,10 @@ extern "C" {
                                   /* processes walk disjoint history ranges of one seed     */
 #define CLS_OPT_SOURCE 11         /* CLS_SOURCE_INCIDENT (default) or CLS_SOURCE_VOLUME, for */
                                   /* every case; only before the first run (CLS_E_STATE)    */
+#define CLS_OPT_GROUP_GEOMETRY 12 /* 1 (default): a batch whose cases have several geometries */
+                                  /* runs one persistent launch per geometry, each compiled   */
+                                  /* for its geometry, as parallel branches of its CUDA graph; */
+                                  /* 0: one launch of the mixed-geometry walk                 */
 
 #define CLS_SOURCE_INCIDENT 0 /* suite I: isotropic incident flux on x = 0, cosine law (Sec. 4.1/4.3) */
 #define CLS_SOURCE_VOLUME 1   /* suite II: one particle, uniform in the volume, isotropic (Sec. 2,    */
@@ -250,7 +254,9 @@ int cls_trace(cls_handle *h, int case_idx, uint64_t seed, uint64_t history, doub
 /* Autotune the handle's launch: time pilot runs of n_pilot histories per case
  * (seed `seed`, history ids far above any a caller uses) for each candidate --
  * history schedule x block {64, 128, 256} x chunk {64, 256, 1024}, and event
- * schedule x block {128, 256} x events per pass {4, 16} -- on a temporary twin
+ * schedule x block {64, 128} x events per pass {4, 16}, each with one launch
+ * per geometry and with one mixed launch for a batch of several geometries
+ * (CLS_OPT_GROUP_GEOMETRY) -- on a temporary twin
  * handle with the same cases and precision, so the handle's own tallies are
  * untouched, then set the fastest candidate's options on the handle.  Results
  * are cached by a signature of (precision, cases) in memory and, if the
@@ -269,10 +275,13 @@ int cls_autotune(cls_handle *h, uint64_t n_pilot, uint64_t seed, void *stream);
  * Errors: as cls_create; ncases in 1..65536. */
 int cls_batch_create(const double *params, int ncases, cls_handle **out);
 
-/* Run n_per_case histories of every case in one persistent launch, its cases
- * ordered by estimated cost (largest first).  The launch sequence (counter
- * reset, tracker, nothing else) is captured once into a CUDA graph and
- * replayed on later calls with new history ranges.  Asynchronous on `stream`.
+/* Run n_per_case histories of every case in one persistent launch per group of
+ * cases (per geometry, CLS_OPT_GROUP_GEOMETRY, and per schedule,
+ * cls_batch_set_case_schedule), each group's cases ordered by estimated cost
+ * (largest first).  The launch sequence (counter reset, the groups' trackers
+ * as parallel graph branches, nothing else) is captured once into a CUDA graph
+ * and replayed on later calls with new history ranges.  Asynchronous on
+ * `stream`.
  * Errors: CLS_E_INVAL, CLS_E_CUDA. */
 int cls_batch_run(cls_handle *h, uint64_t n_per_case, uint64_t seed, void *stream);
 
@@ -285,10 +294,11 @@ int cls_num_cases(const cls_handle *h);
 
 /* Schedule of one case of a batch: CLS_SCHED_HISTORY, CLS_SCHED_EVENT, or
  * CLS_SCHED_AUTO (the default: the handle's CLS_OPT_SCHEDULE).  A batch whose
- * cases have different schedules runs as two persistent launches per
- * cls_batch_run, one per schedule, each over its own cases (largest estimated
- * cost first) and both captured in the batch's CUDA graph; the launch options
- * (block, chunk, bank, events per pass) are the handle's.  Results do not
+ * cases have different schedules runs one persistent launch per schedule (and
+ * per geometry, CLS_OPT_GROUP_GEOMETRY) per cls_batch_run, each over its own
+ * cases (largest estimated cost first) and all captured in the batch's CUDA
+ * graph; the launch options (block, chunk, bank, events per pass) are the
+ * handle's.  Results do not
  * depend on the schedule: both walk every history draw for draw.  Takes
  * effect at the next run.  Errors: CLS_E_INVAL. */
 int cls_batch_set_case_schedule(cls_handle *h, int case_idx, int schedule);

@@ -31,6 +31,7 @@ CLS_OPT_BANK = 8
 CLS_OPT_EVENTS_PER_PASS = 9
 CLS_OPT_FIRST_HISTORY = 10
 CLS_OPT_SOURCE = 11
+CLS_OPT_GROUP_GEOMETRY = 12
 CLS_SOURCE_INCIDENT = 0
 CLS_SOURCE_VOLUME = 1
 
@@ -161,7 +162,8 @@ def _stream_handle(stream) -> int | None:
 OPTIONS = {"precision": CLS_OPT_PRECISION, "schedule": CLS_OPT_SCHEDULE, "block": CLS_OPT_BLOCK,
            "chunk": CLS_OPT_CHUNK, "nbatch": CLS_OPT_NBATCH, "max_events": CLS_OPT_MAX_EVENTS,
            "blocks_per_sm": CLS_OPT_BLOCKS_PER_SM, "bank": CLS_OPT_BANK,
-           "events_per_pass": CLS_OPT_EVENTS_PER_PASS, "first_history": CLS_OPT_FIRST_HISTORY, "source": CLS_OPT_SOURCE}
+           "events_per_pass": CLS_OPT_EVENTS_PER_PASS, "first_history": CLS_OPT_FIRST_HISTORY, "source": CLS_OPT_SOURCE,
+           "group_geometry": CLS_OPT_GROUP_GEOMETRY}
 VALUES = {"fp64": CLS_PREC_FP64, "fp32": CLS_PREC_FP32, "history": CLS_SCHED_HISTORY, "event": CLS_SCHED_EVENT,
           "auto": CLS_SCHED_AUTO, "incident": CLS_SOURCE_INCIDENT, "volume": CLS_SOURCE_VOLUME}
 
@@ -234,7 +236,7 @@ class Problem:
     def autotune(self, n_pilot: int, seed: int = 1, stream=None) -> dict:
         """cls_autotune: returns the chosen schedule and launch shape."""
         _check(load().cls_autotune(self._h, n_pilot, seed, _stream_handle(stream)), "cls_autotune")
-        return {k: self.get_option(k) for k in ("schedule", "block", "chunk", "events_per_pass")}
+        return {k: self.get_option(k) for k in ("schedule", "block", "chunk", "events_per_pass", "group_geometry")}
 
     def set_case_schedule(self, case: int, schedule):
         """cls_batch_set_case_schedule: "history", "event" or "auto" (follow the handle's)."""

@@ -16,6 +16,7 @@
 #pragma once
 
 #include <atomic>
+#include <type_traits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -776,41 +777,61 @@ __device__ __forceinline__ unsigned long long *region_fixed(unsigned char *regio
     return reinterpret_cast<unsigned long long *>(region);
 }
 
-// round(c 2^32) for 0 <= c < 2^31, from the float's bit pattern (a float has
-// 24 significant bits, so c >= 2^-8 converts exactly; smaller values round to
-// the nearest multiple of 2^-32)
-__device__ __forceinline__ unsigned long long fixed32(float c) {
-    const uint32_t b = __float_as_uint(c);
-    const int e = (int)(b >> 23) - 127;  // c = m 2^(e - 23)
-    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
-    const int sh = e + 9;                // c 2^32 = m 2^(e + 9)
-    if (e < -126) return 0ull;          // zero and subnormal
-    return sh >= 0 ? (m << sh) : (sh > -40 ? ((m >> (-sh - 1)) + 1ull) >> 1 : 0ull);
-}
+// round(c 2^32) for 0 <= c < 2^32: scaling by 2^32 is exact in float, and the
+// conversion rounds to the nearest integer (a float has 24 significant bits,
+// so c >= 2^-8 converts exactly; smaller values round to a multiple of 2^-32)
+__device__ __forceinline__ unsigned long long fixed32(float c) { return __float2ull_rn(c * 0x1p32f); }
+
+// The lanes' own copies of the per-history statistics: FP64 in FP64 regions;
+// in FP32 regions u64 fixed point -- t, t0, t1 with 32 fraction bits, t^2 with
+// 24 -- so that the FP32 walk sums them exactly without the FP64 pipe.
+template <typename P>
+using LaneStat = typename std::conditional<kFixedBins<P>, unsigned long long, double>::type;
 
 template <typename P>
-__device__ __forceinline__ double *region_lane_stats(unsigned char *region, int nbs) {
-    return reinterpret_cast<double *>(region + region_lane_stats_offset(kFixedBins<P>, nbs));
+__device__ __forceinline__ LaneStat<P> *region_lane_stats(unsigned char *region, int nbs) {
+    return reinterpret_cast<LaneStat<P> *>(region + region_lane_stats_offset(kFixedBins<P>, nbs));
 }
+
+// A history longer than this (in track length) keeps its statistics out of the
+// fixed-point lane copies: t <= 2^13 is below 2^45 with 32 fraction bits and
+// t^2 below 2^50 with 24, so a lane's sums stay below 2^64 for up to 2^13
+// histories between flushes (FP32 regions flush every 1024).
+constexpr float kFixedTrackMax = 8192.0f;
 
 template <typename P>
 __device__ __forceinline__ double *region_stats(unsigned char *region, int nbs) {
     return reinterpret_cast<double *>(region + region_bins_bytes(kFixedBins<P>, nbs));
 }
 
-// The history's track length t and t^2 into this lane's own FP64 copy of the
-// region's statistics (no atomics).  The FP32 walk's per-history sums are
-// floats; they are widened here, once per history.
+// The history's track length t and t^2 into this lane's own copy of the
+// region's statistics (no atomics).  FP64 walk: in FP64.  FP32 walk: the
+// history's float sums per material, t0 and t1, are rounded once to 32
+// fraction bits and added exactly, t = t0 + t1 from those; t^2 is the square
+// of the float t, rounded to 24 fraction bits.  Returns false, with nothing
+// added, for a history the fixed-point copies cannot hold (track length
+// beyond kFixedTrackMax): the caller adds it to the global FP64 statistics.
 template <typename P>
-__device__ __forceinline__ void finish_history(unsigned char *region, int nbs, const History<P> &s, int lane) {
-    const double t0 = (double)s.track0;
-    const double t1 = (double)s.track1;
-    const double t = t0 + t1;
-    double *ls = region_lane_stats<P>(region, nbs) + lane;
-    ls[32 * S_T] += t;
-    ls[32 * S_T2] += t * t;
-    ls[32 * S_TRACK0] += t0;
-    ls[32 * S_TRACK1] += t1;
+__device__ __forceinline__ bool finish_history(unsigned char *region, int nbs, const History<P> &s, int lane) {
+    LaneStat<P> *ls = region_lane_stats<P>(region, nbs) + lane;
+    if constexpr (kFixedBins<P>) {
+        const float t = s.track0 + s.track1;
+        if (!(t <= kFixedTrackMax)) return false;
+        const unsigned long long q0 = fixed32(s.track0), q1 = fixed32(s.track1);
+        ls[32 * S_T] += q0 + q1;
+        ls[32 * S_T2] += __float2ull_rn(t * t * 0x1p24f);
+        ls[32 * S_TRACK0] += q0;
+        ls[32 * S_TRACK1] += q1;
+    } else {
+        const double t0 = (double)s.track0;
+        const double t1 = (double)s.track1;
+        const double t = t0 + t1;
+        ls[32 * S_T] += t;
+        ls[32 * S_T2] += t * t;
+        ls[32 * S_TRACK0] += t0;
+        ls[32 * S_TRACK1] += t1;
+    }
+    return true;
 }
 
 // Outcome and event counters of the lanes whose history ended this step
@@ -919,9 +940,10 @@ __device__ __forceinline__ void spread_interior(unsigned char *regions, int rbyt
 // Score the warp's flights.
 //   FP32 walk, region lanes: the flight's bins are a0 in k0, c in each interior
 //   bin k0 < k < k1 and a1 in k1, each rounded once to 32 fraction bits (q0,
-//   qc, q1); as a difference array D (bin k = D[0] + ... + D[k]) that is
-//   D[k0] += q0, D[k0+1] += qc - q0, D[k1] += q1 - qc, D[k1+1] -= q1 -- two
-//   integer atomics for a flight inside one bin, three when it spans two, four
+//   qc, q1; zero where the flight has no such bin); as a difference array D
+//   (bin k = D[0] + ... + D[k]) that is D[k0] += q0, D[k0+1] += qc - q0 (or
+//   q1 - q0 when k1 = k0 + 1), D[k1] += q1 - qc, D[k1+1] -= q1 -- two integer
+//   atomics for a flight inside one bin, three when it spans two, four
 //   otherwise -- and the flush's prefix sum returns exactly the rounded
 //   deposits, whatever the order of the atomics.
 //   FP64 walk: each lane adds its two end bins, and the interior bins of all
@@ -939,23 +961,16 @@ __device__ __forceinline__ void warp_deposit(unsigned char *regions, int rbytes,
     if (has) {
         if (lreg < 2) {
             if constexpr (kFixedBins<P>) {
+                // predicated, not branched: every lane with a flight runs the same code
                 unsigned long long *D = region_fixed(regions + lreg * rbytes);
+                const bool multi = f.k1 > f.k0, inter = f.k1 > f.k0 + 1;
                 const unsigned long long q0 = fixed32((float)f.a0);
-                if (f.k1 == f.k0) {
-                    atomicAdd(&D[f.k0], q0);
-                    atomicAdd(&D[f.k0 + 1], 0ull - q0);  // modulo 2^64: exact
-                } else {
-                    const unsigned long long q1 = fixed32((float)f.a1);
-                    const unsigned long long qc = (f.k1 > f.k0 + 1) ? fixed32((float)f.c) : 0ull;
-                    atomicAdd(&D[f.k0], q0);
-                    if (f.k1 > f.k0 + 1) {
-                        atomicAdd(&D[f.k0 + 1], qc - q0);
-                        atomicAdd(&D[f.k1], q1 - qc);
-                    } else {
-                        atomicAdd(&D[f.k1], q1 - q0);
-                    }
-                    atomicAdd(&D[f.k1 + 1], 0ull - q1);
-                }
+                const unsigned long long q1 = fixed32(multi ? (float)f.a1 : 0.0f);
+                const unsigned long long qc = fixed32(inter ? (float)f.c : 0.0f);
+                atomicAdd(&D[f.k0], q0);
+                atomicAdd(&D[f.k0 + 1], (inter ? qc : q1) - q0);  // modulo 2^64: exact
+                if (inter) atomicAdd(&D[f.k1], q1 - qc);
+                if (multi) atomicAdd(&D[f.k1 + 1], 0ull - q1);
             } else {
                 double *bins = reinterpret_cast<double *>(regions + lreg * rbytes);
                 atomicAdd(&bins[f.k0], (double)f.a0);
@@ -986,13 +1001,11 @@ __device__ __forceinline__ void record_outcome(const LaunchArgs &a, int case_ind
     r.codes[(uint64_t)case_index * r.stride + (h - r.first)] = code;
 }
 
-// History end for a lane that scores into global memory: the same statistics
-// and counters as finish_history, added to the case's global tally block.
+// A history's track-length statistics added straight to the case's global
+// FP64 tally block.
 template <typename P>
-__device__ __forceinline__ void finish_history_global(const LaunchArgs &a, int case_index, const History<P> &s,
-                                                      int outcome, bool with_event_counts) {
+__device__ __forceinline__ void add_history_stats_global(const LaunchArgs &a, int case_index, const History<P> &s) {
     double *st = a.t.stats + (size_t)case_index * S_NUM;
-    unsigned long long *ct = a.t.counters + (size_t)case_index * C_NUM;
     const double t0 = (double)s.track0;
     const double t1 = (double)s.track1;
     const double t = t0 + t1;
@@ -1000,6 +1013,15 @@ __device__ __forceinline__ void finish_history_global(const LaunchArgs &a, int c
     atomicAdd(&st[S_T2], t * t);
     if (__double_as_longlong(t0) != 0) atomicAdd(&st[S_TRACK0], t0);
     if (__double_as_longlong(t1) != 0) atomicAdd(&st[S_TRACK1], t1);
+}
+
+// History end for a lane that scores into global memory: the same statistics
+// and counters as finish_history, added to the case's global tally block.
+template <typename P>
+__device__ __forceinline__ void finish_history_global(const LaunchArgs &a, int case_index, const History<P> &s,
+                                                      int outcome, bool with_event_counts) {
+    add_history_stats_global<P>(a, case_index, s);
+    unsigned long long *ct = a.t.counters + (size_t)case_index * C_NUM;
     const int c = (outcome == EV_LEAK_X0) ? C_R : (outcome == EV_LEAK_XL) ? C_T : (outcome == EV_ABSORB) ? C_A : C_CAPPED;
     atomicAdd(&ct[c], 1ull);
     if (with_event_counts) {
@@ -1048,11 +1070,13 @@ __device__ __forceinline__ void flush_region(unsigned char *region, const Launch
         }
     }
     // the lanes' own copies of the per-history statistics, summed over the warp
-    double *ls = region_lane_stats<P>(region, nbs);
+    LaneStat<P> *ls = region_lane_stats<P>(region, nbs);
 #pragma unroll
     for (int q = 0; q < S_NUM; ++q) {
-        double v = ls[32 * q + lane];
-        ls[32 * q + lane] = 0.0;
+        double v;
+        if constexpr (kFixedBins<P>) v = (double)ls[32 * q + lane] * (q == S_T2 ? 0x1p-24 : 0x1p-32);
+        else v = ls[32 * q + lane];
+        ls[32 * q + lane] = 0;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(CLS_FULL_MASK, v, o);
         if (lane == 0 && __double_as_longlong(v) != 0) atomicAdd(&a.t.stats[(size_t)case_index * S_NUM + q], v);
@@ -1228,7 +1252,8 @@ __global__ void __launch_bounds__(HistoryBounds<P, G>::threads, HistoryBounds<P,
         if (out >= 0) {
             record_outcome(a, lcase, s.h_lo, s.h_hi, out);
             if (lreg < 2) {
-                finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, lane);
+                if (!finish_history<P>(regions + lreg * rb, a.t.nbins_stride, s, lane))
+                    add_history_stats_global<P>(a, lcase, s);
                 if constexpr (G != 0)
                     count_one(reinterpret_cast<unsigned long long *>(region_stats<P>(regions + lreg * rb, a.t.nbins_stride) + S_NUM),
                               out, s.n_coll, s.n_int, s.n_refl, s.events);

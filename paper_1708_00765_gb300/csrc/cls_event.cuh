@@ -158,16 +158,16 @@ __device__ __forceinline__ void finish_event_history(unsigned char *region, int 
     atomicMax(&ct[C_MAXEV], (unsigned long long)s.events);
 }
 
-// Blocks per SM the event tracker's registers must allow: 2 (measured on the
-// diffusive box, FP32: 2 blocks at 116 registers run 1.3x faster than 3 blocks
-// at 80 registers with spills).
-template <typename P>
-struct EventMinBlocks {
-    static constexpr int value = 2;
-};
+// Launch bounds of the event tracker: blocks of kEventBlock threads, 5 per SM:
+// 20 warps, 5 per scheduler, whose share of the register file then allows 96
+// registers a thread (the FP32 box spills under 100 bytes).  It ran 2 blocks
+// of 256 threads at up to 128 registers (16 warps) before its per-pass
+// counters became 32-bit.
+constexpr int kEventBlock = kEventBlockThreads;
+constexpr int kEventMinBlocks = 5;
 
 template <typename P, int G>
-__global__ void __launch_bounds__(256, EventMinBlocks<P>::value) event_kernel(const LaunchArgs a) {
+__global__ void __launch_bounds__(kEventBlock, kEventMinBlocks) event_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(256, EventMinBlocks<P>::value) event_kernel(co
 
         // ----------------------------------------------------------- flights
         // collisions, interface crossings, reflections, events of this pass, per region
-        unsigned long long c0 = 0, i0 = 0, f0 = 0, e0 = 0, c1 = 0, i1 = 0, f1 = 0, e1 = 0;
+        uint32_t c0 = 0, i0 = 0, f0 = 0, e0 = 0, c1 = 0, i1 = 0, f1 = 0, e1 = 0;
         uint32_t out = 0;
         for (uint32_t r0 = 0; r0 < nlive; r0 += 32) {
             const uint32_t slot = r0 + lane;

@@ -42,7 +42,12 @@ struct Options {
     int blocks_per_sm = 0;
     int bank = 0;
     int events_per_pass = 4;
+    int group_geometry = 1;  // a batch of mixed geometries: one launch per geometry
 };
+
+// Launch groups of one run: (schedule, geometry) pairs, each its own
+// persistent launch with its own chunk counter.
+constexpr int kMaxGroups = 10;  // 2 schedules x 5 geometries
 
 }  // namespace
 
@@ -91,12 +96,15 @@ struct cls_handle {
     bool ran = false;
     std::vector<cudaEvent_t> ev_pairs;  // start/stop per pending run
     double seconds = 0.0;
-    // batch graph
+    // batch graph: group 0 is captured on capture_stream, group g > 0 on
+    // aux_streams[g - 1], forked after the counter reset and joined at the end
     cudaStream_t capture_stream = nullptr;
+    std::vector<cudaStream_t> aux_streams;
+    std::vector<cudaEvent_t> join_events;  // [0]: the fork, [g]: group g's end
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
-    uint64_t graph_total_chunks[2] = {0, 0};
-    int graph_key[8] = {0};
+    std::vector<uint64_t> graph_total_chunks;
+    int graph_key[9] = {0};
 };
 
 namespace {
@@ -166,7 +174,7 @@ DevLayout dev_layout(const cls_handle *h, size_t bank) {
     L.runs = o;
     o = up(o + runs_bytes(nc));
     L.chunk = o;
-    o = up(o + 2 * sizeof(unsigned long long));
+    o = up(o + kMaxGroups * sizeof(unsigned long long));
     L.bank = o;
     L.total = up(o + bank);
     return L;
@@ -247,7 +255,7 @@ int create_common(const double *params, int ncases, bool batch, cls_handle **out
     int rc = CLS_OK;
     if (cudaMalloc(&h->d_cases, ncases * sizeof(CaseParams)) != cudaSuccess ||
         cudaMalloc(&h->d_runs, runs_bytes(ncases)) != cudaSuccess ||
-        cudaMalloc(&h->d_chunk_counter, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&h->d_chunk_counter, kMaxGroups * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&h->h_runs, runs_bytes(ncases)) != cudaSuccess) {
         rc = CLS_E_NOMEM;
     }
@@ -284,14 +292,55 @@ int case_schedule(const cls_handle *h, int k) {
     return cs != CLS_SCHED_AUTO ? cs : h->opt.schedule;
 }
 
-// One run: a launch per schedule group (one group unless a batch's cases
-// have different schedules).  Group g's cases sit in the work list at
-// runs[off[g] .. off[g] + nruns), largest estimated cost first, with chunk
-// numbers from 0 and chunk counter g.
+// The launch groups of a run: cases grouped by schedule and, when launches
+// are split by geometry, by geometry (a batch of rods and boxes runs the rod
+// walk and the box walk each compiled for its geometry); the handle's schedule
+// first, then the group of largest estimated cost first.  gk[k]: case k's group.
+struct Group {
+    int sched, geom;
+    double cost;
+};
+
+std::vector<Group> plan_groups(const cls_handle *h, std::vector<int> *gk) {
+    std::vector<Group> groups;
+    const int nc = (int)h->cases.size();
+    std::vector<int> of(nc);
+    for (int k = 0; k < nc; ++k) {
+        const int sc = case_schedule(h, k);
+        const int ge = h->opt.group_geometry ? h->cases[k].d : h->geom;
+        int g = 0;
+        while (g < (int)groups.size() && !(groups[g].sched == sc && groups[g].geom == ge)) ++g;
+        if (g == (int)groups.size()) groups.push_back({sc, ge, 0.0});
+        groups[g].cost += h->cases[k].cost;
+        of[k] = g;
+    }
+    std::vector<int> order(groups.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const bool ha = groups[a].sched == h->opt.schedule, hb = groups[b].sched == h->opt.schedule;
+        return ha != hb ? ha : groups[a].cost > groups[b].cost;
+    });
+    std::vector<int> rank(groups.size());
+    std::vector<Group> sorted;
+    for (size_t i = 0; i < order.size(); ++i) {
+        rank[order[i]] = (int)i;
+        sorted.push_back(groups[order[i]]);
+    }
+    if (gk) {
+        gk->resize(nc);
+        for (int k = 0; k < nc; ++k) (*gk)[k] = rank[of[k]];
+    }
+    return sorted;
+}
+
+// One run: a launch per group.  Group g's cases sit in the work list at
+// runs[off .. off + nruns), largest estimated cost first, with chunk numbers
+// from 0 and chunk counter g.
 struct RunPlan {
     int ngroups = 0;
-    int sched[2] = {0, 0};
-    LaunchArgs a[2];
+    int sched[kMaxGroups];
+    int geom[kMaxGroups];
+    LaunchArgs a[kMaxGroups];
 };
 
 // Fill the pinned work list for n histories per case and describe the launches.
@@ -299,34 +348,9 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, RunPlan *plan) {
     // the previous run's copy of the pinned work list must have completed
     CLS_CUDA(cudaEventSynchronize(h->runs_copied));
     const int nc = (int)h->cases.size();
-    const int order_of[2] = {h->opt.schedule, h->opt.schedule == CLS_SCHED_EVENT ? CLS_SCHED_HISTORY : CLS_SCHED_EVENT};
-    int idx = 0, off[2] = {0, 0}, cnt[2] = {0, 0};
-    uint64_t chunks[2] = {0, 0};
-    for (int g = 0; g < 2; ++g) {
-        off[g] = idx;
-        for (int i = 0; i < nc; ++i) {
-            const int k = h->order[i];
-            if (case_schedule(h, k) != order_of[g]) continue;
-            RunCase &r = h->h_runs[idx++];
-            r.first = h->next_history[k];
-            r.n = n;
-            r.batch_len = batch_len_for(n, h->nbatch);
-            r.chunk_begin = chunks[g];
-            r.case_index = k;
-            r.pad = 0;
-            chunks[g] += (n + h->opt.chunk - 1) / h->opt.chunk;
-            ++cnt[g];
-        }
-    }
-    OutcomeRecord *rec = outcome_record(h->h_runs, nc);
-    *rec = OutcomeRecord{nullptr, 0, 0};
-    if (h->outcome_codes) {
-        // every case's row starts at the same history id and holds n codes
-        for (int k = 1; k < nc; ++k)
-            if (h->next_history[k] != h->next_history[0]) return CLS_E_STATE;
-        if (n > h->outcome_cap / (uint64_t)nc) return CLS_E_INVAL;
-        *rec = OutcomeRecord{h->outcome_codes, h->next_history[0], n};
-    }
+    std::vector<int> gk;
+    const std::vector<Group> groups = plan_groups(h, &gk);
+    if ((int)groups.size() > kMaxGroups) return CLS_E_INVAL;
     LaunchArgs a;
     std::memset(&a, 0, sizeof(a));
     a.cases = h->d_cases;
@@ -338,17 +362,40 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, RunPlan *plan) {
     a.region_bytes = region_bytes_for(h);
     a.flush_every = (h->opt.precision == CLS_PREC_FP32) ? kFp32FlushHistories : 0;
     a.outcomes = outcome_record(h->d_runs, nc);
-    plan->ngroups = 0;
-    for (int g = 0; g < 2; ++g) {
-        if (cnt[g] == 0) continue;
-        LaunchArgs &ag = plan->a[plan->ngroups];
+    int idx = 0;
+    plan->ngroups = (int)groups.size();
+    for (int g = 0; g < plan->ngroups; ++g) {
+        const int off = idx;
+        uint64_t chunks = 0;
+        for (int i = 0; i < nc; ++i) {
+            const int k = h->order[i];
+            if (gk[k] != g) continue;
+            RunCase &r = h->h_runs[idx++];
+            r.first = h->next_history[k];
+            r.n = n;
+            r.batch_len = batch_len_for(n, h->nbatch);
+            r.chunk_begin = chunks;
+            r.case_index = k;
+            r.pad = 0;
+            chunks += (n + h->opt.chunk - 1) / h->opt.chunk;
+        }
+        LaunchArgs &ag = plan->a[g];
         ag = a;
-        ag.runs = h->d_runs + off[g];
-        ag.nruns = cnt[g];
-        ag.total_chunks = chunks[g];
-        ag.chunk_counter = h->d_chunk_counter + plan->ngroups;
-        plan->sched[plan->ngroups] = order_of[g];
-        ++plan->ngroups;
+        ag.runs = h->d_runs + off;
+        ag.nruns = idx - off;
+        ag.total_chunks = chunks;
+        ag.chunk_counter = h->d_chunk_counter + g;
+        plan->sched[g] = groups[g].sched;
+        plan->geom[g] = groups[g].geom;
+    }
+    OutcomeRecord *rec = outcome_record(h->h_runs, nc);
+    *rec = OutcomeRecord{nullptr, 0, 0};
+    if (h->outcome_codes) {
+        // every case's row starts at the same history id and holds n codes
+        for (int k = 1; k < nc; ++k)
+            if (h->next_history[k] != h->next_history[0]) return CLS_E_STATE;
+        if (n > h->outcome_cap / (uint64_t)nc) return CLS_E_INVAL;
+        *rec = OutcomeRecord{h->outcome_codes, h->next_history[0], n};
     }
     return CLS_OK;
 }
@@ -368,9 +415,14 @@ struct Shape {
     int grid, block;
     size_t smem;
     uint32_t bank_slots;  // event schedule: slots per block and buffer
+    size_t bank_off;      // event schedule: this launch's slice of the bank
 };
 
-int tracker_shape(cls_handle *h, int region_bytes, int sched, Shape *out) {
+size_t shape_bank_bytes(const cls_handle *h, const Shape &sh) {
+    return (size_t)sh.grid * (sh.block / 32) * 2 * sh.bank_slots * (size_t)event_bank_fields(h->opt.precision) * 16;
+}
+
+int tracker_shape(cls_handle *h, int region_bytes, int sched, int geom, Shape *out) {
     const bool event = sched == CLS_SCHED_EVENT;
     const bool fp64 = h->opt.precision == CLS_PREC_FP64;
     // each warp owns two tally regions; wide meshes get fewer warps per block
@@ -378,12 +430,12 @@ int tracker_shape(cls_handle *h, int region_bytes, int sched, Shape *out) {
     const int fit_warps = (int)std::min<size_t>(kMaxSmemPerBlock / per_warp, 8);
     if (fit_warps < 1) return CLS_E_INVAL;
     // the history trackers' launch bounds
-    const int cap_warps = event ? 8 : fp64 ? kHistoryBlockFp64 / 32 : history_threads_fp32(h->geom) / 32;
+    const int cap_warps = event ? kEventBlockThreads / 32 : fp64 ? kHistoryBlockFp64 / 32 : history_threads_fp32(geom) / 32;
     const int block = 32 * std::min(std::min(h->opt.block / 32, fit_warps), cap_warps);
     const size_t smem = (size_t)(block / 32) * per_warp;
     int bps = h->opt.blocks_per_sm;
     if (bps <= 0) {
-        const int g = h->geom;
+        const int g = geom;
         cudaError_t e = event ? (fp64 ? occupancy_event_fp64(block, smem, &bps, g) : occupancy_event_fp32(block, smem, &bps, g))
                               : (fp64 ? occupancy_history_fp64(block, smem, &bps, g)
                                       : occupancy_history_fp32(block, smem, &bps, g));
@@ -395,15 +447,29 @@ int tracker_shape(cls_handle *h, int region_bytes, int sched, Shape *out) {
     out->block = block;
     out->smem = smem;
     out->bank_slots = event ? (uint32_t)(h->opt.bank > 0 ? ((h->opt.bank + 31) & ~31) : 128) : 0u;
+    out->bank_off = 0;
     return CLS_OK;
 }
 
-// Event schedule: make sure the particle bank (grid warps x 2 buffers x
-// slots x fields x 16 B) is allocated.  Done before any graph capture.
-int ensure_bank(cls_handle *h, int sched, const Shape &sh) {
-    if (sched != CLS_SCHED_EVENT) return CLS_OK;
-    const size_t need = (size_t)sh.grid * (sh.block / 32) * 2 * sh.bank_slots *
-                        (size_t)event_bank_fields(h->opt.precision) * 16;
+// Shapes of a run's launches; the event launches take consecutive slices of
+// one particle bank (grid warps x 2 buffers x slots x fields x 16 B each, all
+// of a run's launches may run at once).  *bank: the bytes they need together.
+int plan_shapes(cls_handle *h, const RunPlan &plan, Shape *sh, size_t *bank) {
+    *bank = 0;
+    for (int g = 0; g < plan.ngroups; ++g) {
+        const int rc = tracker_shape(h, plan.a[g].region_bytes, plan.sched[g], plan.geom[g], &sh[g]);
+        if (rc) return rc;
+        if (plan.sched[g] == CLS_SCHED_EVENT) {
+            sh[g].bank_off = *bank;
+            *bank += (shape_bank_bytes(h, sh[g]) + 255) & ~(size_t)255;
+        }
+    }
+    return CLS_OK;
+}
+
+// Make sure the particle bank holds `need` bytes.  Done before any graph capture.
+int ensure_bank(cls_handle *h, size_t need) {
+    if (need == 0) return CLS_OK;
     if (h->ws) {
         // the bank takes the bound workspace's bytes after its other buffers
         if (need > h->ws_bytes - h->ws_bank_off) return CLS_E_NOMEM;
@@ -425,8 +491,9 @@ int ensure_bank(cls_handle *h, int sched, const Shape &sh) {
 }
 
 // Bytes of event bank the handle's current options need: none unless the
-// handle's schedule (or a case's) is the event schedule or still automatic;
-// for an automatic schedule, the larger of the autotuner's event candidates.
+// handle's schedule (or a case's) is the event schedule or still automatic
+// (then the larger of the autotuner's event candidates, every group on the
+// event schedule).
 int bank_need(cls_handle *h, size_t *need) {
     *need = 0;
     bool event = h->opt.schedule == CLS_SCHED_EVENT || h->opt.schedule == CLS_SCHED_AUTO;
@@ -435,14 +502,24 @@ int bank_need(cls_handle *h, size_t *need) {
     const Options saved = h->opt;
     const int saved_bps = h->used_blocks_per_sm;
     int rc = CLS_OK;
-    for (int block : {h->opt.block, 128, 256}) {
+    for (int block : {h->opt.block, 64, 128}) {
         if (block != saved.block && saved.schedule != CLS_SCHED_AUTO) continue;
         h->opt.block = block;
-        Shape sh;
-        rc = tracker_shape(h, region_bytes_for(h), CLS_SCHED_EVENT, &sh);
+        if (saved.schedule == CLS_SCHED_AUTO) h->opt.schedule = CLS_SCHED_EVENT;
+        RunPlan plan;
+        const std::vector<Group> groups = plan_groups(h, nullptr);
+        plan.ngroups = (int)groups.size();
+        for (int g = 0; g < plan.ngroups; ++g) {
+            plan.sched[g] = groups[g].sched;
+            plan.geom[g] = groups[g].geom;
+            plan.a[g].region_bytes = region_bytes_for(h);
+        }
+        Shape sh[kMaxGroups];
+        size_t bank = 0;
+        rc = plan_shapes(h, plan, sh, &bank);
+        h->opt = saved;
         if (rc) break;
-        *need = std::max(*need, (size_t)sh.grid * (sh.block / 32) * 2 * sh.bank_slots *
-                                    (size_t)event_bank_fields(h->opt.precision) * 16);
+        *need = std::max(*need, bank);
     }
     h->opt = saved;
     h->used_blocks_per_sm = saved_bps;
@@ -468,18 +545,18 @@ int carve_workspace(cls_handle *h, size_t bank) {
     return zero_tallies(h);
 }
 
-int launch_tracker(cls_handle *h, LaunchArgs a, int sched, const Shape &sh, cudaStream_t s) {
+int launch_tracker(cls_handle *h, LaunchArgs a, int sched, int geom, const Shape &sh, cudaStream_t s) {
     cudaError_t e;
     const bool fp64 = h->opt.precision == CLS_PREC_FP64;
     if (sched == CLS_SCHED_EVENT) {
-        a.bank = h->d_bank;
+        a.bank = static_cast<unsigned char *>(h->d_bank) + sh.bank_off;
         a.bank_slots = sh.bank_slots;
         a.events_per_pass = (uint32_t)h->opt.events_per_pass;
-        e = fp64 ? launch_event_fp64(a, sh.grid, sh.block, sh.smem, s, h->geom)
-                 : launch_event_fp32(a, sh.grid, sh.block, sh.smem, s, h->geom);
+        e = fp64 ? launch_event_fp64(a, sh.grid, sh.block, sh.smem, s, geom)
+                 : launch_event_fp32(a, sh.grid, sh.block, sh.smem, s, geom);
     } else {
-        e = fp64 ? launch_history_fp64(a, sh.grid, sh.block, sh.smem, s, h->geom)
-                 : launch_history_fp32(a, sh.grid, sh.block, sh.smem, s, h->geom);
+        e = fp64 ? launch_history_fp64(a, sh.grid, sh.block, sh.smem, s, geom)
+                 : launch_history_fp32(a, sh.grid, sh.block, sh.smem, s, geom);
     }
     return cuda_fail(e);
 }
@@ -619,14 +696,14 @@ int tallies_of(cls_handle *h, int k, cls_tallies_t *out) {
 
 // ------------------------------------------------------------- autotuner
 struct Tuned {
-    int schedule, block, chunk, events_per_pass;
+    int schedule, block, chunk, events_per_pass, group_geometry;
 };
 
 std::mutex g_tune_mutex;
 std::map<std::string, Tuned> g_tune_cache;
 bool g_tune_file_read = false;
 
-// FNV-1a over (precision, nbatch, case parameters): identifies a tuning problem.
+// FNV-1a over (precision, case parameters): identifies a tuning problem.
 std::string tune_signature(const cls_handle *h) {
     unsigned long long x = 1469598103934665603ull;
     auto mix = [&](const void *p, size_t n) {
@@ -652,7 +729,8 @@ void tune_file_load() {
     if (!f) return;
     char key[128];
     Tuned t;
-    while (std::fscanf(f, "%127s %d %d %d %d", key, &t.schedule, &t.block, &t.chunk, &t.events_per_pass) == 5)
+    while (std::fscanf(f, "%127s %d %d %d %d %d", key, &t.schedule, &t.block, &t.chunk, &t.events_per_pass,
+                       &t.group_geometry) == 6)
         g_tune_cache[key] = t;
     std::fclose(f);
 }
@@ -662,7 +740,8 @@ void tune_file_append(const std::string &key, const Tuned &t) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.schedule, t.block, t.chunk, t.events_per_pass);
+    std::fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), t.schedule, t.block, t.chunk, t.events_per_pass,
+                 t.group_geometry);
     std::fclose(f);
 }
 
@@ -671,6 +750,7 @@ void apply_tuned(cls_handle *h, const Tuned &t) {
     h->opt.block = t.block;
     h->opt.chunk = t.chunk;
     h->opt.events_per_pass = t.events_per_pass;
+    h->opt.group_geometry = t.group_geometry;
     destroy_graph(h);
 }
 
@@ -697,10 +777,15 @@ int cls_autotune(cls_handle *h, uint64_t n_pilot, uint64_t seed, void *stream) {
     if (rc) return rc;
     t->opt = h->opt;
     std::vector<Tuned> cand;
-    for (int b : {64, 128, 256})
-        for (int c : {64, 256, 1024}) cand.push_back({CLS_SCHED_HISTORY, b, c, h->opt.events_per_pass});
-    for (int b : {128, 256})
-        for (int e : {4, 16}) cand.push_back({CLS_SCHED_EVENT, b, h->opt.chunk, e});
+    // a batch of several geometries also tries one launch per geometry against one mixed launch
+    std::vector<int> groupings = {h->opt.group_geometry};
+    if (h->geom == 0) groupings = {1, 0};
+    for (int gg : groupings) {
+        for (int b : {64, 128, 256})
+            for (int c : {64, 256, 1024}) cand.push_back({CLS_SCHED_HISTORY, b, c, h->opt.events_per_pass, gg});
+        for (int b : {64, 128})
+            for (int e : {4, 16}) cand.push_back({CLS_SCHED_EVENT, b, h->opt.chunk, e, gg});
+    }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -838,6 +923,10 @@ int cls_set_option(cls_handle *h, int key, int64_t v) {
         CLS_CUDA(cudaSetDevice(h->device));
         CLS_CUDA(cudaMemcpy(h->d_cases, h->cases.data(), h->cases.size() * sizeof(CaseParams), cudaMemcpyHostToDevice));
         break;
+    case CLS_OPT_GROUP_GEOMETRY:
+        if (v != 0 && v != 1) return CLS_E_INVAL;
+        o.group_geometry = (int)v;
+        break;
     case CLS_OPT_FIRST_HISTORY:
         if (v < 0 || v > ((int64_t)1 << 62)) return CLS_E_INVAL;
         for (auto &nh : h->next_history) nh = (uint64_t)v;
@@ -864,6 +953,7 @@ int cls_get_option(const cls_handle *h, int key, int64_t *v) {
     case CLS_OPT_EVENTS_PER_PASS: *v = o.events_per_pass; break;
     case CLS_OPT_FIRST_HISTORY: *v = h->next_history.empty() ? 0 : (int64_t)h->next_history[0]; break;
     case CLS_OPT_SOURCE: *v = h->cases.empty() ? 0 : h->cases[0].source; break;
+    case CLS_OPT_GROUP_GEOMETRY: *v = o.group_geometry; break;
     default: return CLS_E_INVAL;
     }
     return CLS_OK;
@@ -881,18 +971,17 @@ int cls_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
     RunPlan plan;
     int rc = prepare_run(h, n, seed, &plan);
     if (rc) return rc;
-    Shape sh[2];
-    for (int g = 0; g < plan.ngroups && !rc; ++g) {
-        rc = tracker_shape(h, plan.a[g].region_bytes, plan.sched[g], &sh[g]);
-        if (!rc) rc = ensure_bank(h, plan.sched[g], sh[g]);
-    }
+    Shape sh[kMaxGroups];
+    size_t bank = 0;
+    rc = plan_shapes(h, plan, sh, &bank);
+    if (!rc) rc = ensure_bank(h, bank);
     if (rc) return rc;
     rc = record_pair(h, s, true);
     if (rc) return rc;
     CLS_CUDA(cudaMemcpyAsync(h->d_runs, h->h_runs, runs_bytes(h->cases.size()), cudaMemcpyHostToDevice, s));
     CLS_CUDA(cudaEventRecord(h->runs_copied, s));
-    CLS_CUDA(cudaMemsetAsync(h->d_chunk_counter, 0, 2 * sizeof(unsigned long long), s));
-    for (int g = 0; g < plan.ngroups && !rc; ++g) rc = launch_tracker(h, plan.a[g], plan.sched[g], sh[g], s);
+    CLS_CUDA(cudaMemsetAsync(h->d_chunk_counter, 0, kMaxGroups * sizeof(unsigned long long), s));
+    for (int g = 0; g < plan.ngroups && !rc; ++g) rc = launch_tracker(h, plan.a[g], plan.sched[g], plan.geom[g], sh[g], s);
     if (rc) return rc;
     rc = record_pair(h, s, false);
     if (rc) return rc;
@@ -913,28 +1002,46 @@ int cls_batch_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
     RunPlan plan;
     int rc = prepare_run(h, n, seed, &plan);
     if (rc) return rc;
-    // capture {counter reset, one tracker per schedule group} once per (launch
+    // capture {counter reset, one tracker per launch group} once per (launch
     // shape, seed, grouping); later calls only refresh the work list (history
-    // ranges) before replaying the graph
-    const int key[8] = {h->opt.precision, h->opt.schedule, h->opt.block, h->opt.chunk,
-                        (int)h->opt.max_events, h->opt.blocks_per_sm, (int)(seed & 0x7fffffff), (int)(seed >> 31)};
-    const uint64_t tc[2] = {plan.a[0].total_chunks, plan.ngroups > 1 ? plan.a[1].total_chunks : 0};
-    if (h->graph_exec && (tc[0] != h->graph_total_chunks[0] || tc[1] != h->graph_total_chunks[1] ||
-                          std::memcmp(key, h->graph_key, sizeof(key))))
+    // ranges) before replaying the graph.  The groups' launches are parallel
+    // branches of the graph: the second starts its blocks as the first one's
+    // drain, so their tails overlap.
+    const int key[9] = {h->opt.precision, h->opt.schedule, h->opt.block, h->opt.chunk, (int)h->opt.max_events,
+                        h->opt.blocks_per_sm, (int)(seed & 0x7fffffff), (int)(seed >> 31), h->opt.group_geometry};
+    std::vector<uint64_t> tc(plan.ngroups);
+    for (int g = 0; g < plan.ngroups; ++g) tc[g] = plan.a[g].total_chunks;
+    if (h->graph_exec && (tc != h->graph_total_chunks || std::memcmp(key, h->graph_key, sizeof(key))))
         destroy_graph(h);
     if (!h->graph_exec) {
-        Shape sh[2];
-        for (int g = 0; g < plan.ngroups && !rc; ++g) {
-            rc = tracker_shape(h, plan.a[g].region_bytes, plan.sched[g], &sh[g]);
-            if (!rc) rc = ensure_bank(h, plan.sched[g], sh[g]);
-        }
+        Shape sh[kMaxGroups];
+        size_t bank = 0;
+        rc = plan_shapes(h, plan, sh, &bank);
+        if (!rc) rc = ensure_bank(h, bank);
         if (rc) return rc;
         if (!h->capture_stream) CLS_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+        while ((int)h->aux_streams.size() < plan.ngroups - 1) {
+            cudaStream_t a = nullptr;
+            CLS_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+            h->aux_streams.push_back(a);
+        }
+        while ((int)h->join_events.size() < plan.ngroups) {
+            cudaEvent_t e = nullptr;
+            CLS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            h->join_events.push_back(e);
+        }
         CLS_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaMemsetAsync(h->d_chunk_counter, 0, 2 * sizeof(unsigned long long), h->capture_stream);
+        cudaError_t e = cudaMemsetAsync(h->d_chunk_counter, 0, kMaxGroups * sizeof(unsigned long long), h->capture_stream);
+        if (e == cudaSuccess && plan.ngroups > 1) e = cudaEventRecord(h->join_events[0], h->capture_stream);
         int lrc = (e == cudaSuccess) ? CLS_OK : CLS_E_CUDA;
-        for (int g = 0; g < plan.ngroups && !lrc; ++g)
-            lrc = launch_tracker(h, plan.a[g], plan.sched[g], sh[g], h->capture_stream);
+        for (int g = 0; g < plan.ngroups && !lrc; ++g) {
+            cudaStream_t gs = g == 0 ? h->capture_stream : h->aux_streams[g - 1];
+            if (g > 0 && cudaStreamWaitEvent(gs, h->join_events[0], 0) != cudaSuccess) lrc = CLS_E_CUDA;
+            if (!lrc) lrc = launch_tracker(h, plan.a[g], plan.sched[g], plan.geom[g], sh[g], gs);
+            if (!lrc && g > 0 && (cudaEventRecord(h->join_events[g], gs) != cudaSuccess ||
+                                  cudaStreamWaitEvent(h->capture_stream, h->join_events[g], 0) != cudaSuccess))
+                lrc = CLS_E_CUDA;
+        }
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
         if (lrc || e2 != cudaSuccess) {
@@ -947,8 +1054,7 @@ int cls_batch_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
             destroy_graph(h);
             return CLS_E_CUDA;
         }
-        h->graph_total_chunks[0] = tc[0];
-        h->graph_total_chunks[1] = tc[1];
+        h->graph_total_chunks = tc;
         std::memcpy(h->graph_key, key, sizeof(key));
     }
     rc = record_pair(h, s, true);
@@ -1102,6 +1208,8 @@ void cls_destroy(cls_handle *h) {
     cudaDeviceSynchronize();
     destroy_graph(h);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    for (cudaStream_t a : h->aux_streams) cudaStreamDestroy(a);
+    for (cudaEvent_t e : h->join_events) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_pairs) cudaEventDestroy(e);
     if (h->runs_copied) cudaEventDestroy(h->runs_copied);
     free_device(h);
@@ -1135,7 +1243,7 @@ int cls_bind_workspace(cls_handle *h, void *d_workspace, size_t bytes) {
         int rc = CLS_OK;
         if (cudaMalloc(&h->d_cases, h->cases.size() * sizeof(CaseParams)) != cudaSuccess ||
             cudaMalloc(&h->d_runs, runs_bytes(h->cases.size())) != cudaSuccess ||
-            cudaMalloc(&h->d_chunk_counter, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaMalloc(&h->d_chunk_counter, kMaxGroups * sizeof(unsigned long long)) != cudaSuccess) {
             cudaGetLastError();
             rc = CLS_E_NOMEM;
         }

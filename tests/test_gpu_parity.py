@@ -353,9 +353,13 @@ def test_fp32_flux_bins_add_up_to_the_track(schedule, nbins):
 
 # ---------------------------------------------------------------- batches
 
-def test_batch_cases_match_oracle_exactly():
+@pytest.mark.parametrize("group_geometry", [1, 0])
+def test_batch_cases_match_oracle_exactly(group_geometry):
+    """Rods and boxes in one batch: one launch per geometry on parallel graph branches
+    (the default), or one launch of the mixed-geometry walk."""
     params = workloads.batch_sweep(24, seed=7, nbins=20)
     prob = cls.Problem(params, batch=True)
+    prob.set_option("group_geometry", group_geometry)
     prob.run(2000, 9)
     prob.run(1000, 9)  # graph replay with a new history range
     for k in range(params.shape[0]):
@@ -550,7 +554,7 @@ def test_autotune_file_cache(tmp_path):
         assert out.returncode == 0, out.stderr
     lines = cache.read_text().splitlines()
     assert len(lines) == 1  # the second process found the first one's result
-    key, sched, block, chunk, epp = lines[0].split()
+    key, sched, block, chunk, epp, gg = lines[0].split()
     assert int(sched) in (1, 2) and int(block) in (64, 128, 256)
 
 
