@@ -109,15 +109,22 @@ KERNEL_COUNTS = os.path.join(ROOT, "profiles", "kernel_counts.csv")
 
 
 def kernel_counts(kernel: str, workload: str):
-    """Warp instructions and DRAM bytes of one full-size launch, from the committed
-    ncu summary of the current kernels (None when it holds no row for them)."""
+    """Events, warp and thread instructions and DRAM bytes of one launch of each kernel
+    named in `kernel` ("a + b": summed), from the committed ncu summary of the
+    current kernels (None when it lacks a row for one of them)."""
     if not os.path.exists(KERNEL_COUNTS):
         return None
+    keys = ("events", "warp_inst", "thread_inst", "dram_read", "dram_write", "duration_ms")
     with open(KERNEL_COUNTS) as f:
-        for row in csv.DictReader(line for line in f if not line.startswith("#")):
-            if row["kernel"] == kernel and row["workload"] == workload:
-                return {k: float(row[k]) for k in ("events", "warp_inst", "dram_read", "dram_write", "duration_ms")}
-    return None
+        rows = list(csv.DictReader(line for line in f if not line.startswith("#")))
+    out = dict.fromkeys(keys, 0.0)
+    for k in (x.strip() for x in kernel.split("+")):
+        row = next((r for r in rows if r["kernel"] == k and r["workload"] == workload), None)
+        if row is None:
+            return None
+        for key in keys:
+            out[key] += float(row[key])
+    return out
 
 
 def roofline(kernel, workload, ops_per_launch, launch_s, events_per_launch, clk_mhz, n_full: bool):
@@ -133,11 +140,14 @@ def roofline(kernel, workload, ops_per_launch, launch_s, events_per_launch, clk_
            "peak_from": f"{SM_COUNT} SM x {ISSUE_PER_SM_CLK} schedulers x {LANES} lanes x {clk_mhz} MHz (sampled)",
            "issue": None}
     kc = kernel_counts(kernel, workload)
-    if kc is not None and n_full:
+    if kc is not None:
         per_event = kc["warp_inst"] / kc["events"]
         issue_peak = SM_COUNT * ISSUE_PER_SM_CLK * clk_mhz * 1e6
-        out["traffic"] = kc["dram_read"] + kc["dram_write"]
+        # DRAM traffic scales with the launch only while it is the tallies' first touch: kept
+        # for a launch of the captured size
+        out["traffic"] = kc["dram_read"] + kc["dram_write"] if n_full else None
         out["issue"] = {"warp_inst_per_event": per_event,
+                        "threads_per_warp_inst": kc["thread_inst"] / kc["warp_inst"],
                         "frac": per_event * events_per_launch / launch_s / issue_peak,
                         "source": os.path.relpath(KERNEL_COUNTS, ROOT)}
     return out
@@ -651,7 +661,9 @@ def headline(args, rank, world, pg, local):
     clk = merge_clocks([sw["clocks32"]] + ([sw["clocks64"]] if "clocks64" in sw else []))
     clk_mhz = clk.get("sm_mhz") or 2070.0
     f32 = sw["fp32_batched"]
-    full = n == SWEEP_HISTORIES
+    # the sweep's DRAM traffic is its tallies' first touch (13 MB, in L2 afterwards), the same at any
+    # histories per case: the ncu capture at 1e7 per case stands for the full launch
+    full = True
     line = {
         "metric": METRIC, "value": f32["histories_per_s"], "unit": "histories/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": f32["ms_per_step"],
@@ -662,7 +674,7 @@ def headline(args, rank, world, pg, local):
         "clocks": clk,
         "e2e": sw["e2e"],
         "gpu_launches": args.steps,
-        "roofline": roofline("history_kernel<float, 0>", "sweep", f32["ops_per_step"],
+        "roofline": roofline(sweep_kernels(f32["autotuned"]), "sweep", f32["ops_per_step"],
                              f32["ms_per_step"] * 1e-3, f32["events_per_step"], clk_mhz, full),
         "fp32_batched": {k: v for k, v in f32.items() if k not in ("ops_per_step",)},
     }
@@ -695,6 +707,13 @@ def headline(args, rank, world, pg, local):
         pool.close()
         pool.join()
     print(json.dumps(line), flush=True)
+
+
+def sweep_kernels(tuned) -> str:
+    """The FP32 sweep's kernels: one mixed-geometry launch, or one per geometry (rods, boxes)."""
+    if tuned.get("group_geometry", 0):
+        return "history_kernel<float, 1> + history_kernel<float, 3>"
+    return "history_kernel<float, 0>"
 
 
 def box_only(args, rank, world, pg, local):

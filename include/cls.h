@@ -69,9 +69,8 @@ extern "C" {
 #define CLS_OPT_PRECISION 1     /* CLS_PREC_FP64 (default) or CLS_PREC_FP32                 */
 #define CLS_OPT_SCHEDULE 2      /* CLS_SCHED_HISTORY (default), CLS_SCHED_EVENT, CLS_SCHED_AUTO */
 #define CLS_OPT_BLOCK 3         /* threads per block, multiple of 32 in [32, 256]; the FP64
-                                   history tracker and the event tracker use at most 128, the
-                                   FP32 history tracker for the 3D box at most 224 (their
-                                   launch bounds)                                            */
+                                   history tracker uses at most 128, the FP32 history tracker
+                                   for the 3D box at most 224 (their launch bounds)          */
 #define CLS_OPT_CHUNK 4         /* histories a warp claims at once: 32, 64, ..., 1024       */
 #define CLS_OPT_NBATCH 5        /* statistics batches per run, 2..1024 (default 64)         */
 #define CLS_OPT_MAX_EVENTS 6    /* per-history event cap, 1..2^28 (default 1e8)             */
@@ -254,7 +253,7 @@ int cls_trace(cls_handle *h, int case_idx, uint64_t seed, uint64_t history, doub
 /* Autotune the handle's launch: time pilot runs of n_pilot histories per case
  * (seed `seed`, history ids far above any a caller uses) for each candidate --
  * history schedule x block {64, 128, 256} x chunk {64, 256, 1024}, and event
- * schedule x block {64, 128} x events per pass {4, 16}, each with one launch
+ * schedule x block {128, 256} x events per pass {4, 16}, each with one launch
  * per geometry and with one mixed launch for a batch of several geometries
  * (CLS_OPT_GROUP_GEOMETRY) -- on a temporary twin
  * handle with the same cases and precision, so the handle's own tallies are

@@ -158,13 +158,13 @@ __device__ __forceinline__ void finish_event_history(unsigned char *region, int 
     atomicMax(&ct[C_MAXEV], (unsigned long long)s.events);
 }
 
-// Launch bounds of the event tracker: blocks of kEventBlock threads, 5 per SM:
-// 20 warps, 5 per scheduler, whose share of the register file then allows 96
-// registers a thread (the FP32 box spills under 100 bytes).  It ran 2 blocks
-// of 256 threads at up to 128 registers (16 warps) before its per-pass
-// counters became 32-bit.
+// Launch bounds of the event tracker: blocks of up to kEventBlock = 256
+// threads, 2 per SM (16 warps, up to 128 registers a thread).  Measured on the
+// diffusive box (FP32, 2e7 histories): 5 blocks of 128 threads (20 warps, 96
+// registers, about 100 bytes spilled) ran 15% slower, and 3 blocks of 256 at
+// 80 registers (about 350 bytes spilled) 1.3x slower.
 constexpr int kEventBlock = kEventBlockThreads;
-constexpr int kEventMinBlocks = 5;
+constexpr int kEventMinBlocks = 2;
 
 template <typename P, int G>
 __global__ void __launch_bounds__(kEventBlock, kEventMinBlocks) event_kernel(const LaunchArgs a) {

@@ -502,7 +502,7 @@ int bank_need(cls_handle *h, size_t *need) {
     const Options saved = h->opt;
     const int saved_bps = h->used_blocks_per_sm;
     int rc = CLS_OK;
-    for (int block : {h->opt.block, 64, 128}) {
+    for (int block : {h->opt.block, 128, 256}) {
         if (block != saved.block && saved.schedule != CLS_SCHED_AUTO) continue;
         h->opt.block = block;
         if (saved.schedule == CLS_SCHED_AUTO) h->opt.schedule = CLS_SCHED_EVENT;
@@ -783,7 +783,7 @@ int cls_autotune(cls_handle *h, uint64_t n_pilot, uint64_t seed, void *stream) {
     for (int gg : groupings) {
         for (int b : {64, 128, 256})
             for (int c : {64, 256, 1024}) cand.push_back({CLS_SCHED_HISTORY, b, c, h->opt.events_per_pass, gg});
-        for (int b : {64, 128})
+        for (int b : {128, 256})
             for (int e : {4, 16}) cand.push_back({CLS_SCHED_EVENT, b, h->opt.chunk, e, gg});
     }
     cudaStream_t s = (cudaStream_t)stream;

@@ -149,8 +149,8 @@ __host__ __device__ inline int region_bytes(bool fixed, int nbins_stride) {
     return (region_lane_stats_offset(fixed, nbins_stride) + 8 * 32 * S_NUM + 15) & ~15;
 }
 
-// Largest block of the event tracker (its launch bounds: 5 such blocks per SM).
-constexpr int kEventBlockThreads = 128;
+// Largest block of the event tracker (its launch bounds: 2 such blocks per SM).
+constexpr int kEventBlockThreads = 256;
 
 // Largest block of the FP64 history tracker (its launch bounds allow 5 such
 // blocks per SM; the host caps the block option at this size for it).
