@@ -407,12 +407,20 @@ def fom_ratios(tal32, tal64, t32, t64):
 
 
 def z_scores(tal_a, tal_b, keys=("R", "T", "A", "total_flux")):
-    """(a - b) / sqrt(sigma_a^2 + sigma_b^2) per case and observable (paper Eq. combined_var);
-    counts that are exactly equal with zero error give no z-score."""
+    """(a - b) / sqrt(sigma_a^2 + sigma_b^2) per case and observable (paper Eq. combined_var).
+    For the count observables R, T, A both errors come from the pooled proportion of the
+    two runs, p (1 - p) / N_a and p (1 - p) / N_b: a run with no counts at all would
+    otherwise report sigma = 0 for a rare outcome.  Observables with zero combined error
+    (no counts on either side) give no z-score."""
     zs = []
     for a, b in zip(tal_a, tal_b):
+        na, nb = a["n_histories"], b["n_histories"]
         for k in keys:
-            comb = math.hypot(a["sigma_" + k], b["sigma_" + k])
+            if k in ("R", "T", "A"):
+                p = (a[k] * na + b[k] * nb) / (na + nb)
+                comb = math.sqrt(p * (1 - p) * (1 / na + 1 / nb))
+            else:
+                comb = math.hypot(a["sigma_" + k], b["sigma_" + k])
             if comb > 0:
                 zs.append((a[k] - b[k]) / comb)
     zs = np.array(zs)
