@@ -406,26 +406,46 @@ def fom_ratios(tal32, tal64, t32, t64):
     return out
 
 
+def count_z(ka: int, na: int, kb: int, nb: int):
+    """Two runs' counts of one outcome (ka of na histories, kb of nb) compared by the
+    exact conditional (Fisher) test: under equal rates, given k = ka + kb, ka is
+    hypergeometric (k of the na + nb histories, na of them in run a).  The two-sided
+    p-value is returned as the normal z of the same tail probability, signed as
+    ka/na - kb/nb; for large counts it is the combined-variance z with the pooled
+    proportion (Eq. combined_var).  None when neither run saw the outcome, or both
+    saw it every time."""
+    from scipy import stats
+    k, m = ka + kb, na + nb
+    if k == 0 or k == m:
+        return None
+    dist = stats.hypergeom(m, k, na)
+    tail = dist.sf(ka - 1) if ka >= k * na / m else dist.cdf(ka)
+    z = float(stats.norm.isf(min(1.0, 2.0 * tail) / 2.0))
+    return z if ka / na >= kb / nb else -z
+
+
 def z_scores(tal_a, tal_b, keys=("R", "T", "A", "total_flux")):
-    """(a - b) / sqrt(sigma_a^2 + sigma_b^2) per case and observable (paper Eq. combined_var).
-    For the count observables R, T, A both errors come from the pooled proportion of the
-    two runs, p (1 - p) / N_a and p (1 - p) / N_b: a run with no counts at all would
-    otherwise report sigma = 0 for a rare outcome.  Observables with zero combined error
-    (no counts on either side) give no z-score."""
+    """Per case and observable, the difference of two runs in units of its standard
+    error: <phi> with each run's own error, (a - b) / sqrt(sigma_a^2 + sigma_b^2)
+    (paper Eq. combined_var); the counts R, T, A by the exact conditional test
+    (count_z), since a rare outcome may have a handful of counts, or none, in one run.
+    Returns the summary and the largest |z| with its case and observable."""
     zs = []
-    for a, b in zip(tal_a, tal_b):
-        na, nb = a["n_histories"], b["n_histories"]
+    for case, (a, b) in enumerate(zip(tal_a, tal_b)):
+        na, nb = int(a["n_histories"]), int(b["n_histories"])
         for k in keys:
             if k in ("R", "T", "A"):
-                p = (a[k] * na + b[k] * nb) / (na + nb)
-                comb = math.sqrt(p * (1 - p) * (1 / na + 1 / nb))
+                z = count_z(int(round(a[k] * na)), na, int(round(b[k] * nb)), nb)
             else:
                 comb = math.hypot(a["sigma_" + k], b["sigma_" + k])
-            if comb > 0:
-                zs.append((a[k] - b[k]) / comb)
-    zs = np.array(zs)
-    return {"max_abs": float(np.max(np.abs(zs))), "rms": float(np.sqrt(np.mean(zs * zs))),
-            "above_4": int(np.sum(np.abs(zs) > 4)), "n": int(zs.size)}
+                z = (a[k] - b[k]) / comb if comb > 0 else None
+            if z is not None:
+                zs.append((z, case, k, a[k], b[k]))
+    v = np.array([z[0] for z in zs])
+    worst = max(zs, key=lambda z: abs(z[0]))
+    return {"max_abs": float(np.max(np.abs(v))), "rms": float(np.sqrt(np.mean(v * v))),
+            "above_4": int(np.sum(np.abs(v) > 4)), "n": int(v.size),
+            "worst": {"case": worst[1], "observable": worst[2], "a": worst[3], "b": worst[4]}}
 
 
 def oracle_tallies(raw, case):
@@ -546,6 +566,30 @@ def sweep_arms(args, rank, world, pg, local, pool):
                              "events_per_pass": events64}
         out["clocks64"] = s64
         out["fom"] = fom_ratios(tal32, tal64, t32, t64)
+        # the FOM ratio's two factors: FP32 plain (one launch per case, as the FP64 arm)
+        # isolates precision, FP32 batched over FP32 plain isolates batching
+        plain32 = [cls.Problem(c) for c in cases]
+        for p in plain32:
+            p.set_option("precision", "fp32")
+            p.run(20_000, 99, stream=stream)
+            p.reset()
+            p.set_option("first_history", base + (args.warmup + args.steps + E2E_STEPS) * n)
+        torch.cuda.synchronize()
+        barrier(pg)
+        flush.zero_()
+        a32, z32 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a32.record(stream)
+        for p in plain32:
+            p.run(n, SEED32, stream=stream)
+        z32.record(stream)
+        torch.cuda.synchronize()
+        t32p = max_over_ranks(pg, a32.elapsed_time(z32) * 1e-3)
+        tal32p = [p.tallies() for p in plain32]
+        for p in plain32:
+            p.close()
+        out["fp32_plain"] = {"histories_per_s": world * nc * n / t32p, "s_per_pass": t32p,
+                             "fom_batched_over_plain": fom_ratios(tal32, tal32p, t32, t32p)["total_flux"],
+                             "fom_plain_fp32_over_fp64": fom_ratios(tal32p, tal64, t32p, t64)["total_flux"]}
         out["z_fp32_vs_fp64"] = z_scores(tal32, tal64)
         # ---- identical outcomes: both precisions walk ids [0, n) of every case on the FP64
         # arm's seed once more, untimed, recording each history's outcome on the device
@@ -693,6 +737,10 @@ def headline(args, rank, world, pg, local):
             "events_per_s": p64["events_per_s"], "launches": len(cases),
             "roofline": roofline("history_kernel<double, 1|3>", "sweep_plain", p64["ops_per_pass"], p64["s_per_pass"],
                                  p64["events_per_pass"], clk_mhz, False)}
+        if "fp32_plain" in sw:
+            line["fp32_plain"] = dict(sw["fp32_plain"], note=(
+                "the same cases in FP32, one launch per case: FOM(FP32 batched)/FOM(FP64 plain) = "
+                "batching (FP32 batched over FP32 plain) x precision (FP32 plain over FP64 plain)"))
         line["fom_fp32_batched_over_fp64_plain"] = dict(sw["fom"], note=(
             "per case, FOM = 1/(sigma_rel^2 T) with T the arm's whole-sweep time; equal N is equal sigma "
             "(sigma^2 ~ 1/N), so this is also T64/T32 at equal sigma"))

@@ -43,3 +43,19 @@ def test_algorithmic_ops_grow_with_the_work():
     assert 150 < per_event < 200
     more_bins = bench.algorithmic_ops((0.1, 10.0, 1.0, 0.1, 0.99, 0.99, 10.0, 3, 2000), t)
     assert more_bins > ops
+
+
+def test_count_z_is_the_pooled_z_for_large_counts_and_sane_for_few():
+    """The bench compares two runs' R, T, A counts by the exact conditional test: for
+    large counts it equals the combined-variance z with the pooled proportion (Eq.
+    combined_var); for a rare outcome with a handful of counts, or none, in one run it
+    stays a fair z (35 counts in 2e9 histories against none in 1e8 is not significant)."""
+    import math
+    for ka, na, kb, nb in ((72000, 100000, 71500, 100000), (1440000000, 2000000000, 72030000, 100000000),
+                           (30, 100000, 52, 100000)):
+        p = (ka + kb) / (na + nb)
+        pooled = (ka / na - kb / nb) / math.sqrt(p * (1 - p) * (1 / na + 1 / nb))
+        assert abs(bench.count_z(ka, na, kb, nb) - pooled) < 0.05 * max(1.0, abs(pooled))
+    assert abs(bench.count_z(35, 2_000_000_000, 0, 100_000_000)) < 1.5
+    assert bench.count_z(0, 100, 0, 100) is None and bench.count_z(100, 100, 50, 50) is None
+    assert bench.count_z(0, 1000, 40, 1000) < -5
