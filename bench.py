@@ -530,6 +530,8 @@ def sweep_arms(args, rank, world, pg, local, pool):
         "events_per_s": world * events32 * args.steps / t32,
         "collisions_per_s": world * sum(t["n_coll"] for t in tal32) / t32,
         "events_per_history": events32 / (nc * n), "autotuned": tuned,
+        "events_per_step_by_geometry": {int(g): sum(t["n_events"] for c, t in zip(cases, tal32) if int(c[7]) == g)
+                                        / args.steps for g in sorted({int(c[7]) for c in cases})},
         "launch_ms": [1e3 * x for x in times], "ops_per_step": ops32, "events_per_step": events32}
     out["e2e"] = {"value": world * nc * n * E2E_STEPS / e2e_s, "unit": "histories/s", "steps": E2E_STEPS,
                   "h2d_bytes_per_step": nc * 40 + 24,
@@ -675,8 +677,8 @@ def box_arms(args, rank, world, pg, local):
     clk = merge_clocks(samplers) if samplers else None
     clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
     full = n == workloads.BOX_L10_HISTORIES
-    names = {"fp64": ("history_kernel<double, 3>", "box"), "fp32": ("history_kernel<float, 3>", "box"),
-             "fp64_x": ("history_kernel<double, 13>", "box_x"), "fp32_x": ("history_kernel<float, 13>", "box_x")}
+    names = {"fp64": ("history_kernel<double, 3, false>", "box"), "fp32": ("history_kernel<float, 3, false>", "box"),
+             "fp64_x": ("history_kernel<double, 13, false>", "box_x"), "fp32_x": ("history_kernel<float, 13, false>", "box_x")}
     for arm, r in results.items():
         k, w = names[arm]
         r["roofline"] = roofline(k, w, r["ops_per_launch"], r["launch_s"], r["events_per_launch"], clk_mhz, full)
@@ -766,10 +768,11 @@ def headline(args, rank, world, pg, local):
 
 
 def sweep_kernels(tuned) -> str:
-    """The FP32 sweep's kernels: one mixed-geometry launch, or one per geometry (rods, boxes)."""
+    """The FP32 sweep's kernels: one mixed-geometry launch, or one per geometry (rods,
+    boxes; their cases' short histories take the warp-summed-counters instance)."""
     if tuned.get("group_geometry", 0):
-        return "history_kernel<float, 1> + history_kernel<float, 3>"
-    return "history_kernel<float, 0>"
+        return "history_kernel<float, 1, true> + history_kernel<float, 3, true>"
+    return "history_kernel<float, 0, true>"
 
 
 def box_only(args, rank, world, pg, local):
@@ -823,7 +826,8 @@ def diffusive_workload(args, rank, world, pg, local):
     clk_mhz = sampler.summary().get("sm_mhz") or 2070.0
     full = n == workloads.BOX_DIFFUSIVE_HISTORIES
     for sched, r in out.items():
-        r["roofline"] = roofline(f"{sched}_kernel<float, 3>", "diffusive", r["ops_per_launch"], r["launch_s"],
+        r["roofline"] = roofline("history_kernel<float, 3, false>" if sched == "history" else "event_kernel<float, 3>",
+                                 "diffusive", r["ops_per_launch"], r["launch_s"],
                                  r["events_per_launch"], clk_mhz, full)
     if rank == 0:
         h = out["history"]

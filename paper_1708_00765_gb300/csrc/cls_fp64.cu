@@ -6,14 +6,28 @@
 
 namespace cls {
 
+// Internal linkage: the other precision's translation unit has a launcher of the
+// same name and signature, and two external definitions would be merged by the
+// linker into one (whichever it keeps, launching the other precision's kernel).
+namespace {
+
 template <int G>
 cudaError_t launch_history_g(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
+    if (G != 0 && a.warp_counts) {
+        static std::atomic<unsigned long long> optin_wc{0};
+        const cudaError_t e = ensure_smem_optin(history_kernel<double, G, true>, optin_wc);
+        if (e != cudaSuccess) return e;
+        history_kernel<double, G, true><<<grid, block, smem, s>>>(a);
+        return cudaGetLastError();
+    }
     static std::atomic<unsigned long long> optin{0};
     const cudaError_t e = ensure_smem_optin(history_kernel<double, G>, optin);
     if (e != cudaSuccess) return e;
     history_kernel<double, G><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
+
+}  // namespace
 
 // One instantiation per geometry (compile-time branches) plus the mixed one.
 cudaError_t launch_history_fp64(const LaunchArgs &a, int grid, int block, size_t smem, cudaStream_t s, int geom) {

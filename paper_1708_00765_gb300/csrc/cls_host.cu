@@ -104,7 +104,7 @@ struct cls_handle {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<uint64_t> graph_total_chunks;
-    int graph_key[9] = {0};
+    int graph_key[10] = {0};
 };
 
 namespace {
@@ -298,8 +298,13 @@ int case_schedule(const cls_handle *h, int k) {
 // first, then the group of largest estimated cost first.  gk[k]: case k's group.
 struct Group {
     int sched, geom;
-    double cost;
+    double cost;   // summed estimated events per history of its cases
+    int ncases;
 };
+
+// A launch whose cases average fewer estimated events per history than this
+// sums its history-end counters over the warp first.
+constexpr double kWarpCountCost = 32.0;
 
 std::vector<Group> plan_groups(const cls_handle *h, std::vector<int> *gk) {
     std::vector<Group> groups;
@@ -310,8 +315,9 @@ std::vector<Group> plan_groups(const cls_handle *h, std::vector<int> *gk) {
         const int ge = h->opt.group_geometry ? h->cases[k].d : h->geom;
         int g = 0;
         while (g < (int)groups.size() && !(groups[g].sched == sc && groups[g].geom == ge)) ++g;
-        if (g == (int)groups.size()) groups.push_back({sc, ge, 0.0});
+        if (g == (int)groups.size()) groups.push_back({sc, ge, 0.0, 0});
         groups[g].cost += h->cases[k].cost;
+        groups[g].ncases += 1;
         of[k] = g;
     }
     std::vector<int> order(groups.size());
@@ -361,7 +367,10 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, RunPlan *plan) {
     a.max_events = h->opt.max_events;
     a.region_bytes = region_bytes_for(h);
     a.flush_every = (h->opt.precision == CLS_PREC_FP32) ? kFp32FlushHistories : 0;
-    a.outcomes = outcome_record(h->d_runs, nc);
+    // the record's binding is read from device memory at every launch (graph
+    // replays see the current buffer); while nothing is recorded the kernels are
+    // given no record at all and skip that read
+    a.outcomes = h->outcome_codes ? outcome_record(h->d_runs, nc) : nullptr;
     int idx = 0;
     plan->ngroups = (int)groups.size();
     for (int g = 0; g < plan->ngroups; ++g) {
@@ -385,6 +394,7 @@ int prepare_run(cls_handle *h, uint64_t n, uint64_t seed, RunPlan *plan) {
         ag.nruns = idx - off;
         ag.total_chunks = chunks;
         ag.chunk_counter = h->d_chunk_counter + g;
+        ag.warp_counts = (groups[g].geom == 0 || groups[g].cost < kWarpCountCost * groups[g].ncases) ? 1 : 0;
         plan->sched[g] = groups[g].sched;
         plan->geom[g] = groups[g].geom;
     }
@@ -1007,8 +1017,9 @@ int cls_batch_run(cls_handle *h, uint64_t n, uint64_t seed, void *stream) {
     // ranges) before replaying the graph.  The groups' launches are parallel
     // branches of the graph: the second starts its blocks as the first one's
     // drain, so their tails overlap.
-    const int key[9] = {h->opt.precision, h->opt.schedule, h->opt.block, h->opt.chunk, (int)h->opt.max_events,
-                        h->opt.blocks_per_sm, (int)(seed & 0x7fffffff), (int)(seed >> 31), h->opt.group_geometry};
+    const int key[10] = {h->opt.precision, h->opt.schedule, h->opt.block, h->opt.chunk, (int)h->opt.max_events,
+                         h->opt.blocks_per_sm, (int)(seed & 0x7fffffff), (int)(seed >> 31), h->opt.group_geometry,
+                         h->outcome_codes != nullptr};
     std::vector<uint64_t> tc(plan.ngroups);
     for (int g = 0; g < plan.ngroups; ++g) tc[g] = plan.a[g].total_chunks;
     if (h->graph_exec && (tc != h->graph_total_chunks || std::memcmp(key, h->graph_key, sizeof(key))))
@@ -1159,6 +1170,8 @@ int cls_autotune_cases(cls_handle *h, uint64_t n_pilot, uint64_t seed, void *str
 
 int cls_record_outcomes(cls_handle *h, uint8_t *d_codes, uint64_t capacity) {
     if (!h || (d_codes && capacity == 0)) return CLS_E_INVAL;
+    // switching recording on or off changes the launches' arguments: recapture
+    if ((d_codes != nullptr) != (h->outcome_codes != nullptr)) destroy_graph(h);
     h->outcome_codes = d_codes;
     h->outcome_cap = d_codes ? capacity : 0;
     return CLS_OK;

@@ -142,6 +142,7 @@ extern "C" int cls_run_noalloc(const double *params, int ncases, uint64_t first,
     a.max_events = 100000000u;
     a.region_bytes = region_bytes(false, nbins_stride);
     a.flush_every = 0;
+    a.warp_counts = 1;
 
     const size_t per_warp = 2 * (size_t)a.region_bytes;
     int warps = (int)((200 * 1024) / per_warp);

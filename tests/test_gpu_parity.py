@@ -338,6 +338,20 @@ def test_fp32_tallies_are_an_fp64_sum_of_the_fp32_flights(params):
     np.testing.assert_allclose(raw["flux"].sum(0), bins, rtol=1e-4, atol=1e-6 * bins.max())
 
 
+@pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10, workloads.suite_case("2c", d=11, nbins=50)])
+@pytest.mark.parametrize("schedule", ["history", "event"])
+def test_fp32_mode_runs_the_fp32_walk(params, schedule):
+    """The same histories walked in FP32 and in FP64: outcomes all but identical, but the
+    track sums differ at the float rounding level -- they would be bit-equal if the
+    FP32 handle ran the FP64 kernels (the two precisions' launchers once collided at
+    link time)."""
+    raw32, _ = gpu_raw(params, 20_000, 3, precision="fp32", schedule=schedule)
+    raw64, _ = gpu_raw(params, 20_000, 3, schedule=schedule)
+    assert abs(raw32["nR"] - raw64["nR"]) <= 3
+    rel = abs(raw32["sum_t"] - raw64["sum_t"]) / raw64["sum_t"]
+    assert 1e-12 < rel < 1e-4
+
+
 @pytest.mark.parametrize("schedule", ["history", "event"])
 @pytest.mark.parametrize("nbins", [7, 200, 2000])
 def test_fp32_flux_bins_add_up_to_the_track(schedule, nbins):
