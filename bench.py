@@ -677,8 +677,8 @@ def box_arms(args, rank, world, pg, local):
     clk = merge_clocks(samplers) if samplers else None
     clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
     full = n == workloads.BOX_L10_HISTORIES
-    names = {"fp64": ("history_kernel<double, 3, false>", "box"), "fp32": ("history_kernel<float, 3, false>", "box"),
-             "fp64_x": ("history_kernel<double, 13, false>", "box_x"), "fp32_x": ("history_kernel<float, 13, false>", "box_x")}
+    names = {"fp64": ("history_kernel<double, 3, 0>", "box"), "fp32": ("history_kernel<float, 3, 0>", "box"),
+             "fp64_x": ("history_kernel<double, 13, 0>", "box_x"), "fp32_x": ("history_kernel<float, 13, 0>", "box_x")}
     for arm, r in results.items():
         k, w = names[arm]
         r["roofline"] = roofline(k, w, r["ops_per_launch"], r["launch_s"], r["events_per_launch"], clk_mhz, full)
@@ -771,8 +771,8 @@ def sweep_kernels(tuned) -> str:
     """The FP32 sweep's kernels: one mixed-geometry launch, or one per geometry (rods,
     boxes; their cases' short histories take the warp-summed-counters instance)."""
     if tuned.get("group_geometry", 0):
-        return "history_kernel<float, 1, true> + history_kernel<float, 3, true>"
-    return "history_kernel<float, 0, true>"
+        return "history_kernel<float, 1, 1> + history_kernel<float, 3, 1>"
+    return "history_kernel<float, 0, 1>"
 
 
 def box_only(args, rank, world, pg, local):
@@ -826,7 +826,7 @@ def diffusive_workload(args, rank, world, pg, local):
     clk_mhz = sampler.summary().get("sm_mhz") or 2070.0
     full = n == workloads.BOX_DIFFUSIVE_HISTORIES
     for sched, r in out.items():
-        r["roofline"] = roofline("history_kernel<float, 3, false>" if sched == "history" else "event_kernel<float, 3>",
+        r["roofline"] = roofline("history_kernel<float, 3, 0>" if sched == "history" else "event_kernel<float, 3>",
                                  "diffusive", r["ops_per_launch"], r["launch_s"],
                                  r["events_per_launch"], clk_mhz, full)
     if rank == 0:

@@ -369,6 +369,14 @@ int cls_debug_uniform(uint64_t seed, uint32_t case_id, const uint64_t *h, const 
 int cls_debug_math(const uint64_t *k, int n, double *ln1m, double *sin2pi, double *cos2pi, double *u, double *mu,
                    double *recip_mu);
 
+/* The FP32 walk's fixed-point conversion: out[i] = round(c[i] 2^32), to the
+ * nearest integer with ties to even, the form in which the FP32 walk adds its
+ * flights' track lengths to the tallies (exact sums; paper Sec. 4's
+ * track-length estimator).  c: n floats in [0, 2^32); out: n u64.  Host
+ * arrays; synchronous.  Errors: CLS_E_INVAL (c[i] outside [0, 2^32) or NaN,
+ * n < 1, NULL), CLS_E_CUDA, CLS_E_NOMEM. */
+int cls_debug_fixed32(const float *c, int n, unsigned long long *out);
+
 /* ------------------------------------------------- allocation-free run */
 
 /* Largest number of cases one cls_run_noalloc call takes, and its largest

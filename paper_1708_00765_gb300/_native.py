@@ -44,7 +44,8 @@ CLS_SCHED_EVENT = 2
 # every symbol include/cls.h declares
 EXPORTED = ("cls_create", "cls_set_option", "cls_get_option", "cls_run", "cls_tallies", "cls_raw_tallies",
             "cls_reset", "cls_destroy", "cls_strerror", "cls_trace", "cls_batch_create", "cls_batch_run",
-            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_debug_math", "cls_run_noalloc", "cls_autotune", "cls_finalize_raw",
+            "cls_batch_tallies", "cls_num_cases", "cls_debug_philox", "cls_debug_uniform", "cls_debug_math",
+            "cls_debug_fixed32", "cls_run_noalloc", "cls_autotune", "cls_finalize_raw",
             "cls_record_outcomes", "cls_batch_set_case_schedule", "cls_batch_get_case_schedule",
             "cls_autotune_cases", "cls_workspace_bytes", "cls_bind_workspace")
 
@@ -118,6 +119,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "cls_debug_philox": ([P(u32), i, P(u32), P(u32)], i),
         "cls_debug_uniform": ([u64, u32, P(u64), P(u64), i, P(d), P(ctypes.c_float)], i),
         "cls_debug_math": ([P(u64), i, P(d), P(d), P(d), P(d), P(d), P(d)], i),
+        "cls_debug_fixed32": ([P(ctypes.c_float), i, P(u64)], i),
         "cls_run_noalloc": ([P(d), i, u64, u64, u64, i, i, H, H, H, H], i),
         "cls_autotune": ([H, u64, u64, H], i),
         "cls_finalize_raw": ([P(cls_raw_t), P(d), P(u64), d, P(cls_tallies_t)], i),
@@ -331,6 +333,15 @@ def debug_math(k):
     n = k.size
     out = {name: np.zeros(n) for name in ("ln1m", "sin2pi", "cos2pi", "u", "mu", "recip_mu")}
     _check(load().cls_debug_math(_ptr(k, ctypes.c_uint64), n, *(_ptr(out[name]) for name in out)), "cls_debug_math")
+    return out
+
+
+def debug_fixed32(c):
+    """cls_debug_fixed32: the FP32 walk's conversion round(c 2^32) of floats c in [0, 2^32)."""
+    c = np.ascontiguousarray(c, dtype=np.float32)
+    out = np.zeros(c.size, dtype=np.uint64)
+    _check(load().cls_debug_fixed32(_ptr(c, ctypes.c_float), c.size, _ptr(out, ctypes.c_uint64)),
+           "cls_debug_fixed32")
     return out
 
 

@@ -1,6 +1,7 @@
 // cls_debug.cu -- diagnostic entry points: the device Philox next to CUDA's
-// curand_Philox4x32_10 (called from CUDA's header, not restated), and the
-// device draw-to-uniform mapping.
+// curand_Philox4x32_10 (called from CUDA's header, not restated), the device
+// draw-to-uniform mapping, the FP64 walk's elementary functions and the FP32
+// walk's fixed-point conversion.
 #include <curand_kernel.h>
 
 #include <vector>
@@ -68,6 +69,11 @@ __global__ void math_kernel(const uint64_t *k, int n, double *out) {
     o[4] = mu;
     o[5] = cls::Real<double>::recip(mu);
 }
+__global__ void fixed32_kernel(const float *c, int n, unsigned long long *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = cls::fixed32(c[i]);
+}
 }  // namespace
 
 extern "C" int cls_debug_philox(const uint32_t *in, int n, uint32_t *ours, uint32_t *theirs) {
@@ -132,4 +138,23 @@ extern "C" int cls_debug_math(const uint64_t *k, int n, double *ln1m, double *si
         if (outs[c])
             for (int i = 0; i < n; ++i) outs[c][i] = host[6 * (size_t)i + c];
     return CLS_OK;
+}
+
+extern "C" int cls_debug_fixed32(const float *c, int n, unsigned long long *out) {
+    if (!c || !out || n < 1) return CLS_E_INVAL;
+    for (int i = 0; i < n; ++i)
+        if (!(c[i] >= 0.0f && c[i] < 0x1p32f)) return CLS_E_INVAL;
+    float *dc = nullptr;
+    if (cudaMalloc(&dc, (size_t)n * (sizeof(float) + sizeof(unsigned long long)) + 8) != cudaSuccess)
+        return CLS_E_NOMEM;
+    unsigned long long *dout = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(dc + n) + 7) & ~static_cast<uintptr_t>(7));
+    cudaError_t e = cudaMemcpy(dc, c, n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        fixed32_kernel<<<(n + 255) / 256, 256>>>(dc, n, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    cudaFree(dc);
+    return e == cudaSuccess ? CLS_OK : CLS_E_CUDA;
 }

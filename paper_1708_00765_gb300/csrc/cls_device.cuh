@@ -777,10 +777,19 @@ __device__ __forceinline__ unsigned long long *region_fixed(unsigned char *regio
     return reinterpret_cast<unsigned long long *>(region);
 }
 
-// round(c 2^32) for 0 <= c < 2^32: scaling by 2^32 is exact in float, and the
-// conversion rounds to the nearest integer (a float has 24 significant bits,
-// so c >= 2^-8 converts exactly; smaller values round to a multiple of 2^-32)
-__device__ __forceinline__ unsigned long long fixed32(float c) { return __float2ull_rn(c * 0x1p32f); }
+// round(c 2^32), ties to even, for 0 <= c < 2^32, in two 32-bit halves: the
+// integer part of c, and the fraction c - floor(c) (exact in float) scaled by
+// 2^32 (exact) and rounded to the nearest integer, below 2^32 because a
+// fraction of a float is at most 1 - 2^-24.  The halves add up to the one
+// rounding of c 2^32, since its integer part shifts the rounded value by a
+// multiple of 2^32.  Two 32-bit conversions instead of one to 64 bits: those
+// run on the FP64 pipe, which the walk's history-end statistics already use
+// (measured 1% faster on the sweep and the 3D box).
+__device__ __forceinline__ unsigned long long fixed32(float c) {
+    const uint32_t hi = __float2uint_rz(c);
+    const float frac = c - __uint2float_rz(hi);
+    return ((unsigned long long)hi << 32) | __float2uint_rn(frac * 0x1p32f);
+}
 
 // The lanes' own copies of the per-history statistics: FP64 in FP64 regions;
 // in FP32 regions u64 fixed point -- t, t0, t1 with 32 fraction bits, t^2 with

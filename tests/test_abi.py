@@ -12,7 +12,7 @@ def declared_symbols():
     with open(os.path.join(ROOT, "include", "cls.h")) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(cls_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(cls_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_library_exports_every_declared_symbol():

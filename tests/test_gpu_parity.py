@@ -120,6 +120,42 @@ def test_device_log_sincos_reciprocal_accuracy():
     assert float(ulps(out["recip_mu"][nz], 1 / out["mu"][nz].astype(ld)).max()) <= 1.0
 
 
+def _round_times_2_32(c):
+    """round(c 2^32), ties to even, exactly, from the float32's significand and exponent."""
+    bits = c.view(np.uint32).astype(np.int64)
+    ex, fr = (bits >> 23) & 0xFF, bits & 0x7FFFFF
+    m = np.where(ex > 0, fr | 0x800000, fr)             # c = m 2^(e - 23)
+    sh = np.where(ex > 0, ex - 127, -126) - 23 + 32     # c 2^32 = m 2^sh
+    out = np.zeros(c.size, dtype=np.uint64)
+    up = sh >= 0
+    out[up] = m[up].astype(np.uint64) << sh[up].astype(np.uint64)
+    s = np.minimum(-sh[~up], 40)                        # m < 2^24: 2^40 rounds everything to 0
+    q, r, half = m[~up] >> s, m[~up] & ((1 << s) - 1), 1 << (s - 1)
+    out[~up] = (q + ((r > half) | ((r == half) & (q & 1 == 1)))).astype(np.uint64)
+    return out
+
+
+def test_fp32_fixed_point_conversion_rounds_exactly():
+    """The FP32 walk adds track lengths to its tallies as round(c 2^32) with ties to
+    even (exact integer sums): the device conversion against that value worked out
+    from the float's bits, on ties, range ends and random floats across [0, 2^32)."""
+    rng = np.random.default_rng(5)
+    edge = np.array([0.0, 2.0**-33, 3 * 2.0**-33, 5 * 2.0**-33, 2.0**-32, 1.5 * 2.0**-32, 2.5 * 2.0**-32, 2.0**-40,
+                     2.0**-126, 2.0**-8, 2.0**-8 + 2.0**-31, 0.5, 1.0, 1 - 2.0**-24, 1 + 2.0**-23, 2.0**23,
+                     2.0**23 + 1, 2.0**24, 2.0**24 + 2, 2.0**31, 2.0**32 - 256, 12345.678], dtype=np.float32)
+    scale = 2.0 ** rng.integers(-45, 32, 200_000).astype(np.float64)
+    rnd = (rng.random(200_000) * scale).astype(np.float32)
+    c = np.concatenate([edge, rnd, np.float32(2.0**-40) * np.arange(1, 2000, dtype=np.float32)])
+    c = c[c < np.float32(2.0**32)]
+    got = cls.debug_fixed32(c)
+    ref = _round_times_2_32(c)
+    bad = np.nonzero(got != ref)[0]
+    assert bad.size == 0, [(float(c[i]), int(got[i]), int(ref[i])) for i in bad[:5]]
+    assert got[0] == 0 and got[1] == 0 and got[2] == 2 and got[3] == 2 and got[5] == 2 and got[6] == 2
+    with pytest.raises(cls.ClsError):
+        cls.debug_fixed32(np.array([1.0, -1.0], dtype=np.float32))
+
+
 # -------------------------------------------------------------- traces
 
 @pytest.mark.parametrize("params", [workloads.ROD_L10, workloads.BOX_L10, workloads.suite_case("1c", nbins=10),

@@ -90,3 +90,27 @@ def test_workspace_errors_and_unbinding():
     prob.run(1000, 1)
     same_tallies(prob.raw_tallies(), bound)
     prob.close()
+
+
+def test_bound_workspace_with_several_event_launch_groups():
+    """Rods and boxes, half of each on the event schedule: four launch groups, two of
+    them event launches with their own slices of the bank, all in the caller's
+    tensor; the same tallies as the library-owned buffers."""
+    cases = workloads.batch_sweep(12, seed=7, nbins=20)
+
+    def run(ws):
+        prob = cls.Problem(cases, batch=True)
+        prob.set_option("schedule", "history")
+        for k in range(0, 12, 2):
+            prob.set_case_schedule(k, "event")
+        buf = None
+        if ws:
+            buf = torch.empty(prob.workspace_bytes(), dtype=torch.uint8, device="cuda")
+            prob.bind_workspace(buf.data_ptr(), buf.numel())
+        prob.run(3000, 8)
+        out = [prob.raw_tallies(k) for k in range(12)]
+        prob.close()
+        return out
+
+    for a, b in zip(run(True), run(False)):
+        same_tallies(a, b)
