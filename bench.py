@@ -592,6 +592,7 @@ def sweep_arms(args, rank, world, pg, local, pool):
         out["fp32_plain"] = {"histories_per_s": world * nc * n / t32p, "s_per_pass": t32p,
                              "fom_batched_over_plain": fom_ratios(tal32, tal32p, t32, t32p)["total_flux"],
                              "fom_plain_fp32_over_fp64": fom_ratios(tal32p, tal64, t32p, t64)["total_flux"]}
+        out["fp32_batching_by_size"] = batching_by_size(cases, (100_000, 1_000_000), flush, stream)
         out["z_fp32_vs_fp64"] = z_scores(tal32, tal64)
         # ---- identical outcomes: both precisions walk ids [0, n) of every case on the FP64
         # arm's seed once more, untimed, recording each history's outcome on the device
@@ -692,6 +693,35 @@ def box_arms(args, rank, world, pg, local):
     return results
 
 
+def batching_by_size(cases, sizes, flush, stream):
+    """Batching's gain at fewer histories per case, where per-launch overheads and
+    tails weigh more: the sweep batched (autotuned for the size, graph replay) against
+    one handle and one launch per case (default shape), FP32, median of 3 passes each."""
+    import torch
+    import paper_1708_00765_gb300 as cls
+    out = {}
+    for n in sizes:
+        b = cls.Problem(cases, batch=True)
+        b.set_option("precision", "fp32")
+        tuned = b.autotune(max(4096, min(n // 16, 262_144)), seed=3, stream=stream)
+        tb = sorted(timed_pass(lambda: b.run(n, 7, stream=stream), 3, 1, flush, torch, stream))[1]
+        b.close()
+        plain = [cls.Problem(c) for c in cases]
+        for p in plain:
+            p.set_option("precision", "fp32")
+
+        def run_plain():
+            for p in plain:
+                p.run(n, 7, stream=stream)
+        tp = sorted(timed_pass(run_plain, 3, 1, flush, torch, stream))[1]
+        for p in plain:
+            p.close()
+        out[f"{n:.0e}".replace("+0", "")] = {"batched_histories_per_s": len(cases) * n / tb,
+                                             "plain_histories_per_s": len(cases) * n / tp,
+                                             "batched_over_plain": tp / tb, "autotuned": tuned}
+    return out
+
+
 # ------------------------------------------------------------- headline line
 def headline(args, rank, world, pg, local):
     import torch
@@ -727,7 +757,7 @@ def headline(args, rank, world, pg, local):
                    "l2": "flushed between steps (512 MB write)"},
         "clocks": clk,
         "e2e": sw["e2e"],
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_replay(f32["autotuned"], cases),
         "roofline": roofline(sweep_kernels(f32["autotuned"]), "sweep", f32["ops_per_step"],
                              f32["ms_per_step"] * 1e-3, f32["events_per_step"], clk_mhz, full),
         "fp32_batched": {k: v for k, v in f32.items() if k not in ("ops_per_step",)},
@@ -743,6 +773,8 @@ def headline(args, rank, world, pg, local):
             line["fp32_plain"] = dict(sw["fp32_plain"], note=(
                 "the same cases in FP32, one launch per case: FOM(FP32 batched)/FOM(FP64 plain) = "
                 "batching (FP32 batched over FP32 plain) x precision (FP32 plain over FP64 plain)"))
+            line["fp32_batching_by_size"] = dict(sw["fp32_batching_by_size"], note=(
+                "the same comparison at 1e5 and 1e6 histories per case (rates, not FOM: equal N on both sides)"))
         line["fom_fp32_batched_over_fp64_plain"] = dict(sw["fom"], note=(
             "per case, FOM = 1/(sigma_rel^2 T) with T the arm's whole-sweep time; equal N is equal sigma "
             "(sigma^2 ~ 1/N), so this is also T64/T32 at equal sigma"))
@@ -765,6 +797,12 @@ def headline(args, rank, world, pg, local):
         pool.close()
         pool.join()
     print(json.dumps(line), flush=True)
+
+
+def launches_per_replay(tuned, cases) -> int:
+    """Kernel launches in one replay of the sweep's graph: one per geometry when the
+    autotuner groups the cases by geometry, else one mixed launch."""
+    return len({int(c[7]) for c in cases}) if tuned.get("group_geometry", 0) else 1
 
 
 def sweep_kernels(tuned) -> str:

@@ -258,8 +258,9 @@ int cls_trace(cls_handle *h, int case_idx, uint64_t seed, uint64_t history, doub
  * (CLS_OPT_GROUP_GEOMETRY) -- on a temporary twin
  * handle with the same cases and precision, so the handle's own tallies are
  * untouched, then set the fastest candidate's options on the handle.  Results
- * are cached by a signature of (precision, cases) in memory and, if the
- * environment variable CLS_AUTOTUNE_CACHE names a file, in that file.  With
+ * are cached by a signature of (precision, cases, floor(log2 n_pilot)) in
+ * memory and, if the environment variable CLS_AUTOTUNE_CACHE names a file, in
+ * that file: a shape tuned for small runs is not reused for large ones.  With
  * CLS_OPT_SCHEDULE = CLS_SCHED_AUTO the first run calls this itself with
  * n_pilot = n/16 clamped to [4096, 262144].  Synchronous on `stream`.
  * Errors: CLS_E_INVAL, CLS_E_NOMEM, CLS_E_CUDA. */

@@ -713,8 +713,11 @@ std::mutex g_tune_mutex;
 std::map<std::string, Tuned> g_tune_cache;
 bool g_tune_file_read = false;
 
-// FNV-1a over (precision, case parameters): identifies a tuning problem.
-std::string tune_signature(const cls_handle *h) {
+// FNV-1a over (precision, case parameters), and the pilot size's power of
+// two: identifies a tuning problem.  The best shape depends on the run's size
+// (small chunks balance a short run, large ones amortise chunk claims in a long
+// one), so a shape tuned on a small pilot is not reused for a large one.
+std::string tune_signature(const cls_handle *h, uint64_t n_pilot) {
     unsigned long long x = 1469598103934665603ull;
     auto mix = [&](const void *p, size_t n) {
         const unsigned char *c = static_cast<const unsigned char *>(p);
@@ -725,8 +728,10 @@ std::string tune_signature(const cls_handle *h) {
     };
     mix(&h->opt.precision, sizeof(int));
     mix(h->params.data(), h->params.size() * sizeof(double));
-    char buf[64];
-    std::snprintf(buf, sizeof(buf), "p%d-n%zu-%016llx", h->opt.precision, h->params.size() / 9, x);
+    int size_bits = 0;
+    while ((n_pilot >> size_bits) > 1) ++size_bits;
+    char buf[80];
+    std::snprintf(buf, sizeof(buf), "p%d-n%zu-s%d-%016llx", h->opt.precision, h->params.size() / 9, size_bits, x);
     return buf;
 }
 
@@ -771,7 +776,7 @@ extern "C" {
 int cls_autotune(cls_handle *h, uint64_t n_pilot, uint64_t seed, void *stream) {
     if (!h || n_pilot == 0 || n_pilot > (1ull << 32)) return CLS_E_INVAL;
     CLS_CUDA(cudaSetDevice(h->device));
-    const std::string key = tune_signature(h);
+    const std::string key = tune_signature(h, n_pilot);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         tune_file_load();

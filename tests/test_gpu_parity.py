@@ -587,25 +587,34 @@ import sys
 sys.path.insert(0, {root!r})
 import paper_1708_00765_gb300 as cls
 p = cls.Problem([0.5, 5.0, 2.0, 0.5, 0.5, 0.9, 10.0, 1, 100])
-print(p.autotune(8192, seed=1))
+print(p.autotune({pilot}, seed=1))
 """
 
 
 def test_autotune_file_cache(tmp_path):
+    """The autotuner's file cache: a second process finds the first one's result for a
+    pilot of the same power of two (8192, then 12000), and a pilot of another size
+    (65536) is tuned afresh under its own key."""
     import os
     import subprocess
     import sys
     cache = tmp_path / "tune.txt"
     env = dict(os.environ, CLS_AUTOTUNE_CACHE=str(cache))
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    for _ in range(2):
-        out = subprocess.run([sys.executable, "-c", TUNE_SCRIPT.format(root=root)], env=env, capture_output=True,
-                             text=True, timeout=300)
+
+    def tune(pilot):
+        out = subprocess.run([sys.executable, "-c", TUNE_SCRIPT.format(root=root, pilot=pilot)], env=env,
+                             capture_output=True, text=True, timeout=300)
         assert out.returncode == 0, out.stderr
-    lines = cache.read_text().splitlines()
+        return cache.read_text().splitlines()
+
+    assert len(tune(8192)) == 1
+    lines = tune(12000)
     assert len(lines) == 1  # the second process found the first one's result
     key, sched, block, chunk, epp, gg = lines[0].split()
-    assert int(sched) in (1, 2) and int(block) in (64, 128, 256)
+    assert "-s13-" in key and int(sched) in (1, 2) and int(block) in (64, 128, 256)
+    lines = tune(65536)
+    assert len(lines) == 2 and "-s16-" in lines[1].split()[0]
 
 
 # ------------------------------------------------ the paper's printed values
