@@ -40,8 +40,8 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 SWEEP_CASES, SWEEP_SEED, SWEEP_BINS = 256, 7, 100
 SWEEP_HISTORIES = 100_000_000  # per case per step
 SWEEP_WORKLOAD = ("batched sweep: 256 cases (seed 7; d in {rod, 3D box}, L in {0.1, 1, 10}, Sigma and Lambda "
-                  "log-uniform, c uniform), 100 bins, FP32 tracking / FP64 tallies, one persistent launch "
-                  "replayed from a CUDA graph")
+                  "log-uniform, c uniform), 100 bins, FP32 tracking / exact tallies, the cases in one CUDA graph "
+                  "replay (persistent launches as the autotuner groups them)")
 BOX_WORKLOAD = "box L=10, Sigma=(0.1,10), Lambda=(1,0.1), c=0.99, cosine incidence, 200 bins"
 SEED32, SEED64 = 1, 2   # the FP32 and FP64 arms draw from independent Philox keys
 E2E_STEPS = 3           # end-to-end steps through the C ABI (host copies in the timed region)
