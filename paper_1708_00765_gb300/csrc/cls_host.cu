@@ -303,7 +303,8 @@ struct Group {
 };
 
 // A launch whose cases average fewer estimated events per history than this
-// sums its history-end counters over the warp first.
+// runs the tracker's short-history instance (history-end counters summed over
+// the warp, deposits that skip zero and past-the-mesh difference entries).
 constexpr double kWarpCountCost = 32.0;
 
 std::vector<Group> plan_groups(const cls_handle *h, std::vector<int> *gk) {

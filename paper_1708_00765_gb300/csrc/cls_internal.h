@@ -110,7 +110,7 @@ struct LaunchArgs {
     uint32_t max_events;
     int region_bytes;     // bytes per warp tally region (see region_bytes())
     int flush_every;      // flush a region after this many histories were fed into it (0: never)
-    int warp_counts;      // history tracker: the instance that sums history-end counters over the warp first (short histories)
+    int warp_counts;      // history tracker: its short-history instance (warp-summed counters, sparse deposits)
     const OutcomeRecord *outcomes;  // per-history outcome record, or nullptr (never recorded)
     // event schedule only
     void *bank;            // grid warps x 2 buffers x bank_slots particles (SoA)
