@@ -337,7 +337,11 @@ def _host_bins_of_fp32_flights(rows, L, nbins, source_x=0.0):
 
 
 @pytest.mark.parametrize("params", [workloads.BOX_L10, workloads.ROD_L10, workloads.suite_case("2c", d=11, nbins=50),
-                                    (1.0, 10.0, 0.5, 0.2, 0.99, 0.99, 10.0, 3, 500)])
+                                    (1.0, 10.0, 0.5, 0.2, 0.99, 0.99, 10.0, 3, 500),
+                                    # thin rod and box: most flights run from x = 0 to x = L, over whole end bins
+                                    # (the short-history instance, whose deposits skip zero and end entries)
+                                    (0.5, 5.0, 2.0, 0.5, 0.5, 0.9, 0.1, 1, 20),
+                                    (0.5, 5.0, 2.0, 0.5, 0.5, 0.9, 0.1, 3, 20)])
 def test_fp32_tallies_are_an_fp64_sum_of_the_fp32_flights(params):
     """FP32 tracking keeps its tallies in FP64 and exact fixed point: each history's
     flights are summed in float along the walk and widened once, every bin deposit
@@ -402,6 +406,22 @@ def test_fp32_flux_bins_add_up_to_the_track(schedule, nbins):
 
 
 # ---------------------------------------------------------------- batches
+
+def test_batch_counts_exact_with_a_large_event_cap():
+    """The short-history instance sums the histories' event counters over the warp in
+    one 32-bit reduction while the event cap is below 2^27, and in 16-bit halves
+    above it: with the cap at 2^28 the counts stay bit-exact against the oracle."""
+    params = workloads.batch_sweep(12, seed=7, nbins=20)
+    prob = cls.Problem(params, batch=True)
+    prob.set_option("max_events", 1 << 28)
+    prob.run(3000, 4)
+    for k in range(params.shape[0]):
+        raw_g = prob.raw_tallies(k)
+        raw_o = oracle.run(ocase(params[k]), 4, 0, 3000, case_id=k, max_events=1 << 28)
+        for key in COUNT_KEYS:
+            assert raw_g[key] == raw_o[key], (k, key)
+    prob.close()
+
 
 @pytest.mark.parametrize("group_geometry", [1, 0])
 def test_batch_cases_match_oracle_exactly(group_geometry):
