@@ -271,6 +271,14 @@ __global__ void __launch_bounds__(kEventBlock, kEventMinBlocks) event_kernel(con
         __syncwarp();
 
         // ----------------------------------------------------------- flights
+        // Once no history is left to start and the bank fits one row of lanes,
+        // the warp walks its last particles to their ends in registers, as the
+        // history tracker does, instead of storing and reloading them through the
+        // bank every events_per_pass events: the longest histories of a launch
+        // (10^4 events and more) would otherwise pay a bank round trip every few
+        // events while the rest of the GPU idles.
+        const bool tail = exhausted && nlive <= 32u;
+        const uint32_t epp = tail ? 0xFFFFFFFFu : a.events_per_pass;
         // collisions, interface crossings, reflections, events of this pass, per region
         uint32_t c0 = 0, i0 = 0, f0 = 0, e0 = 0, c1 = 0, i1 = 0, f1 = 0, e1 = 0;
         uint32_t out = 0;
@@ -296,7 +304,7 @@ __global__ void __launch_bounds__(kEventBlock, kEventMinBlocks) event_kernel(con
             const uint32_t ev0 = alive ? s.events : 0u;
             s.n_coll = s.n_int = s.n_refl = 0;
             bool died = false;
-            for (uint32_t e = 0; e < a.events_per_pass; ++e) {
+            for (uint32_t e = 0; e < epp; ++e) {
                 if (!__any_sync(CLS_FULL_MASK, alive)) break;
                 int o = -1;
                 f.k0 = 0;
