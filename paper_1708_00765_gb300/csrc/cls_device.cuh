@@ -795,8 +795,9 @@ __device__ __forceinline__ unsigned long long fixed32(float c) {
 }
 
 // The lanes' own copies of the per-history statistics: FP64 in FP64 regions;
-// in FP32 regions u64 fixed point -- t, t0, t1 with 32 fraction bits, t^2 with
-// 24 -- so that the FP32 walk sums them exactly without the FP64 pipe.
+// in FP32 regions u64 fixed point -- t0, t1 with 32 fraction bits, t^2 with
+// 24; the slot of t stays unused, its sum being that of t0 and t1 -- so that
+// the FP32 walk sums them exactly.
 template <typename P>
 using LaneStat = typename std::conditional<kFixedBins<P>, unsigned long long, double>::type;
 
